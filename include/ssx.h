@@ -1,0 +1,179 @@
+/*
+ * ssx.h -- C ABI of the GB300 surface-source-extension solver.
+ *
+ * The library solves the source subproblem of W. W. Symes, "Efficient
+ * Computation of Extended Surface Sources" (arXiv 2203.16573), eqn:esis:
+ *
+ *     given the medium, choose h on the line z = z_s minimising
+ *     || S h - d ||^2 + alpha || A h ||^2,   (A h)(x, t) = |x - x_s| h(x, t)
+ *
+ * by Algorithm 1 (preconditioned CG on the weighted normal equation
+ * eqn:normpart) with the time-reversal preconditioner of eqn:defprecond /
+ * eqn:winvcomp, or by plain CG on the Euclidean normal equation.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: km, s, km/s, g/cm^3 (kappa = rho v^2 in GPa). All gathers are
+ * row-major [nt][n] float64 arrays in DEVICE memory (time-major: sample n of
+ * every trace is contiguous). The caller owns every buffer it passes and keeps
+ * it alive until the call's work on `stream` has finished; the library owns
+ * its internal wavefields, slabs and Krylov vectors (allocated by
+ * ssx_set_geometry / ssx_set_velocity_model, freed by ssx_destroy).
+ * Every call is enqueued on the caller's stream (ordered after the caller's
+ * prior work on it, and the caller's later work is ordered after it); calls
+ * that return host results (ssx_solve_source_subproblem) synchronise.
+ * No call throws; each returns an ssx_status. The message of the last failure
+ * is available from ssx_last_error. A context is not thread-safe.
+ *
+ * Discretisation (section "Synthetic models and simulation"): staggered grid,
+ * order 2 in time and 2k in space, fields FP32 on the device; sampling by
+ * linear interpolation in depth, injection by its adjoint; an absorbing
+ * sponge of n_sponge points padded outside the physical grid. The discrete
+ * transpose is exact (Appendix A; dot-product test to FP32 rounding).
+ */
+#ifndef SSX_H
+#define SSX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssx_ctx ssx_ctx;
+
+typedef enum {
+    SSX_OK = 0,
+    SSX_ERR_ARG = 1,            /* invalid argument or call order        */
+    SSX_ERR_CUDA = 2,           /* a CUDA runtime call failed            */
+    SSX_ERR_CFL = 3,            /* time step violates the CFL bound      */
+    SSX_ERR_OOM = 4,            /* device allocation failed              */
+    SSX_ERR_BREAKDOWN = 5,      /* <p,q> <= 0 or <g,r> <= 0 in Algorithm 1 */
+    SSX_ERR_NONFINITE = 6,      /* a Krylov scalar became NaN/Inf        */
+    SSX_ERR_NOT_CONVERGED = 7   /* maxit reached above rtol (h is valid) */
+} ssx_status;
+
+/* Solver modes of ssx_solve_source_subproblem / ssx_normal_apply. */
+enum {
+    SSX_MODE_PCG = 0,   /* the paper's method: weighted normal equation
+                           (eqn:normpart) + preconditioner (eqn:defprecond) */
+    SSX_MODE_CG = 1     /* plain CG, W_m = W_d = I, M = I (the paper's
+                           comparison in "Preconditioned CG iteration")     */
+};
+
+/* Weight operators of ssx_weight_apply. */
+enum {
+    SSX_W_D = 0,        /* W~_d at the receiver line (eqn:wdef)                  */
+    SSX_W_M = 1,        /* W~_m on the source line (wcomp, prefactor -1)         */
+    SSX_W_M_INV = 2     /* W~_m^{-1} = sym Lambda~ on the source line (eqn:winvcomp) */
+};
+
+typedef struct {
+    int nx, nz;          /* physical grid points (x, z), each >= 8             */
+    double h;            /* grid step, km (same in x and z)                    */
+    double dt;           /* time step, s                                       */
+    int nt;              /* time steps = samples per trace                     */
+    int space_order;     /* 2k in {2, 4, 6, 8}                                 */
+    int n_sponge;        /* absorbing points padded on every side, >= 0        */
+} ssx_grid_desc;
+
+typedef struct {
+    double z_s;          /* extended-source line depth, km                     */
+    int ix_line0;        /* first physical column of the source line           */
+    int n_line;          /* source-line points (columns ix_line0 ..)           */
+    double z_r;          /* receiver line depth, km (!= z_s)                   */
+    int ix_rec0;         /* first physical column of the receivers             */
+    int n_rec;           /* receivers                                          */
+    double x_s;          /* physical source position for A (eqn:penop), km     */
+    double dz_datum;     /* thin-slab datum distance, km (paper: 0.1)          */
+} ssx_geom_desc;
+
+typedef struct {
+    long long kernel_launches;   /* kernels enqueued by this context (graph nodes counted) */
+    long long point_updates;     /* grid-point steps of all sweeps (one v + p update each) */
+    long long sweeps;            /* forward + adjoint sweeps                               */
+    double sweep_ms;             /* event-timed device time of the sweeps (timing mode)    */
+    long long timed_steps;       /* step-kernel launches inside timed sweeps               */
+    double timed_point_updates;  /* grid-point steps inside timed sweeps                   */
+} ssx_stats;
+
+/* Version string of the library. */
+const char *ssx_version(void);
+
+/* Create a context for one grid. `stream` is a cudaStream_t (NULL = legacy
+ * default stream). Returns SSX_ERR_ARG for out-of-range descriptors. */
+int ssx_create(ssx_ctx **out, const ssx_grid_desc *grid, void *stream);
+
+/* Free the context and every device buffer it owns (synchronises). */
+int ssx_destroy(ssx_ctx *ctx);
+
+/* Message of the last failing call on ctx ("" if none). Owned by ctx. */
+const char *ssx_last_error(const ssx_ctx *ctx);
+
+/* Set the medium: v_dev is the physical velocity v[nz][nx] (km/s, float32,
+ * device, row-major), rho the constant density (g/cm^3). kappa = rho v^2
+ * (section "Synthetic models and simulation", constant density as in the
+ * paper's models). Checks the CFL bound v_max dt/h * sqrt(2) sum|c_m| < 1
+ * (SSX_ERR_CFL). */
+int ssx_set_velocity_model(ssx_ctx *ctx, const float *v_dev, double rho);
+
+/* Set the acquisition: the source line z = z_s and receiver line z = z_r
+ * (eqn:fwd's P_s, P_r), the penalty centre x_s (eqn:penop) and the thin-slab
+ * datum distance (eqn:lamnear). Allocates the two thin slabs and the Krylov
+ * vectors. Lines must lie at least k + 1 rows inside the padded grid. */
+int ssx_set_geometry(ssx_ctx *ctx, const ssx_geom_desc *geom);
+
+/* d = S h: pressure-source gather h [nt][n_line] on z_s -> pressure gather
+ * d [nt][n_rec] on z_r (eqn:sdef; one forward sweep from rest). */
+int ssx_forward(ssx_ctx *ctx, const double *h_dev, double *d_dev);
+
+/* h = S^T d: exact discrete transpose of ssx_forward (eqn:sadj1, Appendix A;
+ * one reverse-time sweep). */
+int ssx_adjoint(ssx_ctx *ctx, const double *d_dev, double *h_dev);
+
+/* out = W in for which in {SSX_W_D, SSX_W_M, SSX_W_M_INV} (eqn:winvcomp,
+ * wcomp, eqn:wdef): one forward and one adjoint sweep on the thin slab.
+ * Gathers are [nt][n_rec] for SSX_W_D, [nt][n_line] otherwise. */
+int ssx_weight_apply(ssx_ctx *ctx, int which, const double *in_dev, double *out_dev);
+
+/* g = M^{-1} r = D W~_m^{-1} D r, D = (I + alpha A^T A)^{-1/2}
+ * (eqn:defprecond). alpha >= 0 multiplies ||A h||^2. */
+int ssx_precond_apply(ssx_ctx *ctx, double alpha, const double *r_dev, double *g_dev);
+
+/* q = N p: SSX_MODE_PCG: S^T W~_d S p + alpha A^T W~_m A p (eqn:normpart);
+ * SSX_MODE_CG: S^T S p + alpha A^T A p. */
+int ssx_normal_apply(ssx_ctx *ctx, int mode, double alpha, const double *p_dev, double *q_dev);
+
+/* Solve the source subproblem by Algorithm 1 from h_0 = 0 with
+ * r_0 = S^* d (S^T W~_d d for SSX_MODE_PCG, S^T d for SSX_MODE_CG).
+ * Stops when ||r_k||_2 <= rtol ||r_0||_2 or after maxit updates of h.
+ * d_dev [nt][n_rec] in; h_out_dev [nt][n_line] out (device).
+ * resid_hist_host (host, maxit + 1 doubles, may be NULL) receives ||r_k||_2;
+ * iters_out (host, may be NULL) the number of updates made. Krylov vectors,
+ * scalars and reductions are float64 on the device; one 16-byte device-to-host
+ * read per iteration decides the stop. Returns SSX_ERR_NOT_CONVERGED if maxit
+ * was reached above rtol (h_out is still the last iterate), SSX_ERR_BREAKDOWN
+ * if <p_k,q_k> <= 0 or <g_k,r_k> <= 0 (h_out holds the last good iterate). */
+int ssx_solve_source_subproblem(ssx_ctx *ctx, const double *d_dev, double alpha,
+                                int maxit, double rtol, int mode, double *h_out_dev,
+                                double *resid_hist_host, int *iters_out);
+
+/* d = pressure gather on z_r of a point pressure source w(t) delta(x - x_d)
+ * delta(z - z_d) (fixture of the section "Creating downgoing fields").
+ * wavelet_dev: nt float64 samples (device), sample n integrated over the
+ * pressure update n -> n+1. x_d must fall on a grid column. */
+int ssx_point_source_data(ssx_ctx *ctx, double x_d, double z_d,
+                          const double *wavelet_dev, double *d_dev);
+
+/* Timing mode: when on, every sweep is bracketed by CUDA events on the
+ * launching stream; ssx_get_stats then reports their summed device time. */
+int ssx_set_timing(ssx_ctx *ctx, int on);
+
+/* Counters since creation or the last reset (synchronises when timing). */
+int ssx_get_stats(ssx_ctx *ctx, ssx_stats *out);
+int ssx_reset_stats(ssx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSX_H */

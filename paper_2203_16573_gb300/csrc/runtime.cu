@@ -1,0 +1,845 @@
+// runtime.cu -- host runtime behind include/ssx.h: context, device grids,
+// the operators of the source subproblem built from stencil sweeps, the
+// Algorithm 1 driver and the C ABI entry points.
+//
+// Operators (W. W. Symes, arXiv 2203.16573):
+//   S      = Pi_0 S_{z_s,z_r} Pi_0^T              eqn:sdef (full-grid sweep)
+//   S^T                                            eqn:sadj1 (reverse sweep)
+//   W~_m^{-1} = -4 Pi_1 S^T J S Pi_1^T on the z_s slab   eqn:winvcomp, eqn:lamnear
+//   W~_d      = same construction at z_r               eqn:wdef
+//   W~_m      = -1 Pi_0 S^T J S Pi_0^T on the z_s slab  wcomp (prefactor from
+//               eqn:snull2mod with the second line of eqn:approxinv)
+//   J = Pi_0^T Pi_1 + Pi_1^T Pi_0 (exchange of the two trace components)
+//   N = S^T W~_d S + alpha A^T W~_m A               eqn:normpart, eqn:sadjwt
+//   M^{-1} = D W~_m^{-1} D, D = (I + alpha A^T A)^{-1/2}   eqn:defprecond
+// The thin-slab data sit dz further along the direction from the source line
+// to the receiver line; the printed prefactors hold when that direction is
+// towards smaller z (the geometry of the paper's examples) and change sign in
+// the mirrored geometry so that the weights stay positive.
+//
+// Each sweep (memsets + nt step kernels) is captured once into a CUDA graph
+// per (grid, buffers) and replayed; all operators run on the context's own
+// non-blocking stream, ordered against the caller's stream by events.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ssx.h"
+#include "ssx_internal.cuh"
+
+using namespace ssx;
+
+namespace {
+
+// staggered first-derivative weights of order 2k (Taylor values)
+const float kWeights[5][kMaxR] = {
+    {0.f, 0.f, 0.f, 0.f},
+    {1.0f, 0.f, 0.f, 0.f},
+    {9.0f / 8.0f, -1.0f / 24.0f, 0.f, 0.f},
+    {75.0f / 64.0f, -25.0f / 384.0f, 3.0f / 640.0f, 0.f},
+    {1225.0f / 1024.0f, -245.0f / 3072.0f, 49.0f / 5120.0f, -5.0f / 7168.0f},
+};
+const double kWeightsAbsSum[5] = {0.0, 1.0, 9.0 / 8 + 1.0 / 24,
+                                  75.0 / 64 + 25.0 / 384 + 3.0 / 640,
+                                  1225.0 / 1024 + 245.0 / 3072 + 49.0 / 5120 + 5.0 / 7168};
+
+struct DGrid {
+    FieldLayout L{};
+    int nx = 0, nz = 0;       // physical points of this grid
+    int row0 = 0;             // model row of this grid's physical row 0
+    double z_origin = 0.0;    // depth of physical row 0, km
+    float *mem = nullptr;     // kap | buffer 0 (p vx vz) | buffer 1 (p vx vz)
+    float *tab = nullptr;     // sponge tables: sxi sxh (NX each) szi szh (NZ each)
+    float *kap = nullptr;
+    float *f[2][3] = {};      // origin-offset field pointers
+    GridArgs args{};
+    bool ready = false;
+};
+
+struct EvPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    long long steps = 0;
+    double points = 0.0;
+};
+
+struct Slab {
+    DGrid g;
+    Line plane{}, datum{};         // lines in slab coordinates
+    double z0 = 0, zd = 0;
+    int ix0 = 0, n = 0;
+    double *tp = nullptr, *tv = nullptr;   // datum traces [nt][n]
+};
+
+}  // namespace
+
+struct ssx_ctx {
+    ssx_grid_desc gd{};
+    int R = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::string err;
+
+    float *vel = nullptr;      // physical model copy [nz][nx]
+    float *vmax_dev = nullptr;
+    double rho = 1.0, v_max = 0.0;
+    bool have_model = false, have_geom = false;
+
+    DGrid full;
+    ssx_geom_desc geom{};
+    Line src{}, rec{};
+    double sgn = 1.0;          // +1 in the paper's examples' geometry
+    Slab ss, sr;               // z_s slab (W~_m, W~_m^{-1}), z_r slab (W~_d)
+
+    // gathers: line-shaped [nt][n_line], receiver-shaped [nt][n_rec]
+    double *gbuf = nullptr;
+    double *h = nullptr, *r = nullptr, *g = nullptr, *p = nullptr, *q = nullptr;
+    double *tl1 = nullptr, *tl2 = nullptr, *tr1 = nullptr, *tr2 = nullptr;
+    double *dist = nullptr, *dist2 = nullptr, *D = nullptr;   // [n_line]
+    double D_alpha = -1.0;
+    double *sc = nullptr, *partials = nullptr;                // device scalars
+    double *sc_host = nullptr;                                // pinned
+    std::vector<double> hostD;
+
+    bool use_graphs = true;
+    std::unordered_map<std::string, cudaGraphExec_t> graphs;
+    std::unordered_map<std::string, long long> graph_nodes;
+
+    bool timing = false;
+    std::vector<EvPair> evs;
+    size_t ev_used = 0;
+    ssx_stats st{};
+};
+
+namespace {
+
+int fail(ssx_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? SSX_ERR_OOM : SSX_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != SSX_OK) return rc_; \
+    } while (0)
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------- grids --
+int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) {
+    const int nsp = c->gd.n_sponge;
+    G.nx = nx;
+    G.nz = nz;
+    G.row0 = row0;
+    G.z_origin = z_origin;
+    FieldLayout &L = G.L;
+    L.NX = nx + 2 * nsp;
+    L.NZ = nz + 2 * nsp;
+    L.pitch = round_up(round_up(L.NX, TILE_X_MAX) + 2 * GX, 32);
+    L.rows = round_up(L.NZ, TILE_Z_MAX) + 2 * GZ;
+    const size_t E = L.elems();
+    if (G.mem) cudaFree(G.mem);
+    if (G.tab) cudaFree(G.tab);
+    G.mem = nullptr;
+    G.tab = nullptr;
+    CK(cudaMalloc(&G.mem, 7 * E * sizeof(float)));
+    CK(cudaMalloc(&G.tab, 2 * (size_t)(L.NX + L.NZ) * sizeof(float)));
+    CK(cudaMemsetAsync(G.mem, 0, 7 * E * sizeof(float), c->s));
+    G.kap = G.mem + L.origin();
+    for (int b = 0; b < 2; b++)
+        for (int f = 0; f < 3; f++) G.f[b][f] = G.mem + (1 + 3 * b + f) * E + L.origin();
+    GridArgs &a = G.args;
+    a.NX = L.NX;
+    a.NZ = L.NZ;
+    a.pitch = L.pitch;
+    a.kap = G.kap;
+    a.sxi = G.tab;
+    a.sxh = G.tab + L.NX;
+    a.szi = G.tab + 2 * L.NX;
+    a.szh = G.tab + 2 * L.NX + L.NZ;
+    for (int m = 0; m < kMaxR; m++) a.c[m] = kWeights[c->R][m];
+    G.ready = false;
+    return SSX_OK;
+}
+
+void grid_free(DGrid &G) {
+    if (G.mem) cudaFree(G.mem);
+    if (G.tab) cudaFree(G.tab);
+    G.mem = nullptr;
+    G.tab = nullptr;
+}
+
+// kappa dt/h field and sponge tables from the current model
+int grid_fill(ssx_ctx *c, DGrid &G) {
+    const ssx_grid_desc &d = c->gd;
+    const int nsp = d.n_sponge;
+    CK(launch_fill_kappa(G.kap, G.L, c->vel, d.nx, d.nz, nsp, G.row0, c->rho, d.dt / d.h, c->s));
+    const double smax = nsp > 0 ? 3.0 * c->v_max * std::log(1000.0) / (2.0 * nsp * d.h) : 0.0;
+    CK(launch_sponge_table(G.tab, G.tab + G.L.NX, G.L.NX, G.nx, nsp, smax * d.dt * 0.5, c->s));
+    CK(launch_sponge_table(G.tab + 2 * G.L.NX, G.tab + 2 * G.L.NX + G.L.NZ, G.L.NZ, G.nz, nsp,
+                           smax * d.dt * 0.5, c->s));
+    G.args.cv = (float)(d.dt / (c->rho * d.h));
+    G.ready = true;
+    return SSX_OK;
+}
+
+// linear-interpolation weights at fractional row coordinate zeta
+void row_weights(double zeta, int *k, float *w0, float *w1) {
+    const int kk = (int)std::floor(zeta + 1e-6);
+    double f = zeta - kk;
+    if (f < 1e-6) f = 0.0;
+    *k = kk;
+    *w0 = (float)(1.0 - f);
+    *w1 = (float)f;
+}
+
+int make_line(ssx_ctx *c, const DGrid &G, double z, int ix0, int n, double scale, Line *out) {
+    const int nsp = c->gd.n_sponge;
+    const double zeta = (z - G.z_origin) / c->gd.h + nsp;
+    Line L{};
+    row_weights(zeta, &L.kp, &L.wp0, &L.wp1);
+    row_weights(zeta - 0.5, &L.kv, &L.wv0, &L.wv1);
+    if (!(L.kp >= 0 && L.kp + 1 < G.L.NZ && L.kv >= 0 && L.kv + 1 < G.L.NZ - 1))
+        return fail(c, SSX_ERR_ARG, "line depth outside the grid");
+    if (ix0 < 0 || n < 1 || ix0 + n > G.nx)
+        return fail(c, SSX_ERR_ARG, "line columns outside the physical grid");
+    L.i0 = ix0 + nsp;
+    L.n = n;
+    L.scale = (float)scale;
+    *out = L;
+    return SSX_OK;
+}
+
+// ---------------------------------------------------------------- sweeps --
+int run_cached(ssx_ctx *c, const std::string &key, long long nodes, long long steps, double points,
+               const std::function<int(cudaStream_t)> &enqueue) {
+    EvPair *ev = nullptr;
+    if (c->timing) {
+        if (c->ev_used == c->evs.size()) {
+            EvPair e;
+            CK(cudaEventCreate(&e.a));
+            CK(cudaEventCreate(&e.b));
+            c->evs.push_back(e);
+        }
+        ev = &c->evs[c->ev_used++];
+        ev->steps = steps;
+        ev->points = points;
+        CK(cudaEventRecord(ev->a, c->s));
+    }
+    if (c->use_graphs) {
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue(c->s);
+            cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
+            if (rc != SSX_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            CK(ec);
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ei);
+            it = c->graphs.emplace(key, exec).first;
+            c->graph_nodes[key] = nodes;
+        }
+        CK(cudaGraphLaunch(it->second, c->s));
+    } else {
+        TRY(enqueue(c->s));
+    }
+    if (ev) CK(cudaEventRecord(ev->b, c->s));
+    c->st.kernel_launches += nodes;
+    c->st.point_updates += (long long)points;
+    c->st.sweeps += 1;
+    return SSX_OK;
+}
+
+std::string ptr_key(const char *tag, const void *a, const void *b, const void *d, const void *e) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s:%p:%p:%p:%p", tag, a, b, d, e);
+    return buf;
+}
+
+// forward sweep from rest: sources on `src` -> traces on `rec`
+int sim_fwd(ssx_ctx *c, DGrid &G, const Line &src, const double *hs, const double *fs,
+            const Line &rec, double *outp, double *outv, bool cache = true) {
+    if (!G.ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
+    const int nt = c->gd.nt, R = c->R;
+    auto enqueue = [&, nt, R](cudaStream_t s) -> int {
+        const size_t E = G.L.elems();
+        if (outp) CK(cudaMemsetAsync(outp, 0, (size_t)nt * rec.n * sizeof(double), s));
+        if (outv) CK(cudaMemsetAsync(outv, 0, (size_t)nt * rec.n * sizeof(double), s));
+        CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+        FwdArgs a{};
+        a.g = G.args;
+        a.src = src;
+        a.hsrc = hs;
+        a.fsrc = fs;
+        a.rec = rec;
+        a.outp = outp;
+        a.outv = outv;
+        for (int n = 0; n < nt; n++) {
+            const int bi = n & 1, bo = bi ^ 1;
+            a.p_in = G.f[bi][0];
+            a.vx_in = G.f[bi][1];
+            a.vz_in = G.f[bi][2];
+            a.p_out = G.f[bo][0];
+            a.vx_out = G.f[bo][1];
+            a.vz_out = G.f[bo][2];
+            a.n = n;
+            CK(launch_fwd_step(a, R, s));
+        }
+        return SSX_OK;
+    };
+    const double pts = (double)G.L.NX * G.L.NZ * nt;
+    if (!cache) {
+        TRY(enqueue(c->s));
+        c->st.kernel_launches += nt;
+        c->st.point_updates += (long long)pts;
+        c->st.sweeps += 1;
+        return SSX_OK;
+    }
+    char tag[64];
+    snprintf(tag, sizeof tag, "fwd%p:%d:%d", (void *)&G, src.kp, rec.kp);
+    return run_cached(c, ptr_key(tag, hs, fs, outp, outv), nt, nt, pts, enqueue);
+}
+
+// exact transpose of sim_fwd: adjoint data on `rec` -> adjoint sources on `src`
+int sim_adj(ssx_ctx *c, DGrid &G, const Line &src, double *hb, double *fb, const Line &rec,
+            const double *yp, const double *yv) {
+    if (!G.ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
+    const int nt = c->gd.nt, R = c->R;
+    auto enqueue = [&, nt, R](cudaStream_t s) -> int {
+        const size_t E = G.L.elems();
+        if (hb) CK(cudaMemsetAsync(hb, 0, (size_t)nt * src.n * sizeof(double), s));
+        if (fb) CK(cudaMemsetAsync(fb, 0, (size_t)nt * src.n * sizeof(double), s));
+        CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+        AdjArgs a{};
+        a.g = G.args;
+        a.src = src;
+        a.hbar = hb;
+        a.fbar = fb;
+        a.rec = rec;
+        a.yp = yp;
+        a.yv = yv;
+        a.p_in = G.f[0][0];
+        a.vx_in = G.f[0][1];
+        a.vz_in = G.f[0][2];
+        CK(launch_adj_init(a, nt, s));
+        for (int n = nt - 1, t = 0; n >= 0; n--, t++) {
+            const int bi = t & 1, bo = bi ^ 1;
+            a.p_in = G.f[bi][0];
+            a.vx_in = G.f[bi][1];
+            a.vz_in = G.f[bi][2];
+            a.p_out = G.f[bo][0];
+            a.vx_out = G.f[bo][1];
+            a.vz_out = G.f[bo][2];
+            a.n = n;
+            CK(launch_adj_step(a, R, s));
+        }
+        return SSX_OK;
+    };
+    char tag[64];
+    snprintf(tag, sizeof tag, "adj%p:%d:%d:%g", (void *)&G, src.kp, rec.kp, (double)src.scale);
+    return run_cached(c, ptr_key(tag, hb, fb, yp, yv), nt + 1, nt, (double)G.L.NX * G.L.NZ * nt,
+                      enqueue);
+}
+
+// ------------------------------------------------------------- operators --
+int op_S(ssx_ctx *c, const double *in, double *out) {
+    return sim_fwd(c, c->full, c->src, in, nullptr, c->rec, out, nullptr);
+}
+int op_ST(ssx_ctx *c, const double *in, double *out) {
+    return sim_adj(c, c->full, c->src, out, nullptr, c->rec, in, nullptr);
+}
+// -4 Pi_1 S^T J S Pi_1^T on a slab (eqn:winvcomp)
+int op_sym_lambda(ssx_ctx *c, Slab &sl, const double *in, double *out) {
+    TRY(sim_fwd(c, sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv));
+    Line pl = sl.plane;
+    pl.scale = (float)(-4.0 * c->sgn);
+    return sim_adj(c, sl.g, pl, nullptr, out, sl.datum, sl.tv, sl.tp);
+}
+// -Pi_0 S^T J S Pi_0^T on the z_s slab (wcomp)
+int op_Wm(ssx_ctx *c, const double *in, double *out) {
+    Slab &sl = c->ss;
+    TRY(sim_fwd(c, sl.g, sl.plane, in, nullptr, sl.datum, sl.tp, sl.tv));
+    Line pl = sl.plane;
+    pl.scale = (float)(-1.0 * c->sgn);
+    return sim_adj(c, sl.g, pl, out, nullptr, sl.datum, sl.tv, sl.tp);
+}
+int op_W(ssx_ctx *c, int which, const double *in, double *out) {
+    switch (which) {
+        case SSX_W_D: return op_sym_lambda(c, c->sr, in, out);
+        case SSX_W_M: return op_Wm(c, in, out);
+        case SSX_W_M_INV: return op_sym_lambda(c, c->ss, in, out);
+        default: return fail(c, SSX_ERR_ARG, "unknown weight operator");
+    }
+}
+
+int set_D(ssx_ctx *c, double alpha) {
+    if (c->D_alpha == alpha) return SSX_OK;
+    const int n = c->geom.n_line;
+    c->hostD.resize(n);
+    for (int j = 0; j < n; j++) {
+        const double x = (c->geom.ix_line0 + j) * c->gd.h - c->geom.x_s;
+        c->hostD[j] = 1.0 / std::sqrt(1.0 + alpha * x * x);
+    }
+    CK(cudaMemcpyAsync(c->D, c->hostD.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    c->D_alpha = alpha;
+    return SSX_OK;
+}
+
+// g = D W~_m^{-1} D r (eqn:defprecond); identity for plain CG
+int op_Minv(ssx_ctx *c, int mode, double alpha, const double *r, double *g) {
+    const int nt = c->gd.nt, nl = c->geom.n_line;
+    if (mode == SSX_MODE_CG) {
+        CK(cudaMemcpyAsync(g, r, (size_t)nt * nl * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    }
+    TRY(set_D(c, alpha));
+    CK(launch_colscale(c->tl1, r, c->D, nt, nl, c->s));
+    TRY(op_sym_lambda(c, c->ss, c->tl1, c->tl2));
+    CK(launch_colscale(g, c->tl2, c->D, nt, nl, c->s));
+    c->st.kernel_launches += 2;
+    return SSX_OK;
+}
+
+// q = N p (eqn:normpart) or the Euclidean normal operator
+int op_N(ssx_ctx *c, int mode, double alpha, const double *p, double *q) {
+    const int nt = c->gd.nt, nl = c->geom.n_line;
+    TRY(op_S(c, p, c->tr1));
+    if (mode == SSX_MODE_PCG) {
+        TRY(op_sym_lambda(c, c->sr, c->tr1, c->tr2));
+        TRY(op_ST(c, c->tr2, q));
+        if (alpha != 0.0) {
+            CK(launch_colscale(c->tl1, p, c->dist, nt, nl, c->s));
+            TRY(op_Wm(c, c->tl1, c->tl2));
+            CK(launch_colscale_add(q, c->tl2, c->dist, alpha, nt, nl, c->s));
+            c->st.kernel_launches += 2;
+        }
+    } else {
+        TRY(op_ST(c, c->tr1, q));
+        if (alpha != 0.0) {
+            CK(launch_colscale_add(q, p, c->dist2, alpha, nt, nl, c->s));
+            c->st.kernel_launches += 1;
+        }
+    }
+    return SSX_OK;
+}
+
+int op_rhs(ssx_ctx *c, int mode, const double *d, double *r) {
+    if (mode == SSX_MODE_PCG) {
+        TRY(op_sym_lambda(c, c->sr, d, c->tr2));
+        return op_ST(c, c->tr2, r);
+    }
+    return op_ST(c, d, r);
+}
+
+// ------------------------------------------------------------- plumbing --
+int enter(ssx_ctx *c) {
+    CK(cudaEventRecord(c->ev_in, c->user));
+    CK(cudaStreamWaitEvent(c->s, c->ev_in, 0));
+    return SSX_OK;
+}
+int leave(ssx_ctx *c, int rc) {
+    cudaError_t e1 = cudaEventRecord(c->ev_out, c->s);
+    cudaError_t e2 = cudaStreamWaitEvent(c->user, c->ev_out, 0);
+    if (rc == SSX_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
+        return fail(c, SSX_ERR_CUDA, "stream ordering failed");
+    return rc;
+}
+int ready(ssx_ctx *c) {
+    if (!c) return SSX_ERR_ARG;
+    if (!c->have_model) return fail(c, SSX_ERR_ARG, "ssx_set_velocity_model not called");
+    if (!c->have_geom) return fail(c, SSX_ERR_ARG, "ssx_set_geometry not called");
+    return SSX_OK;
+}
+size_t line_bytes(ssx_ctx *c) { return (size_t)c->gd.nt * c->geom.n_line * sizeof(double); }
+size_t rec_bytes(ssx_ctx *c) { return (size_t)c->gd.nt * c->geom.n_rec * sizeof(double); }
+
+int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
+    const double h = c->gd.h;
+    const int R = c->R;
+    const int kmin = (int)std::floor(std::fmin(z0, zd) / h + 1e-6) - R;
+    const int kmax = (int)std::ceil(std::fmax(z0, zd) / h - 1e-6) + R;
+    TRY(grid_alloc(c, sl.g, c->gd.nx, kmax - kmin + 1, kmin, kmin * h));
+    sl.z0 = z0;
+    sl.zd = zd;
+    sl.ix0 = ix0;
+    sl.n = n;
+    TRY(make_line(c, sl.g, z0, ix0, n, 1.0, &sl.plane));
+    TRY(make_line(c, sl.g, zd, ix0, n, 1.0, &sl.datum));
+    if (sl.tp) cudaFree(sl.tp);
+    sl.tp = nullptr;
+    CK(cudaMalloc(&sl.tp, 2 * (size_t)c->gd.nt * n * sizeof(double)));
+    sl.tv = sl.tp + (size_t)c->gd.nt * n;
+    return SSX_OK;
+}
+
+void drop_graphs(ssx_ctx *c) {
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    c->graph_nodes.clear();
+}
+
+}  // namespace
+
+// ================================================================ C ABI ==
+extern "C" {
+
+const char *ssx_version(void) { return "ssx 0.1 (sm_103a)"; }
+
+const char *ssx_last_error(const ssx_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
+    if (!out || !gd) return SSX_ERR_ARG;
+    *out = nullptr;
+    if (gd->nx < 8 || gd->nz < 8 || gd->nt < 1 || !(gd->h > 0) || !(gd->dt > 0) ||
+        gd->n_sponge < 0 || gd->space_order < 2 || gd->space_order > 8 || gd->space_order % 2)
+        return SSX_ERR_ARG;
+    if ((long long)(gd->nx + 2 * gd->n_sponge) * (gd->nz + 2 * gd->n_sponge) > (1LL << 28))
+        return SSX_ERR_ARG;
+    ssx_ctx *c = new ssx_ctx();
+    c->gd = *gd;
+    c->R = gd->space_order / 2;
+    c->user = (cudaStream_t)stream;
+    int rc = SSX_OK;
+    auto init = [&]() -> int {
+        CK(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+        CK(cudaMalloc(&c->vel, (size_t)gd->nx * gd->nz * sizeof(float)));
+        CK(cudaMalloc(&c->vmax_dev, sizeof(float)));
+        CK(cudaMalloc(&c->sc, SC_COUNT * sizeof(double)));
+        CK(cudaMalloc(&c->partials, kDotBlocks * sizeof(double)));
+        CK(cudaMallocHost(&c->sc_host, SC_COUNT * sizeof(double)));
+        TRY(grid_alloc(c, c->full, gd->nx, gd->nz, 0, 0.0));
+        CK(cudaStreamSynchronize(c->s));
+        return SSX_OK;
+    };
+    rc = init();
+    if (rc != SSX_OK) {
+        ssx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return SSX_OK;
+}
+
+int ssx_destroy(ssx_ctx *c) {
+    if (!c) return SSX_ERR_ARG;
+    if (c->s) cudaStreamSynchronize(c->s);
+    drop_graphs(c);
+    for (auto &e : c->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    grid_free(c->full);
+    grid_free(c->ss.g);
+    grid_free(c->sr.g);
+    if (c->ss.tp) cudaFree(c->ss.tp);
+    if (c->sr.tp) cudaFree(c->sr.tp);
+    if (c->gbuf) cudaFree(c->gbuf);
+    if (c->vel) cudaFree(c->vel);
+    if (c->vmax_dev) cudaFree(c->vmax_dev);
+    if (c->sc) cudaFree(c->sc);
+    if (c->partials) cudaFree(c->partials);
+    if (c->sc_host) cudaFreeHost(c->sc_host);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->s) cudaStreamDestroy(c->s);
+    delete c;
+    return SSX_OK;
+}
+
+int ssx_set_velocity_model(ssx_ctx *c, const float *v_dev, double rho) {
+    if (!c || !v_dev || !(rho > 0)) return c ? fail(c, SSX_ERR_ARG, "bad model arguments") : SSX_ERR_ARG;
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        const size_t n = (size_t)c->gd.nx * c->gd.nz;
+        CK(cudaMemcpyAsync(c->vel, v_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, c->s));
+        CK(launch_vmax(c->vel, (int)n, c->vmax_dev, c->s));
+        float vm = 0.f;
+        CK(cudaMemcpyAsync(&vm, c->vmax_dev, sizeof(float), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        if (!(vm > 0) || !std::isfinite(vm)) return fail(c, SSX_ERR_ARG, "velocity must be positive");
+        const double cfl = vm * c->gd.dt / c->gd.h * std::sqrt(2.0) * kWeightsAbsSum[c->R];
+        if (!(cfl < 1.0)) {
+            char b[128];
+            snprintf(b, sizeof b, "CFL violated: v_max dt/h sqrt(2) sum|c| = %.4f >= 1", cfl);
+            return fail(c, SSX_ERR_CFL, b);
+        }
+        c->v_max = vm;
+        c->rho = rho;
+        TRY(grid_fill(c, c->full));
+        if (c->have_geom) {
+            TRY(grid_fill(c, c->ss.g));
+            TRY(grid_fill(c, c->sr.g));
+        }
+        c->have_model = true;
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_set_geometry(ssx_ctx *c, const ssx_geom_desc *gm) {
+    if (!c || !gm) return c ? fail(c, SSX_ERR_ARG, "null geometry") : SSX_ERR_ARG;
+    const double h = c->gd.h;
+    const double zmax = (c->gd.nz - 1) * h;
+    if (gm->z_s < -1e-9 || gm->z_s > zmax + 1e-9 || gm->z_r < -1e-9 || gm->z_r > zmax + 1e-9)
+        return fail(c, SSX_ERR_ARG, "z_s and z_r must lie in the physical model");
+    if (std::fabs(gm->z_s - gm->z_r) < h) return fail(c, SSX_ERR_ARG, "z_s and z_r must differ by >= h");
+    if (!(gm->dz_datum >= h)) return fail(c, SSX_ERR_ARG, "dz_datum must be >= h");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaStreamSynchronize(c->s));
+        drop_graphs(c);
+        c->have_geom = false;
+        TRY(make_line(c, c->full, gm->z_s, gm->ix_line0, gm->n_line, 1.0, &c->src));
+        TRY(make_line(c, c->full, gm->z_r, gm->ix_rec0, gm->n_rec, 1.0, &c->rec));
+        c->geom = *gm;
+        const double dir = gm->z_r > gm->z_s ? 1.0 : -1.0;
+        c->sgn = -dir;
+        TRY(slab_setup(c, c->ss, gm->z_s, gm->z_s + dir * gm->dz_datum, gm->ix_line0, gm->n_line));
+        TRY(slab_setup(c, c->sr, gm->z_r, gm->z_r + dir * gm->dz_datum, gm->ix_rec0, gm->n_rec));
+        if (c->gbuf) cudaFree(c->gbuf);
+        c->gbuf = nullptr;
+        const size_t nl = (size_t)c->gd.nt * gm->n_line, nr = (size_t)c->gd.nt * gm->n_rec;
+        CK(cudaMalloc(&c->gbuf, (7 * nl + 2 * nr + 3 * (size_t)gm->n_line) * sizeof(double)));
+        double *b = c->gbuf;
+        c->h = b; b += nl;
+        c->r = b; b += nl;
+        c->g = b; b += nl;
+        c->p = b; b += nl;
+        c->q = b; b += nl;
+        c->tl1 = b; b += nl;
+        c->tl2 = b; b += nl;
+        c->tr1 = b; b += nr;
+        c->tr2 = b; b += nr;
+        c->dist = b; b += gm->n_line;
+        c->dist2 = b; b += gm->n_line;
+        c->D = b;
+        c->D_alpha = -1.0;
+        std::vector<double> dd(2 * (size_t)gm->n_line);
+        for (int j = 0; j < gm->n_line; j++) {
+            const double x = (gm->ix_line0 + j) * h - gm->x_s;
+            dd[j] = std::fabs(x);
+            dd[gm->n_line + j] = x * x;
+        }
+        CK(cudaMemcpyAsync(c->dist, dd.data(), dd.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        if (c->have_model) {
+            TRY(grid_fill(c, c->ss.g));
+            TRY(grid_fill(c, c->sr.g));
+        }
+        CK(cudaStreamSynchronize(c->s));
+        c->have_geom = true;
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_forward(ssx_ctx *c, const double *h_dev, double *d_dev) {
+    TRY(ready(c));
+    if (!h_dev || !d_dev) return fail(c, SSX_ERR_ARG, "null gather");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->tl1, h_dev, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_S(c, c->tl1, c->tr1));
+        CK(cudaMemcpyAsync(d_dev, c->tr1, rec_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_adjoint(ssx_ctx *c, const double *d_dev, double *h_dev) {
+    TRY(ready(c));
+    if (!h_dev || !d_dev) return fail(c, SSX_ERR_ARG, "null gather");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->tr2, d_dev, rec_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_ST(c, c->tr2, c->tl2));
+        CK(cudaMemcpyAsync(h_dev, c->tl2, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_weight_apply(ssx_ctx *c, int which, const double *in, double *out) {
+    TRY(ready(c));
+    if (!in || !out) return fail(c, SSX_ERR_ARG, "null gather");
+    if (which != SSX_W_D && which != SSX_W_M && which != SSX_W_M_INV)
+        return fail(c, SSX_ERR_ARG, "unknown weight operator");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        const bool rec = which == SSX_W_D;
+        double *bi = rec ? c->tr1 : c->tl1;
+        double *bo = rec ? c->tr2 : c->tl2;
+        const size_t bytes = rec ? rec_bytes(c) : line_bytes(c);
+        CK(cudaMemcpyAsync(bi, in, bytes, cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_W(c, which, bi, bo));
+        CK(cudaMemcpyAsync(out, bo, bytes, cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_precond_apply(ssx_ctx *c, double alpha, const double *r, double *g) {
+    TRY(ready(c));
+    if (!r || !g || !(alpha >= 0)) return fail(c, SSX_ERR_ARG, "bad arguments");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->r, r, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_Minv(c, SSX_MODE_PCG, alpha, c->r, c->g));
+        CK(cudaMemcpyAsync(g, c->g, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_normal_apply(ssx_ctx *c, int mode, double alpha, const double *p, double *q) {
+    TRY(ready(c));
+    if (!p || !q || !(alpha >= 0) || (mode != SSX_MODE_PCG && mode != SSX_MODE_CG))
+        return fail(c, SSX_ERR_ARG, "bad arguments");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->p, p, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_N(c, mode, alpha, c->p, c->q));
+        CK(cudaMemcpyAsync(q, c->q, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        return SSX_OK;
+    };
+    return leave(c, body());
+}
+
+int ssx_solve_source_subproblem(ssx_ctx *c, const double *d_dev, double alpha, int maxit,
+                                double rtol, int mode, double *h_out, double *hist, int *iters) {
+    TRY(ready(c));
+    if (!d_dev || !h_out || maxit < 0 || !(alpha >= 0) || !(rtol >= 0) ||
+        (mode != SSX_MODE_PCG && mode != SSX_MODE_CG))
+        return fail(c, SSX_ERR_ARG, "bad arguments");
+    TRY(enter(c));
+    int done = 0;
+    auto body = [&]() -> int {
+        const size_t nl = (size_t)c->gd.nt * c->geom.n_line;
+        double *sc = c->sc, *sh = c->sc_host;
+        cudaStream_t s = c->s;
+        CK(cudaMemcpyAsync(c->tr1, d_dev, rec_bytes(c), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(c->h, 0, line_bytes(c), s));
+        // r_0 = S^* d ; p_0 = g_0 = M^{-1} r_0 ; q_0 = N p_0
+        TRY(op_rhs(c, mode, c->tr1, c->r));
+        TRY(op_Minv(c, mode, alpha, c->r, c->g));
+        CK(cudaMemcpyAsync(c->p, c->g, line_bytes(c), cudaMemcpyDeviceToDevice, s));
+        TRY(op_N(c, mode, alpha, c->p, c->q));
+        CK(launch_dot(c->g, c->r, nl, c->partials, sc + SC_GR, s));
+        CK(launch_dot(c->r, c->r, nl, c->partials, sc + SC_RR, s));
+        c->st.kernel_launches += 4;
+        CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double r0 = std::sqrt(sh[SC_RR]);
+        if (hist) hist[0] = r0;
+        if (!std::isfinite(r0)) return fail(c, SSX_ERR_NONFINITE, "non-finite initial residual");
+        if (r0 == 0.0) return SSX_OK;
+        for (int k = 0; k < maxit; k++) {
+            // alpha_k = <g,r>/<p,q>; h += alpha p; r -= alpha q
+            CK(launch_dot(c->p, c->q, nl, c->partials, sc + SC_PQ, s));
+            CK(launch_pcg_alpha(sc, s));
+            CK(launch_pcg_update(c->h, c->r, c->p, c->q, nl, sc, c->partials, s));
+            c->st.kernel_launches += 5;
+            CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (sh[SC_FLAG] != 0.0) {
+                if (!std::isfinite(sh[SC_PQ]) || !std::isfinite(sh[SC_GR]))
+                    return fail(c, SSX_ERR_NONFINITE, "non-finite Krylov scalar");
+                char b[160];
+                snprintf(b, sizeof b, "PCG breakdown at k=%d: <p,q>=%.6e <g,r>=%.6e", k,
+                         sh[SC_PQ], sh[SC_GR]);
+                return fail(c, SSX_ERR_BREAKDOWN, b);
+            }
+            const double rn = std::sqrt(sh[SC_RR]);
+            done = k + 1;
+            if (hist) hist[k + 1] = rn;
+            if (!std::isfinite(rn)) return fail(c, SSX_ERR_NONFINITE, "non-finite residual");
+            if (rn <= rtol * r0) return SSX_OK;
+            if (k == maxit - 1) break;
+            // g = M^{-1} r; beta = <g,r>_new/<g,r>; p = g + beta p; q = N p
+            TRY(op_Minv(c, mode, alpha, c->r, c->g));
+            CK(launch_dot(c->g, c->r, nl, c->partials, sc + SC_GRNEW, s));
+            CK(launch_pcg_beta(sc, s));
+            CK(launch_xpby(c->p, c->g, nl, sc, s));
+            c->st.kernel_launches += 4;
+            TRY(op_N(c, mode, alpha, c->p, c->q));
+        }
+        return fail(c, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
+    };
+    int rc = body();
+    if (iters) *iters = done;
+    if (rc == SSX_OK || rc == SSX_ERR_NOT_CONVERGED || rc == SSX_ERR_BREAKDOWN) {
+        cudaError_t e = cudaMemcpyAsync(h_out, c->h, line_bytes(c), cudaMemcpyDeviceToDevice, c->s);
+        if (e != cudaSuccess && rc == SSX_OK) rc = fail(c, SSX_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return leave(c, rc);
+}
+
+int ssx_point_source_data(ssx_ctx *c, double x_d, double z_d, const double *w, double *d_dev) {
+    if (!c) return SSX_ERR_ARG;
+    if (!c->have_model || !c->have_geom) return ready(c);
+    if (!w || !d_dev) return fail(c, SSX_ERR_ARG, "null buffer");
+    const double h = c->gd.h;
+    const int ix = (int)std::lround(x_d / h);
+    if (std::fabs(ix * h - x_d) > 1e-9) return fail(c, SSX_ERR_ARG, "x_d must fall on a grid column");
+    Line pt{};
+    TRY(make_line(c, c->full, z_d, ix, 1, 1.0 / h, &pt));
+    TRY(enter(c));
+    int rc = sim_fwd(c, c->full, pt, w, nullptr, c->rec, d_dev, nullptr, false);
+    return leave(c, rc);
+}
+
+int ssx_set_timing(ssx_ctx *c, int on) {
+    if (!c) return SSX_ERR_ARG;
+    c->timing = on != 0;
+    return SSX_OK;
+}
+
+int ssx_get_stats(ssx_ctx *c, ssx_stats *out) {
+    if (!c || !out) return SSX_ERR_ARG;
+    if (c->ev_used) {
+        CK(cudaStreamSynchronize(c->s));
+        for (size_t i = 0; i < c->ev_used; i++) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->evs[i].a, c->evs[i].b));
+            c->st.sweep_ms += ms;
+            c->st.timed_steps += c->evs[i].steps;
+            c->st.timed_point_updates += c->evs[i].points;
+        }
+        c->ev_used = 0;
+    }
+    *out = c->st;
+    return SSX_OK;
+}
+
+int ssx_reset_stats(ssx_ctx *c) {
+    if (!c) return SSX_ERR_ARG;
+    if (c->ev_used) CK(cudaStreamSynchronize(c->s));
+    c->ev_used = 0;
+    c->st = ssx_stats{};
+    return SSX_OK;
+}
+
+}  // extern "C"

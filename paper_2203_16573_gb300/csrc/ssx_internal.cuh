@@ -1,0 +1,107 @@
+// ssx_internal.cuh -- device-side data layout and kernel interfaces shared by
+// the CUDA translation units of libssx (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssx {
+
+// Field storage. A field of the padded grid (NZ x NX points) lives in a
+// zero apron: GX columns left and right, GZ rows above and below, with the
+// row pitch a multiple of 32 floats and the whole allocation rounded up to
+// whole kernel tiles, so that a tile plus its 2k halo never reads outside the
+// allocation and never needs a bounds test. The apron is never written, so it
+// reads as the zero extension the difference operators assume.
+constexpr int GX = 32;          // x apron (floats); keeps row starts 128-B aligned
+constexpr int GZ = 8;           // z apron (rows) >= 2k for k <= 4
+constexpr int TILE_X_MAX = 128;
+constexpr int TILE_Z_MAX = 32;
+constexpr int kMaxR = 4;        // order 8
+
+struct FieldLayout {
+    int NX, NZ;        // padded grid points
+    int pitch;         // floats per storage row
+    int rows;          // storage rows
+    size_t elems() const { return (size_t)pitch * rows; }
+    size_t origin() const { return (size_t)GZ * pitch + GX; }   // offset of (k=0, i=0)
+};
+
+// An injection / sampling line: columns i0 .. i0+n-1 of the padded grid at one
+// depth; pressure rows kp (weight wp0) and kp+1 (wp1), v_z half rows kv (wv0)
+// and kv+1 (wv1) -- linear interpolation in z; `scale` multiplies injected
+// values (1 for a line density, 1/h for a point source) and, in the adjoint
+// sweep, the read-out transposed injection.
+struct Line {
+    int i0, n;
+    int kp;
+    float wp0, wp1;
+    int kv;
+    float wv0, wv1;
+    float scale;
+};
+
+// Per-grid constant inputs of a step.
+struct GridArgs {
+    int NX, NZ, pitch;
+    const float *kap;       // kappa dt / h at p points (origin-offset pointer)
+    const float *sxi, *sxh; // sigma dt/2 at x = i h and (i+1/2) h, [NX]
+    const float *szi, *szh; // sigma dt/2 at z = k h and (k+1/2) h, [NZ]
+    float cv;               // dt / (rho h)
+    float c[kMaxR];         // staggered weights c_1..c_k
+};
+
+struct FwdArgs {
+    GridArgs g;
+    const float *p_in, *vx_in, *vz_in;  // origin-offset pointers
+    float *p_out, *vx_out, *vz_out;
+    Line src;
+    const double *hsrc;   // pressure source [nt][src.n] or null
+    const double *fsrc;   // velocity source [nt][src.n] or null
+    Line rec;
+    double *outp;         // P p   [nt][rec.n] or null (zeroed before the sweep)
+    double *outv;         // P v_z [nt][rec.n] or null
+    int n;                // step index
+};
+
+struct AdjArgs {
+    GridArgs g;
+    const float *p_in, *vx_in, *vz_in;  // adjoint state entering reverse step n
+    float *p_out, *vx_out, *vz_out;
+    Line src;
+    double *hbar;         // adjoint of the pressure injection [nt][src.n] or null
+    double *fbar;         // adjoint of the velocity injection or null
+    Line rec;
+    const double *yp;     // adjoint data for P p   [nt][rec.n] or null
+    const double *yv;     // adjoint data for P v_z or null
+    int n;                // step index (reverse sweep: nt-1 .. 0)
+};
+
+// Kernel launchers (stencil.cu). Return cudaGetLastError() of the launch.
+cudaError_t launch_fwd_step(const FwdArgs &a, int R, cudaStream_t s);
+cudaError_t launch_adj_step(const AdjArgs &a, int R, cudaStream_t s);
+cudaError_t launch_adj_init(const AdjArgs &a, int nt, cudaStream_t s);
+cudaError_t launch_fill_kappa(float *kap, const FieldLayout &L, const float *vel, int nx, int nz,
+                              int nsp, int row0, double rho, double dt_over_h, cudaStream_t s);
+cudaError_t launch_sponge_table(float *ti, float *th, int N, int n_phys, int nsp,
+                                double smax_dt_half, cudaStream_t s);
+cudaError_t launch_vmax(const float *v, int n, float *out, cudaStream_t s);
+void tile_shape(int R, int *tx, int *tz);
+
+// FP64 Krylov kernels (krylov.cu).
+constexpr int kDotBlocks = 512;
+cudaError_t launch_dot(const double *a, const double *b, size_t n, double *partials,
+                       double *out, cudaStream_t s);
+cudaError_t launch_pcg_alpha(double *sc, cudaStream_t s);
+cudaError_t launch_pcg_update(double *h, double *r, const double *p, const double *q, size_t n,
+                              double *sc, double *partials, cudaStream_t s);
+cudaError_t launch_pcg_beta(double *sc, cudaStream_t s);
+cudaError_t launch_xpby(double *p, const double *g, size_t n, const double *sc, cudaStream_t s);
+cudaError_t launch_colscale(double *out, const double *in, const double *w, int nt, int nc,
+                            cudaStream_t s);
+cudaError_t launch_colscale_add(double *q, const double *in, const double *w, double alpha,
+                                int nt, int nc, cudaStream_t s);
+
+// Device scalar slots used by the PCG kernels.
+enum { SC_GR = 0, SC_PQ, SC_ALPHA, SC_RR, SC_GRNEW, SC_BETA, SC_FLAG, SC_COUNT };
+
+}  // namespace ssx

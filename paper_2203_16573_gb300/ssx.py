@@ -1,0 +1,236 @@
+"""Thin Python binding of the C ABI in include/ssx.h (ctypes).
+
+Argument marshalling only: every step of the solver runs in libssx's CUDA
+kernels. PyTorch provides device memory and the stream. There is no CPU
+fallback: constructing a Context without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libssx.so")
+
+SSX_OK = 0
+STATUS = {0: "SSX_OK", 1: "SSX_ERR_ARG", 2: "SSX_ERR_CUDA", 3: "SSX_ERR_CFL", 4: "SSX_ERR_OOM",
+          5: "SSX_ERR_BREAKDOWN", 6: "SSX_ERR_NONFINITE", 7: "SSX_ERR_NOT_CONVERGED"}
+MODE_PCG, MODE_CG = 0, 1
+W_D, W_M, W_M_INV = 0, 1, 2
+
+# every symbol the header declares, in declaration order
+EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
+           "ssx_set_velocity_model", "ssx_set_geometry", "ssx_forward", "ssx_adjoint",
+           "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
+           "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
+           "ssx_get_stats", "ssx_reset_stats"]
+
+
+class SSXError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.msg = msg
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nt", ctypes.c_int), ("space_order", ctypes.c_int),
+                ("n_sponge", ctypes.c_int)]
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("z_s", ctypes.c_double), ("ix_line0", ctypes.c_int), ("n_line", ctypes.c_int),
+                ("z_r", ctypes.c_double), ("ix_rec0", ctypes.c_int), ("n_rec", ctypes.c_int),
+                ("x_s", ctypes.c_double), ("dz_datum", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("point_updates", ctypes.c_longlong),
+                ("sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double),
+                ("timed_steps", ctypes.c_longlong), ("timed_point_updates", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libssx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2203_16573_gb300.build`")
+    L = ctypes.CDLL(path)
+    P, vp, i, d = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ssx_version": ([], ctypes.c_char_p),
+        "ssx_create": ([P(vp), P(GridDesc), vp], i),
+        "ssx_destroy": ([vp], i),
+        "ssx_last_error": ([vp], ctypes.c_char_p),
+        "ssx_set_velocity_model": ([vp, vp, d], i),
+        "ssx_set_geometry": ([vp, P(GeomDesc)], i),
+        "ssx_forward": ([vp, vp, vp], i),
+        "ssx_adjoint": ([vp, vp, vp], i),
+        "ssx_weight_apply": ([vp, i, vp, vp], i),
+        "ssx_precond_apply": ([vp, d, vp, vp], i),
+        "ssx_normal_apply": ([vp, i, d, vp, vp], i),
+        "ssx_solve_source_subproblem": ([vp, vp, d, i, d, i, vp, P(d), P(i)], i),
+        "ssx_point_source_data": ([vp, d, d, vp, vp], i),
+        "ssx_set_timing": ([vp, i], i),
+        "ssx_get_stats": ([vp, P(Stats)], i),
+        "ssx_reset_stats": ([vp], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dev_ptr(t: torch.Tensor, shape, dtype=torch.float64, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                        f"got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One grid (and its thin slabs) on the current CUDA device."""
+
+    def __init__(self, nx, nz, h, dt, nt, space_order, n_sponge, stream=None):
+        self._lib = load_library()
+        self.nx, self.nz, self.h, self.dt, self.nt = nx, nz, h, dt, nt
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = torch.cuda.current_stream() if stream is None else stream
+        self.stream = s
+        gd = GridDesc(nx, nz, h, dt, nt, space_order, n_sponge)
+        self._c = ctypes.c_void_p()
+        rc = self._lib.ssx_create(ctypes.byref(self._c), ctypes.byref(gd), ctypes.c_void_p(s.cuda_stream))
+        if rc != SSX_OK:
+            raise SSXError(rc, "ssx_create failed")
+        self.n_line = self.n_rec = None
+
+    @classmethod
+    def from_spec(cls, spec, stream=None):
+        return cls(spec.nx, spec.nz, spec.h, spec.dt, spec.nt, spec.order, spec.n_sponge, stream)
+
+    def _check(self, rc):
+        if rc != SSX_OK:
+            raise SSXError(rc, self._lib.ssx_last_error(self._c).decode())
+        return rc
+
+    def close(self):
+        if self._c:
+            self._lib.ssx_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup ------------------------------------------------------------
+    def set_velocity_model(self, v: torch.Tensor, rho: float):
+        p = _dev_ptr(v, (self.nz, self.nx), torch.float32, "v")
+        self._check(self._lib.ssx_set_velocity_model(self._c, p, float(rho)))
+
+    def set_geometry(self, z_s, ix_line0, n_line, z_r, ix_rec0, n_rec, x_s, dz_datum=0.1):
+        g = GeomDesc(z_s, ix_line0, n_line, z_r, ix_rec0, n_rec, x_s, dz_datum)
+        self._check(self._lib.ssx_set_geometry(self._c, ctypes.byref(g)))
+        self.n_line, self.n_rec = n_line, n_rec
+
+    @classmethod
+    def for_problem(cls, spec, vel, stream=None):
+        """Context with the workload's model and geometry set (vel: numpy or
+        tensor [nz][nx], km/s)."""
+        ctx = cls.from_spec(spec, stream)
+        v = torch.as_tensor(np.asarray(vel), dtype=torch.float32).to(ctx.device).contiguous()
+        ctx.set_velocity_model(v, spec.rho)
+        ctx.set_geometry(spec.z_s, spec.ix_line0, spec.n_line, spec.z_r, spec.ix_rec0,
+                         spec.n_rec, spec.x_s, spec.dz_datum)
+        return ctx
+
+    # -- operators ----------------------------------------------------------
+    def _line(self, t, name):
+        return _dev_ptr(t, (self.nt, self.n_line), name=name)
+
+    def _rec(self, t, name):
+        return _dev_ptr(t, (self.nt, self.n_rec), name=name)
+
+    def _empty(self, n):
+        return torch.empty((self.nt, n), dtype=torch.float64, device=self.device)
+
+    def forward(self, h, out=None):
+        out = self._empty(self.n_rec) if out is None else out
+        self._check(self._lib.ssx_forward(self._c, self._line(h, "h"), self._rec(out, "d")))
+        return out
+
+    def adjoint(self, d, out=None):
+        out = self._empty(self.n_line) if out is None else out
+        self._check(self._lib.ssx_adjoint(self._c, self._rec(d, "d"), self._line(out, "h")))
+        return out
+
+    def weight_apply(self, which, x, out=None):
+        chk = self._rec if which == W_D else self._line
+        out = self._empty(self.n_rec if which == W_D else self.n_line) if out is None else out
+        self._check(self._lib.ssx_weight_apply(self._c, which, chk(x, "in"), chk(out, "out")))
+        return out
+
+    def precond_apply(self, alpha, r, out=None):
+        out = self._empty(self.n_line) if out is None else out
+        self._check(self._lib.ssx_precond_apply(self._c, float(alpha), self._line(r, "r"),
+                                                self._line(out, "g")))
+        return out
+
+    def normal_apply(self, mode, alpha, p, out=None):
+        out = self._empty(self.n_line) if out is None else out
+        self._check(self._lib.ssx_normal_apply(self._c, mode, float(alpha), self._line(p, "p"),
+                                               self._line(out, "q")))
+        return out
+
+    def solve(self, d, alpha, maxit, rtol, mode=MODE_PCG, out=None, allow_not_converged=True):
+        """Algorithm 1. Returns (h, residual history (numpy), iterations, status)."""
+        out = self._empty(self.n_line) if out is None else out
+        hist = (ctypes.c_double * (maxit + 1))()
+        iters = ctypes.c_int(0)
+        rc = self._lib.ssx_solve_source_subproblem(self._c, self._rec(d, "d"), float(alpha),
+                                                   int(maxit), float(rtol), int(mode),
+                                                   self._line(out, "h"), hist, ctypes.byref(iters))
+        if rc != SSX_OK and not (allow_not_converged and rc == 7):
+            self._check(rc)
+        k = iters.value
+        return out, np.array(hist[: k + 1]), k, STATUS[rc]
+
+    def point_source_data(self, x_d, z_d, wavelet, out=None):
+        w = _dev_ptr(wavelet, (self.nt,), name="wavelet")
+        out = self._empty(self.n_rec) if out is None else out
+        self._check(self._lib.ssx_point_source_data(self._c, float(x_d), float(z_d), w,
+                                                    self._rec(out, "d")))
+        return out
+
+    # -- instrumentation ------------------------------------------------------
+    def set_timing(self, on: bool):
+        self._check(self._lib.ssx_set_timing(self._c, 1 if on else 0))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.ssx_get_stats(self._c, ctypes.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(self._lib.ssx_reset_stats(self._c))
+
+
+def version() -> str:
+    return load_library().ssx_version().decode()

@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every symbol include/ssx.h
+declares; the binding rejects bad arguments before any device work. CPU only:
+no call here touches a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "ssx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssx_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_16573_gb300 import build, ssx
+    build.build()
+    return ssx.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2203_16573_gb300 import ssx
+    syms = _header_symbols()
+    assert len(syms) >= 16
+    assert sorted(ssx.EXPORTS) == syms
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_version_string(lib):
+    assert b"sm_103a" in lib.ssx_version()
+
+
+def test_create_rejects_bad_descriptor_without_touching_the_device(lib):
+    from paper_2203_16573_gb300 import ssx
+    out = ctypes.c_void_p()
+    for bad in [ssx.GridDesc(4, 100, 0.01, 1e-3, 10, 4, 5),      # nx too small
+                ssx.GridDesc(100, 100, 0.01, 1e-3, 10, 5, 5),    # odd order
+                ssx.GridDesc(100, 100, 0.01, 1e-3, 10, 10, 5),   # order > 8
+                ssx.GridDesc(100, 100, -0.01, 1e-3, 10, 4, 5),   # h <= 0
+                ssx.GridDesc(100, 100, 0.01, 1e-3, 0, 4, 5),     # nt = 0
+                ssx.GridDesc(100, 100, 0.01, 1e-3, 10, 4, -1)]:  # sponge < 0
+        assert lib.ssx_create(ctypes.byref(out), ctypes.byref(bad), None) == 1
+        assert not out.value
+    assert lib.ssx_create(None, None, None) == 1
+    assert lib.ssx_destroy(None) == 1
+    assert lib.ssx_last_error(None) == b"null context"
+
+
+def test_oracle_shares_no_code_with_the_library():
+    """The oracle and the CUDA path are independent: no file of one includes,
+    imports or loads the other."""
+    csrc = os.path.join(ROOT, "paper_2203_16573_gb300", "csrc")
+    for f in os.listdir(csrc):
+        t = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in t.lower(), f
+    for f in ("ssx.py", "build.py", "__init__.py", "workloads.py"):
+        t = open(os.path.join(ROOT, "paper_2203_16573_gb300", f)).read()
+        assert "import oracle" not in t and "from oracle" not in t, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c")):
+            t = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "import paper_2203_16573_gb300" not in t and "libssx.so" not in t, f

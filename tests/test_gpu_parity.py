@@ -1,0 +1,249 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (the solver's stated bar): traces, gathers and recovered sources
+within 1e-4 relative L2; PCG residual histories within 1e-3 relative per
+iteration. GPU fields are FP32, Krylov vectors and scalars FP64.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_16573_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+HIST_TOL = 1e-3
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def ssx():
+    from paper_2203_16573_gb300 import build, ssx as S
+    build.build()
+    assert torch.cuda.is_available()
+    return S
+
+
+def make(ssx, oracle, spec):
+    vel = W.velocity(spec)
+    return ssx.Context.for_problem(spec, vel), oracle.Problem(spec, vel)
+
+
+def frac_spec(order, nt=300, **kw):
+    """small c2-like case with both lines between grid rows (interpolation)"""
+    return dataclasses.replace(W.small(order=order, nt=nt), z_s=0.5537, z_r=0.0471, **kw)
+
+
+# ------------------------------------------------------------- S and S^T --
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("fractional", [False, True])
+def test_forward_and_adjoint_parity(ssx, oracle, order, fractional):
+    spec = frac_spec(order) if fractional else W.small(order=order, nt=300)
+    ctx, P = make(ssx, oracle, spec)
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 1)
+    d = W.smooth_random_gather(spec.nt, spec.n_rec, 2)
+    assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
+    assert rel(ctx.adjoint(dev(d)), P.ST(d)) <= TOL
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_gpu_dot_product_test(ssx, order):
+    """<S h, d> = <h, S^T d> for the FP32 sweeps (exact transpose up to FP32
+    rounding of the fields)."""
+    spec = frac_spec(order, nt=500)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    h = dev(W.random_gather(spec.nt, spec.n_line, 3))
+    d = dev(W.random_gather(spec.nt, spec.n_rec, 4))
+    a = float((ctx.forward(h) * d).sum())
+    b = float((h * ctx.adjoint(d)).sum())
+    assert abs(a - b) <= 1e-5 * abs(a)
+
+
+def test_point_source_data_parity(ssx, oracle):
+    spec = W.small(order=8, nt=400)
+    ctx, P = make(ssx, oracle, spec)
+    w = W.ricker(spec)
+    d_gpu = ctx.point_source_data(spec.x_d, spec.z_d, dev(w))
+    assert rel(d_gpu, P.point_source_data(w, spec.x_d, spec.z_d)) <= TOL
+
+
+# ---------------------------------------------------------------- weights --
+@pytest.mark.parametrize("which", ["Wd", "Wm", "Wminv"])
+@pytest.mark.parametrize("fractional", [False, True])
+def test_weight_parity(ssx, oracle, which, fractional):
+    spec = frac_spec(8) if fractional else W.small(order=8, nt=300)
+    ctx, P = make(ssx, oracle, spec)
+    code = {"Wd": ssx.W_D, "Wm": ssx.W_M, "Wminv": ssx.W_M_INV}[which]
+    n = spec.n_rec if which == "Wd" else spec.n_line
+    x = W.smooth_random_gather(spec.nt, n, 5)
+    assert rel(ctx.weight_apply(code, dev(x)), getattr(P, which)(x)) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["pcg", "cg"])
+def test_normal_operator_and_preconditioner_parity(ssx, oracle, mode):
+    spec = W.small(order=8, nt=300)
+    ctx, P = make(ssx, oracle, spec)
+    m = ssx.MODE_PCG if mode == "pcg" else ssx.MODE_CG
+    x = W.smooth_random_gather(spec.nt, spec.n_line, 6)
+    assert rel(ctx.normal_apply(m, 0.3, dev(x)), P.N(x, 0.3, mode)) <= TOL
+    assert rel(ctx.normal_apply(m, 0.0, dev(x)), P.N(x, 0.0, mode)) <= TOL
+    if mode == "pcg":
+        assert rel(ctx.precond_apply(0.3, dev(x)), P.Minv(x, 0.3)) <= TOL
+
+
+def test_mirrored_geometry_weights_positive_and_match(ssx, oracle):
+    """Receivers below the source line: datum side and prefactor sign follow."""
+    spec = dataclasses.replace(W.small(order=4, nt=300), z_s=0.08, z_r=0.6)
+    ctx, P = make(ssx, oracle, spec)
+    x = W.smooth_random_gather(spec.nt, spec.n_line, 7)
+    y = ctx.weight_apply(ssx.W_M_INV, dev(x))
+    assert rel(y, P.Wminv(x)) <= TOL
+    assert float((y * dev(x)).sum()) > 0
+
+
+# -------------------------------------------------------------------- PCG --
+def _check_solve(ctx, P, spec, d, mode, maxit, rtol):
+    from paper_2203_16573_gb300 import ssx as S
+    m = S.MODE_PCG if mode == "pcg" else S.MODE_CG
+    h_or, hist_or = oracle_pcg(P, d, spec.alpha, maxit, rtol, mode)
+    h_gpu, hist_gpu, iters, status = ctx.solve(dev(d), spec.alpha, maxit, rtol, m)
+    assert iters == len(hist_or) - 1, (iters, len(hist_or))
+    np.testing.assert_array_less(np.abs(hist_gpu - hist_or) / hist_or, HIST_TOL)
+    assert rel(h_gpu, h_or) <= TOL
+    return h_gpu, hist_gpu, status
+
+
+def oracle_pcg(P, d, alpha, maxit, rtol, mode):
+    from oracle import ssx_oracle
+    return ssx_oracle.pcg(P, d, alpha, maxit, rtol, mode)
+
+
+@pytest.mark.parametrize("mode", ["pcg", "cg"])
+def test_pcg_parity_small(ssx, oracle, mode):
+    spec = W.small(order=8, nt=500)
+    ctx, P = make(ssx, oracle, spec)
+    d = P.point_source_data(W.ricker(spec), spec.x_d, spec.z_d)
+    _check_solve(ctx, P, spec, d, mode, 12, 0.0)
+
+
+def test_config1_solve_parity(ssx, oracle):
+    """Homogeneous 201 x 101, order 4, 1000 steps, 10 Hz Ricker point source
+    on the line, 20 preconditioned CG iterations (rtol 1e-3)."""
+    spec = W.c1()
+    ctx, P = make(ssx, oracle, spec)
+    w = W.ricker(spec)
+    d = P.point_source_data(w, spec.x_d, spec.z_d)
+    assert rel(ctx.point_source_data(spec.x_d, spec.z_d, dev(w)), d) <= TOL
+    _check_solve(ctx, P, spec, d, "pcg", spec.maxit, spec.rtol)
+
+
+def test_config2_full_size_sampled(ssx, oracle):
+    """Full 601 x 301, order 8, 3000-step lens workload at the bench's launch
+    configuration: the data gather and the first residual r_0 = S^T W~_d d
+    against the oracle, plus the dot-product test."""
+    spec = W.c2()
+    ctx, P = make(ssx, oracle, spec)
+    w = W.ricker(spec)
+    d = P.point_source_data(w, spec.x_d, spec.z_d)
+    assert rel(ctx.point_source_data(spec.x_d, spec.z_d, dev(w)), d) <= TOL
+    r0 = P.rhs(d)
+    _, hist, iters, _ = ctx.solve(dev(d), spec.alpha, 0, spec.rtol)
+    assert iters == 0 and abs(hist[0] - np.linalg.norm(r0)) <= TOL * np.linalg.norm(r0)
+    h = dev(W.random_gather(spec.nt, spec.n_line, 8))
+    y = dev(W.random_gather(spec.nt, spec.n_rec, 9))
+    a, b = float((ctx.forward(h) * y).sum()), float((h * ctx.adjoint(y)).sum())
+    assert abs(a - b) <= 1e-5 * abs(a)
+
+
+# ------------------------------------------------------------- edge cases --
+@pytest.mark.parametrize("nt", [1, 2, 7])
+def test_few_steps_and_single_point_lines(ssx, oracle, nt):
+    """nt = 1 and 2 (the lines 2 rows apart so one step couples them) and
+    one-point lines."""
+    spec = dataclasses.replace(W.small(order=4, nt=nt), z_r=0.53, ix_line0=40, n_line=1,
+                               ix_rec0=38, n_rec=5)
+    ctx, P = make(ssx, oracle, spec)
+    h = W.random_gather(spec.nt, 1, 10)
+    ref = P.S(h)
+    assert np.abs(ref).max() > 0
+    assert rel(ctx.forward(dev(h)), ref) <= TOL
+    d = W.random_gather(spec.nt, spec.n_rec, 11)
+    ref = P.ST(d)
+    assert np.abs(ref).max() > 0
+    assert rel(ctx.adjoint(dev(d)), ref) <= TOL
+
+
+def test_no_sponge_tiny_grid_parity(ssx, oracle):
+    spec = dataclasses.replace(W.tiny(order=8), n_sponge=0, nx=9, nz=12, ix_line0=0, n_line=9,
+                               ix_rec0=0, n_rec=9, z_s=0.08, z_r=0.03, dz_datum=0.02)
+    ctx, P = make(ssx, oracle, spec)
+    h = W.random_gather(spec.nt, spec.n_line, 12)
+    assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
+    x = W.random_gather(spec.nt, spec.n_line, 13)
+    assert rel(ctx.weight_apply(ssx.W_M_INV, dev(x)), P.Wminv(x)) <= TOL
+
+
+def test_zero_data_gives_zero_source(ssx):
+    spec = W.small(order=4, nt=100)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    h, hist, iters, status = ctx.solve(torch.zeros(spec.nt, spec.n_rec, dtype=torch.float64,
+                                                   device="cuda"), 0.1, 5, 1e-3)
+    assert iters == 0 and status == "SSX_OK" and float(h.abs().max()) == 0.0 and hist[0] == 0.0
+
+
+def test_errors_are_reported_not_raised_from_cuda(ssx):
+    spec = W.small(order=4, nt=50)
+    ctx = ssx.Context.from_spec(spec)
+    # operators before the model and geometry are set: SSX_ERR_ARG, no device work
+    assert ctx._lib.ssx_forward(ctx._c, None, None) == 1
+    assert b"not called" in ctx._lib.ssx_last_error(ctx._c)
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.set_geometry(spec.z_s, 0, spec.nx + 1, spec.z_r, 0, 10, spec.x_s)
+    assert e.value.code == 1
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.set_geometry(spec.z_s, 0, 10, spec.z_s, 0, 10, spec.x_s)
+    assert e.value.code == 1
+    fast = torch.full((spec.nz, spec.nx), 100.0, dtype=torch.float32, device="cuda")
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.set_velocity_model(fast, 1.0)
+    assert e.value.code == 3                      # SSX_ERR_CFL
+    ctx.set_velocity_model(torch.as_tensor(W.velocity(spec), dtype=torch.float32, device="cuda"), 1.0)
+    ctx.set_geometry(spec.z_s, spec.ix_line0, spec.n_line, spec.z_r, spec.ix_rec0, spec.n_rec, spec.x_s)
+    with pytest.raises(TypeError):
+        ctx.forward(torch.zeros(spec.nt, spec.n_line, dtype=torch.float32, device="cuda"))
+
+
+def test_deterministic(ssx):
+    spec = frac_spec(8)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    x = dev(W.random_gather(spec.nt, spec.n_line, 14))
+    a = ctx.normal_apply(ssx.MODE_PCG, 0.2, x).clone()
+    b = ctx.normal_apply(ssx.MODE_PCG, 0.2, x).clone()
+    assert torch.equal(a, b)
+
+
+def test_stream_ordering_with_torch_stream(ssx, oracle):
+    """Work queued by torch on a side stream before the call is seen by it."""
+    spec = W.small(order=4, nt=200)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+        h = dev(W.smooth_random_gather(spec.nt, spec.n_line, 15))
+        h2 = h * 2.0               # queued on s
+        d = ctx.forward(h2)        # must run after the multiply
+        d2 = d * 0.5
+    s.synchronize()
+    P = oracle.Problem(spec, W.velocity(spec))
+    assert rel(d2, P.S(h.cpu().numpy())) <= TOL
