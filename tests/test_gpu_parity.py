@@ -176,13 +176,12 @@ def test_few_steps_and_single_point_lines(ssx, oracle, nt):
                                ix_rec0=38, n_rec=5)
     ctx, P = make(ssx, oracle, spec)
     h = W.random_gather(spec.nt, 1, 10)
-    ref = P.S(h)
-    assert np.abs(ref).max() > 0
-    assert rel(ctx.forward(dev(h)), ref) <= TOL
     d = W.random_gather(spec.nt, spec.n_rec, 11)
-    ref = P.ST(d)
-    assert np.abs(ref).max() > 0
-    assert rel(ctx.adjoint(dev(d)), ref) <= TOL
+    for got, ref in ((ctx.forward(dev(h)), P.S(h)), (ctx.adjoint(dev(d)), P.ST(d))):
+        if nt == 1:   # one step cannot carry the source two rows up
+            assert np.abs(ref).max() == 0 and float(got.abs().max()) == 0.0
+        else:
+            assert np.abs(ref).max() > 0 and rel(got, ref) <= TOL
 
 
 def test_no_sponge_tiny_grid_parity(ssx, oracle):
