@@ -1,0 +1,352 @@
+"""Benchmark: preconditioned-CG source-subproblem solves per second on one
+GB300 (or N replicas under torchrun), with the stencil roofline, an
+end-to-end host-buffer measurement and the FP64 oracle as the CPU baseline.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one whole solve (Algorithm 1, up to 30 PCG iterations, stop at
+1e-3 relative residual) of the 601 x 301 lens workload: 3000 time steps of
+an order-8 staggered grid, FP32 fields, FP64 Krylov vectors. Inputs (the
+velocity model and the data gather) are resident in HBM before the timed
+region; L2 is flushed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG source solves/sec to 1e-3 rel. residual; stencil Gpt-updates/s & HBM % of peak"
+BYTES_PER_POINT = 28.0   # fused v+p step: read p, vx, vz, kappa dt/h; write p, vx, vz (FP32)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_2203_16573_gb300 import workloads as W
+    return W.c2()
+
+
+def config_of(spec, n_gpus, extra=None):
+    cfg = {"workload": spec.name, "grid": f"{spec.nx}x{spec.nz}", "h_m": spec.h * 1000,
+           "padded": f"{spec.nx + 2 * spec.n_sponge}x{spec.nz + 2 * spec.n_sponge}",
+           "space_order": spec.order, "nt": spec.nt, "dt_ms": spec.dt * 1000,
+           "n_line": spec.n_line, "n_rec": spec.n_rec, "alpha": spec.alpha,
+           "maxit": spec.maxit, "rtol": spec.rtol, "model": "gradient 1.5-3 km/s + -20% lens",
+           "source": f"{spec.f_peak:g} Hz Ricker point source on the line",
+           "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU",
+           "l2": "flushed between steps (256 MB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------- oracle legs --
+def oracle_rate(spec, steps_sample):
+    """Oracle point-update rate on the host: a forward sweep of the full grid
+    for `steps_sample` time steps (plus its S^T), FP64."""
+    import dataclasses
+    from oracle import ssx_oracle
+    from paper_2203_16573_gb300 import workloads as W
+    sub = dataclasses.replace(spec, nt=steps_sample)
+    P = ssx_oracle.Problem(sub, W.velocity(sub))
+    h = W.smooth_random_gather(sub.nt, sub.n_line, 1)
+    t = time.perf_counter()
+    d = P.S(h)
+    P.ST(d)
+    el = time.perf_counter() - t
+    pts = 2.0 * P.g.NX * P.g.NZ * steps_sample
+    return pts / el, el, ssx_oracle.num_threads()
+
+
+def solve_point_updates(spec, iters, alpha):
+    """Grid-point steps of one PCG solve with `iters` iterations: r_0 (W~_d
+    slab pair + S^T), M^{-1} (slab pair) and N (S, slab pair, S^T and, for
+    alpha > 0, the W~_m slab pair) per iteration."""
+    from oracle import ssx_oracle
+    from paper_2203_16573_gb300 import workloads as W
+    P = ssx_oracle.Problem(spec, W.velocity(spec))
+    full = P.g.NX * P.g.NZ
+    ss = P.slab_s.grid.NX * P.slab_s.grid.NZ
+    sr = P.slab_r.grid.NX * P.slab_r.grid.NZ
+    per_N = 2 * full + 2 * sr + (2 * ss if alpha > 0 else 0)
+    per_M = 2 * ss
+    setup = 2 * sr + full + per_M + per_N
+    return spec.nt * (setup + max(iters - 1, 0) * (per_M + per_N))
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    spec = workload()
+    sample_steps = 300
+    iters = spec.maxit
+    work = solve_point_updates(spec, iters, spec.alpha)
+    for _ in range(args.warmup):
+        oracle_rate(spec, 20)
+    times, rates = [], []
+    for _ in range(args.steps):
+        rate, el, cores = oracle_rate(spec, sample_steps)
+        rates.append(rate)
+        times.append(el)
+    rate = float(np.median(rates))
+    value = rate / work
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(spec, args.gpus),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: S and S^T sweeps of the full {spec.nx}x{spec.nz} "
+                                       f"grid for {sample_steps} of {spec.nt} time steps, "
+                                       f"extrapolated by point updates to a {iters}-iteration solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_gpt_updates_per_s": rate / 1e9}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm --
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from oracle import ssx_oracle
+    from paper_2203_16573_gb300 import build, ssx, workloads as W
+    build.build()
+    spec = workload()
+    vel = W.velocity(spec)
+    ctx = ssx.Context.for_problem(spec, vel)
+    wavelet = torch.as_tensor(W.ricker(spec), device=dev)
+    d = ctx.point_source_data(spec.x_d, spec.z_d, wavelet)     # data gather, resident
+    h = torch.empty(spec.nt, spec.n_line, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve():
+        return ctx.solve(d, spec.alpha, spec.maxit, spec.rtol, ssx.MODE_PCG, out=h)
+
+    for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
+        flush.fill_(1.0)
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves on resident inputs ----
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters_list, res_list = [], []
+    t_dev = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0.record(stream)
+        _, hist, iters, status = solve()
+        ev1.record(stream)
+        ev1.synchronize()
+        t_dev += ev0.elapsed_time(ev1)
+        iters_list.append(iters)
+        res_list.append(float(hist[-1] / hist[0]))
+    barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    st = ctx.stats()
+    t_max = t_dev
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * args.steps / (t_max / 1000.0)
+
+    # ---- end to end through the public API with host buffers ----
+    d_host = d.cpu().pin_memory()
+    h_host = torch.empty(spec.nt, spec.n_line, dtype=torch.float64).pin_memory()
+    d_dev = torch.empty_like(d)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    t_e2e = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(1.0)
+        e0.record(stream)
+        d_dev.copy_(d_host, non_blocking=True)
+        ctx.solve(d_dev, spec.alpha, spec.maxit, spec.rtol, ssx.MODE_PCG, out=h)
+        h_host.copy_(h, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * e2e_steps / (t_e2e / 1000.0)
+
+    # ---- roofline of the stencil step kernels (event-timed sweeps) ----
+    hbm, peak_kind = peaks()
+    gpts = st["timed_point_updates"] / (st["sweep_ms"] / 1000.0) / 1e9 if st["sweep_ms"] else 0.0
+    achieved = gpts * BYTES_PER_POINT
+    per_launch_us = 1000.0 * st["sweep_ms"] / max(st["timed_steps"], 1)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        if tj.get("kernel_source_hash") == _stencil_hash():
+            traffic = tj.get("bytes_per_launch")
+    except Exception:
+        pass
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "k_fwd/k_adj fused staggered step (all sweeps of the solve)",
+            "bytes_per_point_update": BYTES_PER_POINT,
+            "avg_launch_us": per_launch_us,
+            "note": "achieved = 28 B x grid points x steps / event-timed sweep time"}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 fields, f64 krylov", "data": "synthetic (seeded lens model, Ricker point source)",
+            "config": config_of(spec, world),
+            "iterations": iters_list, "final_rel_residual": res_list,
+            "converged": all(r <= spec.rtol for r in res_list),
+            "stencil_gpt_updates_per_s": gpts,
+            "point_updates_per_solve": st["point_updates"] / args.steps,
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": d_host.numel() * 8, "d2h_bytes_per_step": h_host.numel() * 8},
+            "gpu_launches": st["kernel_launches"],
+            "clocks": clk}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el, cores = oracle_rate(spec, args.cpu_steps)
+        work = st["point_updates"] / args.steps
+        line["cpu_baseline"] = {"value": rate / work, "unit": "solves/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"S and S^T sweeps of the full {spec.nx}x{spec.nz} grid for "
+                                          f"{args.cpu_steps} of {spec.nt} time steps ({el:.1f} s), "
+                                          f"extrapolated by point updates to one solve",
+                                "oracle_gpt_updates_per_s": rate / 1e9}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _stencil_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "stencil.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=600)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
