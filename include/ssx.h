@@ -173,6 +173,44 @@ int ssx_set_timing(ssx_ctx *ctx, int on);
 int ssx_get_stats(ssx_ctx *ctx, ssx_stats *out);
 int ssx_reset_stats(ssx_ctx *ctx);
 
+/* Capacity, in floats (16 MiB), of the fixed device scratch array used by
+ * ssx_forward_noalloc. */
+#define SSX_NOALLOC_MAX_FLOATS 4194304
+
+/* d = S h, like ssx_forward, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this entry point exists for integration only.
+ *
+ * Some callers cannot call cudaMalloc: a plug-in inside a framework that owns
+ * the device's whole memory pool, code running under a fixed memory budget,
+ * or code that must not allocate (and risk an implicit synchronisation) in
+ * the middle of its own work. Here the caller passes the grid and geometry
+ * descriptors, the model v_dev [nz][nx] (float32, device), rho, the source
+ * gather h_dev [nt][n_line] and the output d_dev [nt][n_rec] (float64,
+ * device); no context is needed. All scratch (padded kappa field, two
+ * ping-pong wavefield triples, sponge tables, the model maximum) lives in
+ * one file-scope device array of SSX_NOALLOC_MAX_FLOATS floats that every
+ * GPU loading the library holds until the process exits. Nothing is
+ * allocated or freed.
+ *
+ * The grid must fit: 7 P Q + 2 (nx + nz + 4 n_sponge) + 64 <= SSX_NOALLOC_MAX_FLOATS
+ * with P = roundup(roundup(nx + 2 n_sponge, 128) + 64, 32) and
+ * Q = roundup(nz + 2 n_sponge, 32) + 16 (the 601 x 301 grid with a
+ * 40-point sponge uses 2.33 M floats); larger grids return SSX_ERR_ARG
+ * before any device work. Other errors: SSX_ERR_ARG for invalid arguments,
+ * SSX_ERR_CFL, SSX_ERR_CUDA; there is no message string.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. The call enqueues its work on `stream` and
+ * synchronises that stream once (a 4-byte read of the model maximum for the
+ * CFL check). Every call shares the one array, which keeps the last call's
+ * contents; each call clears what must start at zero. Calls whose work
+ * overlaps on the GPU (other streams or threads) race on the array and must
+ * be serialised by the caller. */
+int ssx_forward_noalloc(const ssx_grid_desc *grid, const ssx_geom_desc *geom,
+                        const float *v_dev, double rho, const double *h_dev,
+                        double *d_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

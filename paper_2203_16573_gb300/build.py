@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libssx.so")
-SOURCES = ["stencil.cu", "krylov.cu", "runtime.cu"]
+SOURCES = ["stencil.cu", "krylov.cu", "runtime.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

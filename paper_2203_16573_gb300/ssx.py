@@ -26,7 +26,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_velocity_model", "ssx_set_geometry", "ssx_forward", "ssx_adjoint",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
-           "ssx_get_stats", "ssx_reset_stats"]
+           "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc"]
 
 
 class SSXError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_set_timing": ([vp, i], i),
         "ssx_get_stats": ([vp, P(Stats)], i),
         "ssx_reset_stats": ([vp], i),
+        "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
