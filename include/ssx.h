@@ -165,6 +165,22 @@ int ssx_solve_source_subproblem(ssx_ctx *ctx, const double *d_dev, double alpha,
 int ssx_point_source_data(ssx_ctx *ctx, double x_d, double z_d,
                           const double *wavelet_dev, double *d_dev);
 
+/* How a sweep (nt time steps of one grid) is launched:
+ * SSX_SWEEP_AUTO (default): one cooperative launch for the whole sweep when
+ *   every tile's CTA can be resident at once (each CTA steps its tile and
+ *   waits, with a 2 s bound, only for its four edge neighbours); otherwise
+ *   SSX_SWEEP_STEP.
+ * SSX_SWEEP_STEP: one launch per time step, replayed from a CUDA graph.
+ * SSX_SWEEP_PERSISTENT: cooperative launch or SSX_ERR_ARG if it cannot fit.
+ * Both launch forms run the same per-tile arithmetic. A neighbour wait that
+ * times out makes the call return SSX_ERR_CUDA ("timed out") instead of
+ * hanging; the context stays usable.
+ * SSX_SWEEP_TEST_STALL (test hook, not a mode): in the next persistent sweep
+ *   one tile never signals its neighbours, whose waits then run out after
+ *   0.2 s, so the timeout path can be exercised without a fault. */
+enum { SSX_SWEEP_AUTO = 0, SSX_SWEEP_STEP = 1, SSX_SWEEP_PERSISTENT = 2, SSX_SWEEP_TEST_STALL = 3 };
+int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
+
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the
  * launching stream; ssx_get_stats then reports their summed device time. */
 int ssx_set_timing(ssx_ctx *ctx, int on);

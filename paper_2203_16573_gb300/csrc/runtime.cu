@@ -58,6 +58,8 @@ struct DGrid {
     float *tab = nullptr;     // sponge tables: sxi sxh (NX each) szi szh (NZ each)
     float *kap = nullptr;
     float *f[2][3] = {};      // origin-offset field pointers
+    unsigned *flags = nullptr;  // per-tile step counters of the persistent sweep
+    int tiles_x = 0, tiles_z = 0;
     GridArgs args{};
     bool ready = false;
 };
@@ -107,6 +109,10 @@ struct ssx_ctx {
     double *sc_host = nullptr;                                // pinned
     std::vector<double> hostD;
 
+    int *d_err = nullptr;      // persistent-sweep wait timeout flag (device)
+    int sweep_mode = SSX_SWEEP_AUTO;
+    int cap_fwd = -1, cap_adj = -1;   // co-resident CTAs of the persistent kernels
+    bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
     bool use_graphs = true;
     std::unordered_map<std::string, cudaGraphExec_t> graphs;
     std::unordered_map<std::string, long long> graph_nodes;
@@ -160,6 +166,13 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     CK(cudaMalloc(&G.mem, 7 * E * sizeof(float)));
     CK(cudaMalloc(&G.tab, 2 * (size_t)(L.NX + L.NZ) * sizeof(float)));
     CK(cudaMemsetAsync(G.mem, 0, 7 * E * sizeof(float), c->s));
+    int tx = 0, tz = 0;
+    tile_shape(c->R, &tx, &tz);
+    G.tiles_x = (L.NX + tx - 1) / tx;
+    G.tiles_z = (L.NZ + tz - 1) / tz;
+    if (G.flags) cudaFree(G.flags);
+    G.flags = nullptr;
+    CK(cudaMalloc(&G.flags, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned)));
     G.kap = G.mem + L.origin();
     for (int b = 0; b < 2; b++)
         for (int f = 0; f < 3; f++) G.f[b][f] = G.mem + (1 + 3 * b + f) * E + L.origin();
@@ -180,8 +193,40 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
 void grid_free(DGrid &G) {
     if (G.mem) cudaFree(G.mem);
     if (G.tab) cudaFree(G.tab);
+    if (G.flags) cudaFree(G.flags);
     G.mem = nullptr;
     G.tab = nullptr;
+    G.flags = nullptr;
+}
+
+// Persistent sweeps need every tile's CTA resident at once (cooperative
+// launch); otherwise a sweep is nt step launches replayed from a CUDA graph.
+int use_persistent(ssx_ctx *c, const DGrid &G, bool adj) {
+    if (c->sweep_mode == SSX_SWEEP_STEP) return 0;
+    int &cap = adj ? c->cap_adj : c->cap_fwd;
+    if (cap < 0) cap = persist_capacity(c->R, adj);
+    const bool fits = G.tiles_x * G.tiles_z <= cap;
+    if (c->sweep_mode == SSX_SWEEP_PERSISTENT && !fits) return -1;
+    return fits ? 1 : 0;
+}
+
+PersistArgs persist_args(ssx_ctx *c, const DGrid &G) {
+    PersistArgs pa{};
+    for (int b = 0; b < 2; b++)
+        for (int f = 0; f < 3; f++) pa.f[b][f] = G.f[b][f];
+    pa.nt = c->gd.nt;
+    pa.tiles_x = G.tiles_x;
+    pa.tiles_z = G.tiles_z;
+    pa.flags = G.flags;
+    pa.err = c->d_err;
+    pa.timeout_ns = 2000000000ull;   // 2 s per neighbour wait
+    pa.stall_tile = -1;
+    if (c->stall_next) {             // a wait that must run out: tile 0 never publishes
+        pa.stall_tile = 0;
+        pa.timeout_ns = 200000000ull;
+        c->stall_next = false;
+    }
+    return pa;
 }
 
 // kappa dt/h field and sponge tables from the current model
@@ -309,6 +354,32 @@ int sim_fwd(ssx_ctx *c, DGrid &G, const Line &src, const double *hs, const doubl
         return SSX_OK;
     };
     const double pts = (double)G.L.NX * G.L.NZ * nt;
+    const int pers = use_persistent(c, G, false);
+    if (pers < 0) return fail(c, SSX_ERR_ARG, "persistent sweep requested but the grid's tiles do not fit");
+    if (pers) {
+        auto enqueue_p = [&, nt](cudaStream_t s) -> int {
+            if (outp) CK(cudaMemsetAsync(outp, 0, (size_t)nt * rec.n * sizeof(double), s));
+            if (outv) CK(cudaMemsetAsync(outv, 0, (size_t)nt * rec.n * sizeof(double), s));
+            const size_t E = G.L.elems();
+            CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+            CK(cudaMemsetAsync(G.flags, 0, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned), s));
+            FwdArgs a{};
+            a.g = G.args;
+            a.src = src;
+            a.hsrc = hs;
+            a.fsrc = fs;
+            a.rec = rec;
+            a.outp = outp;
+            a.outv = outv;
+            CK(launch_fwd_persist(a, persist_args(c, G), c->R, s));
+            return SSX_OK;
+        };
+        const bool g0 = c->use_graphs;
+        c->use_graphs = false;
+        int rc = run_cached(c, "", 1, nt, pts, enqueue_p);
+        c->use_graphs = g0;
+        return rc;
+    }
     if (!cache) {
         TRY(enqueue(c->s));
         c->st.kernel_launches += nt;
@@ -356,6 +427,36 @@ int sim_adj(ssx_ctx *c, DGrid &G, const Line &src, double *hb, double *fb, const
         }
         return SSX_OK;
     };
+    const int pers = use_persistent(c, G, true);
+    if (pers < 0) return fail(c, SSX_ERR_ARG, "persistent sweep requested but the grid's tiles do not fit");
+    if (pers) {
+        auto enqueue_p = [&, nt](cudaStream_t s) -> int {
+            const size_t E = G.L.elems();
+            if (hb) CK(cudaMemsetAsync(hb, 0, (size_t)nt * src.n * sizeof(double), s));
+            if (fb) CK(cudaMemsetAsync(fb, 0, (size_t)nt * src.n * sizeof(double), s));
+            CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+            CK(cudaMemsetAsync(G.flags, 0, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned), s));
+            AdjArgs a{};
+            a.g = G.args;
+            a.src = src;
+            a.hbar = hb;
+            a.fbar = fb;
+            a.rec = rec;
+            a.yp = yp;
+            a.yv = yv;
+            a.p_in = G.f[0][0];
+            a.vx_in = G.f[0][1];
+            a.vz_in = G.f[0][2];
+            CK(launch_adj_init(a, nt, s));
+            CK(launch_adj_persist(a, persist_args(c, G), c->R, s));
+            return SSX_OK;
+        };
+        const bool g0 = c->use_graphs;
+        c->use_graphs = false;
+        int rc = run_cached(c, "", 2, nt, (double)G.L.NX * G.L.NZ * nt, enqueue_p);
+        c->use_graphs = g0;
+        return rc;
+    }
     char tag[64];
     snprintf(tag, sizeof tag, "adj%p:%d:%d:%g", (void *)&G, src.kp, rec.kp, (double)src.scale);
     return run_cached(c, ptr_key(tag, hb, fb, yp, yv), nt + 1, nt, (double)G.L.NX * G.L.NZ * nt,
@@ -466,6 +567,18 @@ int leave(ssx_ctx *c, int rc) {
         return fail(c, SSX_ERR_CUDA, "stream ordering failed");
     return rc;
 }
+// Reads (and clears) the persistent-sweep timeout flag; synchronises.
+int check_sweeps(ssx_ctx *c) {
+    int *eh = reinterpret_cast<int *>(c->sc_host + SC_COUNT);
+    CK(cudaMemcpyAsync(eh, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (*eh != 0) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
+        return fail(c, SSX_ERR_CUDA, "a persistent sweep's neighbour wait timed out");
+    }
+    return SSX_OK;
+}
+
 int ready(ssx_ctx *c) {
     if (!c) return SSX_ERR_ARG;
     if (!c->have_model) return fail(c, SSX_ERR_ARG, "ssx_set_velocity_model not called");
@@ -530,7 +643,9 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
         CK(cudaMalloc(&c->vmax_dev, sizeof(float)));
         CK(cudaMalloc(&c->sc, SC_COUNT * sizeof(double)));
         CK(cudaMalloc(&c->partials, kDotBlocks * sizeof(double)));
-        CK(cudaMallocHost(&c->sc_host, SC_COUNT * sizeof(double)));
+        CK(cudaMallocHost(&c->sc_host, (SC_COUNT + 1) * sizeof(double)));
+        CK(cudaMalloc(&c->d_err, sizeof(int)));
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
         TRY(grid_alloc(c, c->full, gd->nx, gd->nz, 0, 0.0));
         CK(cudaStreamSynchronize(c->s));
         return SSX_OK;
@@ -563,6 +678,7 @@ int ssx_destroy(ssx_ctx *c) {
     if (c->sc) cudaFree(c->sc);
     if (c->partials) cudaFree(c->partials);
     if (c->sc_host) cudaFreeHost(c->sc_host);
+    if (c->d_err) cudaFree(c->d_err);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->s) cudaStreamDestroy(c->s);
@@ -664,7 +780,7 @@ int ssx_forward(ssx_ctx *c, const double *h_dev, double *d_dev) {
         CK(cudaMemcpyAsync(c->tl1, h_dev, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
         TRY(op_S(c, c->tl1, c->tr1));
         CK(cudaMemcpyAsync(d_dev, c->tr1, rec_bytes(c), cudaMemcpyDeviceToDevice, c->s));
-        return SSX_OK;
+        return check_sweeps(c);
     };
     return leave(c, body());
 }
@@ -677,7 +793,7 @@ int ssx_adjoint(ssx_ctx *c, const double *d_dev, double *h_dev) {
         CK(cudaMemcpyAsync(c->tr2, d_dev, rec_bytes(c), cudaMemcpyDeviceToDevice, c->s));
         TRY(op_ST(c, c->tr2, c->tl2));
         CK(cudaMemcpyAsync(h_dev, c->tl2, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
-        return SSX_OK;
+        return check_sweeps(c);
     };
     return leave(c, body());
 }
@@ -696,7 +812,7 @@ int ssx_weight_apply(ssx_ctx *c, int which, const double *in, double *out) {
         CK(cudaMemcpyAsync(bi, in, bytes, cudaMemcpyDeviceToDevice, c->s));
         TRY(op_W(c, which, bi, bo));
         CK(cudaMemcpyAsync(out, bo, bytes, cudaMemcpyDeviceToDevice, c->s));
-        return SSX_OK;
+        return check_sweeps(c);
     };
     return leave(c, body());
 }
@@ -709,7 +825,7 @@ int ssx_precond_apply(ssx_ctx *c, double alpha, const double *r, double *g) {
         CK(cudaMemcpyAsync(c->r, r, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
         TRY(op_Minv(c, SSX_MODE_PCG, alpha, c->r, c->g));
         CK(cudaMemcpyAsync(g, c->g, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
-        return SSX_OK;
+        return check_sweeps(c);
     };
     return leave(c, body());
 }
@@ -723,7 +839,7 @@ int ssx_normal_apply(ssx_ctx *c, int mode, double alpha, const double *p, double
         CK(cudaMemcpyAsync(c->p, p, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
         TRY(op_N(c, mode, alpha, c->p, c->q));
         CK(cudaMemcpyAsync(q, c->q, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
-        return SSX_OK;
+        return check_sweeps(c);
     };
     return leave(c, body());
 }
@@ -750,6 +866,7 @@ int ssx_solve_source_subproblem(ssx_ctx *c, const double *d_dev, double alpha, i
         CK(launch_dot(c->g, c->r, nl, c->partials, sc + SC_GR, s));
         CK(launch_dot(c->r, c->r, nl, c->partials, sc + SC_RR, s));
         c->st.kernel_launches += 4;
+        TRY(check_sweeps(c));
         CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const double r0 = std::sqrt(sh[SC_RR]);
@@ -762,6 +879,7 @@ int ssx_solve_source_subproblem(ssx_ctx *c, const double *d_dev, double alpha, i
             CK(launch_pcg_alpha(sc, s));
             CK(launch_pcg_update(c->h, c->r, c->p, c->q, nl, sc, c->partials, s));
             c->st.kernel_launches += 5;
+            TRY(check_sweeps(c));   // copies the sweep flag and synchronises
             CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (sh[SC_FLAG] != 0.0) {
@@ -808,7 +926,20 @@ int ssx_point_source_data(ssx_ctx *c, double x_d, double z_d, const double *w, d
     TRY(make_line(c, c->full, z_d, ix, 1, 1.0 / h, &pt));
     TRY(enter(c));
     int rc = sim_fwd(c, c->full, pt, w, nullptr, c->rec, d_dev, nullptr, false);
+    if (rc == SSX_OK) rc = check_sweeps(c);
     return leave(c, rc);
+}
+
+int ssx_set_sweep_mode(ssx_ctx *c, int mode) {
+    if (!c) return SSX_ERR_ARG;
+    if (mode == SSX_SWEEP_TEST_STALL) {
+        c->stall_next = true;
+        return SSX_OK;
+    }
+    if (mode != SSX_SWEEP_AUTO && mode != SSX_SWEEP_STEP && mode != SSX_SWEEP_PERSISTENT)
+        return fail(c, SSX_ERR_ARG, "unknown sweep mode");
+    c->sweep_mode = mode;
+    return SSX_OK;
 }
 
 int ssx_set_timing(ssx_ctx *c, int on) {

@@ -76,8 +76,22 @@ struct AdjArgs {
     int n;                // step index (reverse sweep: nt-1 .. 0)
 };
 
+// A whole sweep in one cooperative launch (one CTA per tile, neighbour flags).
+struct PersistArgs {
+    float *f[2][3];              // ping-pong field triples (origin-offset pointers)
+    int nt;
+    int tiles_x, tiles_z;
+    unsigned *flags;             // [tiles] steps completed, zeroed before the sweep
+    int *err;                    // set to 1 if a neighbour wait timed out
+    unsigned long long timeout_ns;
+    int stall_tile;              // test hook: this tile never publishes (-1: none)
+};
+
 // Kernel launchers (stencil.cu). Return cudaGetLastError() of the launch.
 cudaError_t launch_fwd_step(const FwdArgs &a, int R, cudaStream_t s);
+cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, cudaStream_t s);
+cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, cudaStream_t s);
+int persist_capacity(int R, bool adj);   // co-resident CTAs of the persistent kernels
 cudaError_t launch_adj_step(const AdjArgs &a, int R, cudaStream_t s);
 cudaError_t launch_adj_init(const AdjArgs &a, int nt, cudaStream_t s);
 cudaError_t launch_fill_kappa(float *kap, const FieldLayout &L, const float *vel, int nx, int nz,

@@ -44,228 +44,386 @@ __device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
 
 constexpr int kThreads = 256;
 
-template <int R, int TX, int TZ>
-__global__ void __launch_bounds__(kThreads) k_fwd(const FwdArgs a) {
-    constexpr int H = 2 * R;
-    constexpr int PW = TX + 2 * H, PH = TZ + 2 * H;
-    constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
-    __shared__ float sp[PH][PW];
-    __shared__ float svx[TZ][VXW];
-    __shared__ float svz[VZH][TX];
+// Field loads go through L2 only (ld.global.cg): in the persistent sweep a
+// neighbour CTA rewrote these lines during the previous step, and L1 is not
+// coherent across SMs.
+__device__ __forceinline__ float ldf(const float *p) { return __ldcg(p); }
 
+template <int R, int TX, int TZ>
+struct TileSmem {
+    static constexpr int H = 2 * R;
+    static constexpr int PW = TX + 2 * H, PH = TZ + 2 * H;
+    static constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
+    float sp[PH][PW];      // p^n (forward) or q = C_p pbar (transpose), tile + 2k halo
+    float svx[TZ][VXW];    // v_x^{n+1/2} (forward) or C_vx vbar_x' (transpose)
+    float svz[VZH][TX];    // v_z^{n+1/2} (forward) or C_vz vbar_z' (transpose)
+};
+
+// Thread layout for the tile loops: 8 warps; a warp walks a row, the warps
+// walk rows (no integer division in the loops).
+#define TILE_LANE (threadIdx.x & 31)
+#define TILE_WARP (threadIdx.x >> 5)
+
+// One forward step on the TX x TZ tile at (i0, k0).
+template <int R, int TX, int TZ>
+__device__ __forceinline__ void fwd_tile(const FwdArgs &a, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    constexpr int H = S::H, PW = S::PW, PH = S::PH, VXW = S::VXW, VZH = S::VZH;
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
-    const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
-    const int tid = threadIdx.x;
+    const int lane = TILE_LANE, wy = TILE_WARP;
 
-    // p^n over the tile and a 2k halo (the apron makes every read in bounds)
-    for (int idx = tid; idx < PH * PW; idx += kThreads) {
-        const int r = idx / PW, c = idx - r * PW;
-        sp[r][c] = a.p_in[(k0 - H + r) * pitch + (i0 - H + c)];
+    // p^n over the tile and a 2k halo, corners skipped (the apron makes
+    // every read in bounds)
+    for (int r = wy; r < PH; r += 8) {
+        const bool zh = (r < H) || (r >= H + TZ);
+        const float *row = a.p_in + (k0 - H + r) * pitch + (i0 - H);
+        for (int c = lane; c < PW; c += 32) {
+            if (zh && (c < H || c >= H + TX)) continue;
+            sm.sp[r][c] = ldf(row + c);
+        }
     }
     __syncthreads();
 
     // v_x^{n+1/2} on the tile rows, columns i0-k .. i0+TX+k-2
-    for (int idx = tid; idx < TZ * VXW; idx += kThreads) {
-        const int r = idx / VXW, jj = idx - r * VXW;
-        const int k = k0 + r, j = i0 - R + jj;
-        float val = 0.0f;
-        if (k < g.NZ && j >= 0 && j < g.NX - 1) {
-            const float *row = &sp[r + H][jj + R];
-            float d = 0.0f;
+    for (int r = wy; r < TZ; r += 8) {
+        const int k = k0 + r;
+        for (int jj = lane; jj < VXW; jj += 32) {
+            const int j = i0 - R + jj;
+            float val = 0.0f;
+            if (k < g.NZ && j >= 0 && j < g.NX - 1) {
+                const float *row = &sm.sp[r + H][jj + R];
+                float d = 0.0f;
 #pragma unroll
-            for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
-            float A, B;
-            damp(g.sxh[j] + g.szi[k], A, B);
-            const int o = k * pitch + j;
-            val = A * a.vx_in[o] - (B * g.cv) * d;
-            if (jj >= R && jj < R + TX) a.vx_out[o] = val;
+                for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
+                float A, B;
+                damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                const int o = k * pitch + j;
+                val = A * ldf(a.vx_in + o) - (B * g.cv) * d;
+                if (jj >= R && jj < R + TX) a.vx_out[o] = val;
+            }
+            sm.svx[r][jj] = val;
         }
-        svx[r][jj] = val;
     }
     // v_z^{n+1/2} on rows k0-k .. k0+TZ+k-2, the tile columns
-    for (int idx = tid; idx < VZH * TX; idx += kThreads) {
-        const int kk = idx / TX, c = idx - kk * TX;
-        const int k = k0 - R + kk, i = i0 + c;
-        float val = 0.0f;
-        if (i < g.NX && k >= 0 && k < g.NZ - 1) {
-            float d = 0.0f;
+    for (int kk = wy; kk < VZH; kk += 8) {
+        const int k = k0 - R + kk;
+        const bool own = (kk >= R && kk < R + TZ);
+        for (int c = lane; c < TX; c += 32) {
+            const int i = i0 + c;
+            float val = 0.0f;
+            if (i < g.NX && k >= 0 && k < g.NZ - 1) {
+                float d = 0.0f;
 #pragma unroll
-            for (int m = 1; m <= R; m++)
-                d += g.c[m - 1] * (sp[kk + R + m][c + H] - sp[kk + R + 1 - m][c + H]);
-            float A, B;
-            damp(g.sxi[i] + g.szh[k], A, B);
-            const int o = k * pitch + i;
-            const float cvz = B * g.cv;
-            val = A * a.vz_in[o] - cvz * d;
-            if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
-                const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-                const int jl = i - a.src.i0;
-                if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                    val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)a.n * a.src.n + jl];
-            }
-            if (kk >= R && kk < R + TZ) {
-                a.vz_out[o] = val;
-                if (a.outv) {
-                    const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
-                    const int jl = i - a.rec.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        atomicAdd(&a.outv[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+                for (int m = 1; m <= R; m++)
+                    d += g.c[m - 1] * (sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H]);
+                float A, B;
+                damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                const int o = k * pitch + i;
+                const float cvz = B * g.cv;
+                val = A * ldf(a.vz_in + o) - cvz * d;
+                if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
+                    const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+                    const int jl = i - a.src.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                        val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)a.n * a.src.n + jl];
+                }
+                if (own) {
+                    a.vz_out[o] = val;
+                    if (a.outv) {
+                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+                        const int jl = i - a.rec.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                            atomicAdd(&a.outv[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+                    }
                 }
             }
+            sm.svz[kk][c] = val;
         }
-        svz[kk][c] = val;
     }
     __syncthreads();
 
     // p^{n+1} on the tile
-    for (int idx = tid; idx < TZ * TX; idx += kThreads) {
-        const int r = idx / TX, c = idx - r * TX;
-        const int k = k0 + r, i = i0 + c;
-        if (k < g.NZ && i < g.NX) {
-            float d = 0.0f;
+    for (int r = wy; r < TZ; r += 8) {
+        const int k = k0 + r;
+        for (int c = lane; c < TX; c += 32) {
+            const int i = i0 + c;
+            if (k < g.NZ && i < g.NX) {
+                float d = 0.0f;
 #pragma unroll
-            for (int m = 1; m <= R; m++) {
-                d += g.c[m - 1] * (svx[r][c + R + m - 1] - svx[r][c + R - m]);
-                d += g.c[m - 1] * (svz[r + R + m - 1][c] - svz[r + R - m][c]);
+                for (int m = 1; m <= R; m++) {
+                    d += g.c[m - 1] * (sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m]);
+                    d += g.c[m - 1] * (sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c]);
+                }
+                float A, B;
+                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                const int o = k * pitch + i;
+                const float cp = B * __ldg(g.kap + o);
+                float val = A * sm.sp[r + H][c + H] - cp * d;
+                if (a.hsrc) {   // constitutive defect h delta(z - z_s)
+                    const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+                    const int jl = i - a.src.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                        val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)a.n * a.src.n + jl];
+                }
+                a.p_out[o] = val;
+                if (a.outp) {
+                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+                    const int jl = i - a.rec.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                        atomicAdd(&a.outp[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+                }
             }
-            float A, B;
-            damp(g.sxi[i] + g.szi[k], A, B);
-            const int o = k * pitch + i;
-            const float cp = B * g.kap[o];
-            float val = A * sp[r + H][c + H] - cp * d;
-            if (a.hsrc) {   // constitutive defect h delta(z - z_s)
-                const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
-                const int jl = i - a.src.i0;
-                if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                    val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)a.n * a.src.n + jl];
+        }
+    }
+}
+
+// One transposed step on the tile at (i0, k0).
+template <int R, int TX, int TZ>
+__device__ __forceinline__ void adj_tile(const AdjArgs &a, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    constexpr int H = S::H, PW = S::PW, PH = S::PH, VXW = S::VXW, VZH = S::VZH;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch;
+    const int lane = TILE_LANE, wy = TILE_WARP;
+
+    // q = C_p pbar over tile + 2k halo; read out the transposed p injection
+    for (int r = wy; r < PH; r += 8) {
+        const int k = k0 - H + r;
+        const bool zh = (r < H) || (r >= H + TZ);
+        for (int c = lane; c < PW; c += 32) {
+            if (zh && (c < H || c >= H + TX)) continue;
+            const int i = i0 - H + c;
+            float q = 0.0f;
+            if (k >= 0 && k < g.NZ && i >= 0 && i < g.NX) {
+                float A, B;
+                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                const int o = k * pitch + i;
+                q = (B * __ldg(g.kap + o)) * ldf(a.p_in + o);
+                if (a.hbar && !zh && c >= H && c < H + TX) {
+                    const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+                    const int jl = i - a.src.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                        atomicAdd(&a.hbar[(size_t)a.n * a.src.n + jl],
+                                  (double)(w * a.src.scale) * (double)q);
+                }
             }
-            a.p_out[o] = val;
-            if (a.outp) {
-                const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
-                const int jl = i - a.rec.i0;
-                if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                    atomicAdd(&a.outp[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+            sm.sp[r][c] = q;
+        }
+    }
+    __syncthreads();
+
+    // vbar_x' = vbar_x + D+ q; keep C_vx vbar_x' for the p update
+    for (int r = wy; r < TZ; r += 8) {
+        const int k = k0 + r;
+        for (int jj = lane; jj < VXW; jj += 32) {
+            const int j = i0 - R + jj;
+            float val = 0.0f;
+            if (k < g.NZ && j >= 0 && j < g.NX - 1) {
+                const float *row = &sm.sp[r + H][jj + R];
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
+                float A, B;
+                damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                const int o = k * pitch + j;
+                const float vb = ldf(a.vx_in + o) + d;
+                val = (B * g.cv) * vb;
+                if (jj >= R && jj < R + TX) a.vx_out[o] = A * vb;
+            }
+            sm.svx[r][jj] = val;
+        }
+    }
+    // vbar_z' likewise; read out the transposed velocity injection
+    for (int kk = wy; kk < VZH; kk += 8) {
+        const int k = k0 - R + kk;
+        const bool own = (kk >= R && kk < R + TZ);
+        for (int c = lane; c < TX; c += 32) {
+            const int i = i0 + c;
+            float val = 0.0f;
+            if (i < g.NX && k >= 0 && k < g.NZ - 1) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++)
+                    d += g.c[m - 1] * (sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H]);
+                float A, B;
+                damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                const int o = k * pitch + i;
+                const float vb = ldf(a.vz_in + o) + d;
+                val = (B * g.cv) * vb;
+                if (own) {
+                    if (a.fbar) {
+                        const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+                        const int jl = i - a.src.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                            atomicAdd(&a.fbar[(size_t)a.n * a.src.n + jl],
+                                      (double)(w * a.src.scale) * (double)val);
+                    }
+                    float out = A * vb;
+                    if (a.yv && a.n >= 1) {   // transposed sampling of step n-1
+                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+                        const int jl = i - a.rec.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                            out += w * (float)a.yv[(size_t)(a.n - 1) * a.rec.n + jl];
+                    }
+                    a.vz_out[o] = out;
+                }
+            }
+            sm.svz[kk][c] = val;
+        }
+    }
+    __syncthreads();
+
+    // pbar <- A_p pbar + D- (C_v vbar')
+    for (int r = wy; r < TZ; r += 8) {
+        const int k = k0 + r;
+        for (int c = lane; c < TX; c += 32) {
+            const int i = i0 + c;
+            if (k < g.NZ && i < g.NX) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) {
+                    d += g.c[m - 1] * (sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m]);
+                    d += g.c[m - 1] * (sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c]);
+                }
+                float A, B;
+                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                const int o = k * pitch + i;
+                float out = A * ldf(a.p_in + o) + d;
+                if (a.yp && a.n >= 1) {
+                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+                    const int jl = i - a.rec.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                        out += w * (float)a.yp[(size_t)(a.n - 1) * a.rec.n + jl];
+                }
+                a.p_out[o] = out;
             }
         }
     }
 }
 
 template <int R, int TX, int TZ>
+__global__ void __launch_bounds__(kThreads) k_fwd(const FwdArgs a) {
+    __shared__ TileSmem<R, TX, TZ> sm;
+    fwd_tile<R, TX, TZ>(a, blockIdx.x * TX, blockIdx.y * TZ, sm);
+}
+
+template <int R, int TX, int TZ>
 __global__ void __launch_bounds__(kThreads) k_adj(const AdjArgs a) {
-    constexpr int H = 2 * R;
-    constexpr int PW = TX + 2 * H, PH = TZ + 2 * H;
-    constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
-    __shared__ float sq[PH][PW];
-    __shared__ float svx[TZ][VXW];
-    __shared__ float svz[VZH][TX];
+    __shared__ TileSmem<R, TX, TZ> sm;
+    adj_tile<R, TX, TZ>(a, blockIdx.x * TX, blockIdx.y * TZ, sm);
+}
 
-    const GridArgs &g = a.g;
-    const int pitch = g.pitch;
-    const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
-    const int tid = threadIdx.x;
+// ---------------------------------------------------------------------------
+// Persistent sweep: one cooperative launch runs all nt steps. CTA b owns tile
+// b for the whole sweep. Before step n it waits until its four edge
+// neighbours have published "n steps done" (their step n-1 outputs, which
+// its halo reads, are complete, and they no longer read the buffer it is
+// about to overwrite); after the step it publishes n+1. The tile is at least
+// 2k wide in both directions, so the halo never reaches beyond those four
+// neighbours. Waits are bounded: past `timeout_ns` of %globaltimer the CTA
+// records an error and every CTA leaves the sweep.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
-    // q = C_p pbar over tile + 2k halo; read out the transposed p injection
-    for (int idx = tid; idx < PH * PW; idx += kThreads) {
-        const int r = idx / PW, c = idx - r * PW;
-        const int k = k0 - H + r, i = i0 - H + c;
-        float q = 0.0f;
-        if (k >= 0 && k < g.NZ && i >= 0 && i < g.NX) {
-            float A, B;
-            damp(g.sxi[i] + g.szi[k], A, B);
-            const int o = k * pitch + i;
-            q = (B * g.kap[o]) * a.p_in[o];
-            if (a.hbar && r >= H && r < H + TZ && c >= H && c < H + TX) {
-                const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
-                const int jl = i - a.src.i0;
-                if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                    atomicAdd(&a.hbar[(size_t)a.n * a.src.n + jl],
-                              (double)(w * a.src.scale) * (double)q);
+// true = go on; false = leave the sweep (timeout here or elsewhere)
+__device__ __forceinline__ bool wait_neighbours(const PersistArgs &pa, int tile, unsigned need,
+                                                int *s_abort) {
+    if (threadIdx.x < 4) {
+        const int tx = tile % pa.tiles_x, tz = tile / pa.tiles_x;
+        int nb = -1;
+        if (threadIdx.x == 0 && tx > 0) nb = tile - 1;
+        if (threadIdx.x == 1 && tx + 1 < pa.tiles_x) nb = tile + 1;
+        if (threadIdx.x == 2 && tz > 0) nb = tile - pa.tiles_x;
+        if (threadIdx.x == 3 && tz + 1 < pa.tiles_z) nb = tile + pa.tiles_x;
+        if (nb >= 0 && ld_acquire(pa.flags + nb) < need) {
+            const unsigned long long t0 = globaltimer();
+            unsigned spins = 0;
+            while (ld_acquire(pa.flags + nb) < need) {
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)pa.err != 0) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    if (globaltimer() - t0 > pa.timeout_ns) {
+                        atomicExch(pa.err, 1);
+                        *s_abort = 1;
+                        break;
+                    }
+                }
+                __nanosleep(20);
             }
         }
-        sq[r][c] = q;
     }
     __syncthreads();
+    return *s_abort == 0;
+}
 
-    // vbar_x' = vbar_x + D+ q; keep C_vx vbar_x' for the p update
-    for (int idx = tid; idx < TZ * VXW; idx += kThreads) {
-        const int r = idx / VXW, jj = idx - r * VXW;
-        const int k = k0 + r, j = i0 - R + jj;
-        float val = 0.0f;
-        if (k < g.NZ && j >= 0 && j < g.NX - 1) {
-            const float *row = &sq[r + H][jj + R];
-            float d = 0.0f;
-#pragma unroll
-            for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
-            float A, B;
-            damp(g.sxh[j] + g.szi[k], A, B);
-            const int o = k * pitch + j;
-            const float vb = a.vx_in[o] + d;
-            val = (B * g.cv) * vb;
-            if (jj >= R && jj < R + TX) a.vx_out[o] = A * vb;
-        }
-        svx[r][jj] = val;
-    }
-    // vbar_z' likewise; read out the transposed velocity injection
-    for (int idx = tid; idx < VZH * TX; idx += kThreads) {
-        const int kk = idx / TX, c = idx - kk * TX;
-        const int k = k0 - R + kk, i = i0 + c;
-        float val = 0.0f;
-        if (i < g.NX && k >= 0 && k < g.NZ - 1) {
-            float d = 0.0f;
-#pragma unroll
-            for (int m = 1; m <= R; m++)
-                d += g.c[m - 1] * (sq[kk + R + m][c + H] - sq[kk + R + 1 - m][c + H]);
-            float A, B;
-            damp(g.sxi[i] + g.szh[k], A, B);
-            const int o = k * pitch + i;
-            const float vb = a.vz_in[o] + d;
-            val = (B * g.cv) * vb;
-            if (kk >= R && kk < R + TZ) {
-                if (a.fbar) {
-                    const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-                    const int jl = i - a.src.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        atomicAdd(&a.fbar[(size_t)a.n * a.src.n + jl],
-                                  (double)(w * a.src.scale) * (double)val);
-                }
-                float out = A * vb;
-                if (a.yv && a.n >= 1) {   // transposed sampling of step n-1
-                    const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
-                    const int jl = i - a.rec.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        out += w * (float)a.yv[(size_t)(a.n - 1) * a.rec.n + jl];
-                }
-                a.vz_out[o] = out;
-            }
-        }
-        svz[kk][c] = val;
-    }
+__device__ __forceinline__ void publish(const PersistArgs &pa, int tile, unsigned done) {
     __syncthreads();
+    if (threadIdx.x == 0 && tile != pa.stall_tile) {
+        __threadfence();
+        st_release(pa.flags + tile, done);
+    }
+}
 
-    // pbar <- A_p pbar + D- (C_v vbar')
-    for (int idx = tid; idx < TZ * TX; idx += kThreads) {
-        const int r = idx / TX, c = idx - r * TX;
-        const int k = k0 + r, i = i0 + c;
-        if (k < g.NZ && i < g.NX) {
-            float d = 0.0f;
-#pragma unroll
-            for (int m = 1; m <= R; m++) {
-                d += g.c[m - 1] * (svx[r][c + R + m - 1] - svx[r][c + R - m]);
-                d += g.c[m - 1] * (svz[r + R + m - 1][c] - svz[r + R - m][c]);
-            }
-            float A, B;
-            damp(g.sxi[i] + g.szi[k], A, B);
-            const int o = k * pitch + i;
-            float out = A * a.p_in[o] + d;
-            if (a.yp && a.n >= 1) {
-                const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
-                const int jl = i - a.rec.i0;
-                if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                    out += w * (float)a.yp[(size_t)(a.n - 1) * a.rec.n + jl];
-            }
-            a.p_out[o] = out;
-        }
+template <int R, int TX, int TZ>
+__global__ void __launch_bounds__(kThreads) k_fwd_persist(FwdArgs a, const PersistArgs pa) {
+    __shared__ TileSmem<R, TX, TZ> sm;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const int tile = blockIdx.x;
+    const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
+    for (int n = 0; n < pa.nt; n++) {
+        if (n > 0 && !wait_neighbours(pa, tile, (unsigned)n, &s_abort)) return;
+        const int bi = n & 1, bo = bi ^ 1;
+        a.p_in = pa.f[bi][0];
+        a.vx_in = pa.f[bi][1];
+        a.vz_in = pa.f[bi][2];
+        a.p_out = pa.f[bo][0];
+        a.vx_out = pa.f[bo][1];
+        a.vz_out = pa.f[bo][2];
+        a.n = n;
+        fwd_tile<R, TX, TZ>(a, i0, k0, sm);
+        publish(pa, tile, (unsigned)(n + 1));
+    }
+}
+
+template <int R, int TX, int TZ>
+__global__ void __launch_bounds__(kThreads) k_adj_persist(AdjArgs a, const PersistArgs pa) {
+    __shared__ TileSmem<R, TX, TZ> sm;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const int tile = blockIdx.x;
+    const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
+    for (int t = 0; t < pa.nt; t++) {
+        if (t > 0 && !wait_neighbours(pa, tile, (unsigned)t, &s_abort)) return;
+        const int bi = t & 1, bo = bi ^ 1;
+        a.p_in = pa.f[bi][0];
+        a.vx_in = pa.f[bi][1];
+        a.vz_in = pa.f[bi][2];
+        a.p_out = pa.f[bo][0];
+        a.vx_out = pa.f[bo][1];
+        a.vz_out = pa.f[bo][2];
+        a.n = pa.nt - 1 - t;
+        adj_tile<R, TX, TZ>(a, i0, k0, sm);
+        publish(pa, tile, (unsigned)(t + 1));
     }
 }
 
@@ -333,6 +491,22 @@ __global__ void k_vmax(const float *v, int n, float *out) {
 
 constexpr int kTX = 64, kTZ = 16;
 static_assert(kTX <= TILE_X_MAX && kTZ <= TILE_Z_MAX, "tile larger than the allocation rounding");
+static_assert(kTX >= 2 * kMaxR && kTZ >= 2 * kMaxR, "halo must not reach past the edge neighbours");
+
+template <int R>
+void *fwd_persist_fn() { return (void *)k_fwd_persist<R, kTX, kTZ>; }
+template <int R>
+void *adj_persist_fn() { return (void *)k_adj_persist<R, kTX, kTZ>; }
+
+void *persist_fn(int R, bool adj) {
+    switch (R) {
+        case 1: return adj ? adj_persist_fn<1>() : fwd_persist_fn<1>();
+        case 2: return adj ? adj_persist_fn<2>() : fwd_persist_fn<2>();
+        case 3: return adj ? adj_persist_fn<3>() : fwd_persist_fn<3>();
+        case 4: return adj ? adj_persist_fn<4>() : fwd_persist_fn<4>();
+        default: return nullptr;
+    }
+}
 
 }  // namespace
 
@@ -340,6 +514,37 @@ void tile_shape(int R, int *tx, int *tz) {
     (void)R;
     *tx = kTX;
     *tz = kTZ;
+}
+
+int persist_capacity(int R, bool adj) {
+    void *fn = persist_fn(R, adj);
+    if (!fn) return 0;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, cudaStream_t s) {
+    void *fn = persist_fn(R, false);
+    if (!fn) return cudaErrorInvalidValue;
+    FwdArgs aa = a;
+    PersistArgs pp = pa;
+    void *args[] = {&aa, &pp};
+    return cudaLaunchCooperativeKernel(fn, dim3(pa.tiles_x * pa.tiles_z), dim3(kThreads), args, 0, s);
+}
+
+cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, cudaStream_t s) {
+    void *fn = persist_fn(R, true);
+    if (!fn) return cudaErrorInvalidValue;
+    AdjArgs aa = a;
+    PersistArgs pp = pa;
+    void *args[] = {&aa, &pp};
+    return cudaLaunchCooperativeKernel(fn, dim3(pa.tiles_x * pa.tiles_z), dim3(kThreads), args, 0, s);
 }
 
 cudaError_t launch_fwd_step(const FwdArgs &a, int R, cudaStream_t s) {

@@ -19,6 +19,7 @@ SSX_OK = 0
 STATUS = {0: "SSX_OK", 1: "SSX_ERR_ARG", 2: "SSX_ERR_CUDA", 3: "SSX_ERR_CFL", 4: "SSX_ERR_OOM",
           5: "SSX_ERR_BREAKDOWN", 6: "SSX_ERR_NONFINITE", 7: "SSX_ERR_NOT_CONVERGED"}
 MODE_PCG, MODE_CG = 0, 1
+SWEEP_AUTO, SWEEP_STEP, SWEEP_PERSISTENT, SWEEP_TEST_STALL = 0, 1, 2, 3
 W_D, W_M, W_M_INV = 0, 1, 2
 
 # every symbol the header declares, in declaration order
@@ -26,7 +27,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_velocity_model", "ssx_set_geometry", "ssx_forward", "ssx_adjoint",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
-           "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc"]
+           "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode"]
 
 
 class SSXError(RuntimeError):
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_get_stats": ([vp, P(Stats)], i),
         "ssx_reset_stats": ([vp], i),
         "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
+        "ssx_set_sweep_mode": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -219,6 +221,9 @@ class Context:
         self._check(self._lib.ssx_point_source_data(self._c, float(x_d), float(z_d), w,
                                                     self._rec(out, "d")))
         return out
+
+    def set_sweep_mode(self, mode: int):
+        self._check(self._lib.ssx_set_sweep_mode(self._c, int(mode)))
 
     # -- instrumentation ------------------------------------------------------
     def set_timing(self, on: bool):

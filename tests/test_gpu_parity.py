@@ -246,3 +246,35 @@ def test_stream_ordering_with_torch_stream(ssx, oracle):
     s.synchronize()
     P = oracle.Problem(spec, W.velocity(spec))
     assert rel(d2, P.S(h.cpu().numpy())) <= TOL
+
+
+# ------------------------------------------------------------ sweep forms --
+@pytest.mark.parametrize("spec_name", ["small", "c2"])
+def test_persistent_and_per_step_sweeps_agree(ssx, spec_name):
+    """The cooperative whole-sweep launch and the per-step graph replay run the
+    same per-tile arithmetic: identical results."""
+    spec = frac_spec(8) if spec_name == "small" else W.c2()
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 16))
+    y = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 17))
+    out = {}
+    for mode in (ssx.SWEEP_PERSISTENT, ssx.SWEEP_STEP):
+        ctx.set_sweep_mode(mode)
+        out[mode] = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
+                     ctx.weight_apply(ssx.W_M_INV, x).clone())
+    for a, b in zip(out[ssx.SWEEP_PERSISTENT], out[ssx.SWEEP_STEP]):
+        assert torch.equal(a, b)
+
+
+def test_persistent_wait_timeout_is_reported_and_context_survives(ssx, oracle):
+    """A neighbour wait that nothing satisfies runs out (0.2 s), the call
+    returns SSX_ERR_CUDA, and the next call on the same context is correct."""
+    spec = W.small(order=4, nt=200)
+    ctx, P = make(ssx, oracle, spec)
+    ctx.set_sweep_mode(ssx.SWEEP_PERSISTENT)
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 18)
+    ctx.set_sweep_mode(ssx.SWEEP_TEST_STALL)
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.forward(dev(h))
+    assert e.value.code == 2 and "timed out" in e.value.msg
+    assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
