@@ -305,6 +305,30 @@ class Problem:
         hb, _ = simulate_adj(g, self.nt, pl, dl, yp=tv, yv=tp, want_h=True, want_f=False)
         return -1.0 * self.sgn * hb
 
+    # -- unsymmetrised pressure-to-source and time-reversal inverse ---------
+    def lambda_tilde(self, r, transpose=False):
+        """eqn:lamtilde: Lambda~ = -8 (V+_{zs,zs+dz})^T Pi_0 S+ Pi_1^T r (velocity
+        injection of r on the plane, the pressure trace at the datum taken back
+        through V^T); with transpose=True eqn:lamtransp:
+        Lambda~^T = -8 Pi_1 S^T Pi_0^T V r (the v_z trace at the datum taken
+        back through the pressure-trace adjoint)."""
+        s, slab = self.spec, self.slab_s
+        g = slab.grid
+        pl, dl = g.line(slab.z0, s.ix_line0, s.n_line), g.line(slab.zd, s.ix_line0, s.n_line)
+        tp, tv = simulate(g, self.nt, pl, dl, f=r, want_p=True, want_v=True)
+        if transpose:
+            _, fb = simulate_adj(g, self.nt, pl, dl, yp=tv, want_h=False, want_f=True)
+        else:
+            _, fb = simulate_adj(g, self.nt, pl, dl, yv=tp, want_h=False, want_f=True)
+        return -8.0 * self.sgn * fb
+
+    def time_reversal_inverse(self, d):
+        """eqn:approxinv: h ~ 4 (V+_{zs,zr})^T d -- the data injected as a
+        vertical load at the receivers, propagated back in time, the v_z
+        response read on the source line."""
+        _, fb = simulate_adj(self.g, self.nt, self.src, self.rec, yv=d, want_h=False, want_f=True)
+        return 4.0 * fb
+
     # -- penalty and normal operator ---------------------------------------
     def A(self, h):
         return h * self.dist[None, :]

@@ -186,6 +186,12 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     a.szi = G.tab + 2 * L.NX;
     a.szh = G.tab + 2 * L.NX + L.NZ;
     for (int m = 0; m < kMaxR; m++) a.c[m] = kWeights[c->R][m];
+    // sigma vanishes at integer positions nsp .. nsp+n-1 and half positions
+    // nsp .. nsp+n-2; v points are valid up to NX-2 / NZ-2
+    a.in_x0 = nsp;
+    a.in_x1 = nsp + nx - 1;
+    a.in_z0 = nsp;
+    a.in_z1 = nsp + nz - 1;
     G.ready = false;
     return SSX_OK;
 }

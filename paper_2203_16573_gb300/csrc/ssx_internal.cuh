@@ -48,6 +48,8 @@ struct GridArgs {
     const float *szi, *szh; // sigma dt/2 at z = k h and (k+1/2) h, [NZ]
     float cv;               // dt / (rho h)
     float c[kMaxR];         // staggered weights c_1..c_k
+    int in_x0, in_x1;       // [in_x0, in_x1) x: every sponge factor is exactly 1
+    int in_z0, in_z1;       // same in z (integer and half positions)
 };
 
 struct FwdArgs {

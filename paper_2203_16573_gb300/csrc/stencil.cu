@@ -28,14 +28,11 @@ namespace ssx {
 
 namespace {
 
+// Sponge factors of a point with s = (sigma_x + sigma_z) dt/2:
+// B = 1/(1+s) (correctly rounded) and A = (1-s)/(1+s) = 2B - 1.
 __device__ __forceinline__ void damp(float s, float &A, float &B) {
-    if (s == 0.0f) {
-        A = 1.0f;
-        B = 1.0f;
-    } else {
-        B = 1.0f / (1.0f + s);
-        A = (1.0f - s) * B;
-    }
+    B = __frcp_rn(1.0f + s);
+    A = fmaf(2.0f, B, -1.0f);
 }
 
 __device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
@@ -43,6 +40,7 @@ __device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
 }
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 
 // Field loads go through L2 only (ld.global.cg): in the persistent sweep a
 // neighbour CTA rewrote these lines during the previous step, and L1 is not
@@ -59,83 +57,130 @@ struct TileSmem {
     float svz[VZH][TX];    // v_z^{n+1/2} (forward) or C_vz vbar_z' (transpose)
 };
 
-// Thread layout for the tile loops: 8 warps; a warp walks a row, the warps
-// walk rows (no integer division in the loops).
-#define TILE_LANE (threadIdx.x & 31)
-#define TILE_WARP (threadIdx.x >> 5)
+// The field buffers and step index of one step (kept in registers).
+struct StepIO {
+    const float *p_in, *vx_in, *vz_in;
+    float *p_out, *vx_out, *vz_out;
+    int n;
+};
+
+// A tile is "interior" when its whole 2k-wide neighbourhood lies where every
+// sponge factor is exactly 1 and every staggered point is valid: there the
+// update needs neither damping factors nor bounds tests, and gives the same
+// bits as the general path.
+template <int R, int TX, int TZ>
+__device__ __forceinline__ bool interior_tile(const GridArgs &g, int i0, int k0) {
+    return i0 - 2 * R >= g.in_x0 && i0 + TX + 2 * R <= g.in_x1 && k0 - 2 * R >= g.in_z0 &&
+           k0 + TZ + 2 * R <= g.in_z1;
+}
+
+// Loops over the shared-memory regions: warp w takes rows w, w+8, ...; lanes
+// take columns lane, lane+32, ... (trip counts are compile-time constants).
+#define FOR_ROWS(r, n) for (int r = wy; r < (n); r += kWarps)
+#define FOR_COLS(c, n) _Pragma("unroll") for (int c##_u = 0; c##_u < ((n) + 31) / 32; c##_u++) \
+    if (const int c = lane + 32 * c##_u; c < (n))
+
+// Stage a field over tile + 2k halo (corners are never used and not loaded);
+// with PRE the staged value is C_p * field (transpose step).
+template <int R, int TX, int TZ, bool SP, bool PRE>
+__device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i0, int k0,
+                                        float (&sp)[TZ + 4 * R][TX + 4 * R]) {
+    constexpr int H = 2 * R, PW = TX + 2 * H;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int pitch = g.pitch;
+    auto val = [&](int k, int i) -> float {
+        const int o = k * pitch + i;
+        if (!PRE) return ldf(f + o);
+        if (!SP) return __ldg(g.kap + o) * ldf(f + o);
+        if (k < 0 || k >= g.NZ || i < 0 || i >= g.NX) return 0.0f;
+        float A, B;
+        damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+        return (B * __ldg(g.kap + o)) * ldf(f + o);
+    };
+    // tile rows with the x halo
+    FOR_ROWS(r, TZ) {
+        FOR_COLS(c, PW) { sp[r + H][c] = val(k0 + r, i0 - H + c); }
+    }
+    // z halo rows, tile columns
+    FOR_ROWS(r, 2 * H) {
+        const int rr = r < H ? r : r + TZ;
+        FOR_COLS(c, TX) { sp[rr][c + H] = val(k0 - H + rr, i0 + c); }
+    }
+}
 
 // One forward step on the TX x TZ tile at (i0, k0).
-template <int R, int TX, int TZ>
-__device__ __forceinline__ void fwd_tile(const FwdArgs &a, int i0, int k0,
-                                         TileSmem<R, TX, TZ> &sm) {
+template <int R, int TX, int TZ, bool SP>
+__device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                              TileSmem<R, TX, TZ> &sm) {
     using S = TileSmem<R, TX, TZ>;
-    constexpr int H = S::H, PW = S::PW, PH = S::PH, VXW = S::VXW, VZH = S::VZH;
+    constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
-    const int lane = TILE_LANE, wy = TILE_WARP;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = io.n;
 
-    // p^n over the tile and a 2k halo, corners skipped (the apron makes
-    // every read in bounds)
-    for (int r = wy; r < PH; r += 8) {
-        const bool zh = (r < H) || (r >= H + TZ);
-        const float *row = a.p_in + (k0 - H + r) * pitch + (i0 - H);
-        for (int c = lane; c < PW; c += 32) {
-            if (zh && (c < H || c >= H + TX)) continue;
-            sm.sp[r][c] = ldf(row + c);
-        }
-    }
+    stage_p<R, TX, TZ, SP, false>(g, io.p_in, i0, k0, sm.sp);
     __syncthreads();
 
     // v_x^{n+1/2} on the tile rows, columns i0-k .. i0+TX+k-2
-    for (int r = wy; r < TZ; r += 8) {
+    FOR_ROWS(r, TZ) {
         const int k = k0 + r;
-        for (int jj = lane; jj < VXW; jj += 32) {
+        FOR_COLS(jj, VXW) {
             const int j = i0 - R + jj;
             float val = 0.0f;
-            if (k < g.NZ && j >= 0 && j < g.NX - 1) {
+            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
-                for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
-                float A, B;
-                damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
                 const int o = k * pitch + j;
-                val = A * ldf(a.vx_in + o) - (B * g.cv) * d;
-                if (jj >= R && jj < R + TX) a.vx_out[o] = val;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                    val = A * ldf(io.vx_in + o) - (B * g.cv) * d;
+                } else {
+                    val = ldf(io.vx_in + o) - g.cv * d;
+                }
+                if (jj >= R && jj < R + TX) io.vx_out[o] = val;
             }
             sm.svx[r][jj] = val;
         }
     }
     // v_z^{n+1/2} on rows k0-k .. k0+TZ+k-2, the tile columns
-    for (int kk = wy; kk < VZH; kk += 8) {
+    FOR_ROWS(kk, VZH) {
         const int k = k0 - R + kk;
         const bool own = (kk >= R && kk < R + TZ);
-        for (int c = lane; c < TX; c += 32) {
+        FOR_COLS(c, TX) {
             const int i = i0 + c;
             float val = 0.0f;
-            if (i < g.NX && k >= 0 && k < g.NZ - 1) {
+            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
-                    d += g.c[m - 1] * (sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H]);
-                float A, B;
-                damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
                 const int o = k * pitch + i;
-                const float cvz = B * g.cv;
-                val = A * ldf(a.vz_in + o) - cvz * d;
+                float cvz = g.cv;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                    cvz = B * g.cv;
+                    val = A * ldf(io.vz_in + o) - cvz * d;
+                } else {
+                    val = ldf(io.vz_in + o) - cvz * d;
+                }
                 if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
                     const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
                     const int jl = i - a.src.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)a.n * a.src.n + jl];
+                        val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)n * a.src.n + jl];
                 }
                 if (own) {
-                    a.vz_out[o] = val;
+                    io.vz_out[o] = val;
                     if (a.outv) {
                         const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
                         const int jl = i - a.rec.i0;
                         if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                            atomicAdd(&a.outv[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+                            atomicAdd(&a.outv[(size_t)n * a.rec.n + jl], (double)w * (double)val);
                     }
                 }
             }
@@ -145,34 +190,37 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int i0, int k0,
     __syncthreads();
 
     // p^{n+1} on the tile
-    for (int r = wy; r < TZ; r += 8) {
+    FOR_ROWS(r, TZ) {
         const int k = k0 + r;
-        for (int c = lane; c < TX; c += 32) {
+        FOR_COLS(c, TX) {
             const int i = i0 + c;
-            if (k < g.NZ && i < g.NX) {
+            if (!SP || (k < g.NZ && i < g.NX)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) {
-                    d += g.c[m - 1] * (sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m]);
-                    d += g.c[m - 1] * (sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c]);
+                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
-                float A, B;
-                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
                 const int o = k * pitch + i;
-                const float cp = B * __ldg(g.kap + o);
-                float val = A * sm.sp[r + H][c + H] - cp * d;
+                float cp = __ldg(g.kap + o), A = 1.0f;
+                if (SP) {
+                    float B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                    cp *= B;
+                }
+                float val = SP ? A * sm.sp[r + H][c + H] - cp * d : sm.sp[r + H][c + H] - cp * d;
                 if (a.hsrc) {   // constitutive defect h delta(z - z_s)
                     const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
                     const int jl = i - a.src.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)a.n * a.src.n + jl];
+                        val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)n * a.src.n + jl];
                 }
-                a.p_out[o] = val;
+                io.p_out[o] = val;
                 if (a.outp) {
                     const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
                     const int jl = i - a.rec.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        atomicAdd(&a.outp[(size_t)a.n * a.rec.n + jl], (double)w * (double)val);
+                        atomicAdd(&a.outp[(size_t)n * a.rec.n + jl], (double)w * (double)val);
                 }
             }
         }
@@ -180,95 +228,94 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int i0, int k0,
 }
 
 // One transposed step on the tile at (i0, k0).
-template <int R, int TX, int TZ>
-__device__ __forceinline__ void adj_tile(const AdjArgs &a, int i0, int k0,
-                                         TileSmem<R, TX, TZ> &sm) {
+template <int R, int TX, int TZ, bool SP>
+__device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                              TileSmem<R, TX, TZ> &sm) {
     using S = TileSmem<R, TX, TZ>;
-    constexpr int H = S::H, PW = S::PW, PH = S::PH, VXW = S::VXW, VZH = S::VZH;
+    constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
-    const int lane = TILE_LANE, wy = TILE_WARP;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = io.n;
 
-    // q = C_p pbar over tile + 2k halo; read out the transposed p injection
-    for (int r = wy; r < PH; r += 8) {
-        const int k = k0 - H + r;
-        const bool zh = (r < H) || (r >= H + TZ);
-        for (int c = lane; c < PW; c += 32) {
-            if (zh && (c < H || c >= H + TX)) continue;
-            const int i = i0 - H + c;
-            float q = 0.0f;
-            if (k >= 0 && k < g.NZ && i >= 0 && i < g.NX) {
-                float A, B;
-                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
-                const int o = k * pitch + i;
-                q = (B * __ldg(g.kap + o)) * ldf(a.p_in + o);
-                if (a.hbar && !zh && c >= H && c < H + TX) {
-                    const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
-                    const int jl = i - a.src.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        atomicAdd(&a.hbar[(size_t)a.n * a.src.n + jl],
-                                  (double)(w * a.src.scale) * (double)q);
+    // q = C_p pbar over tile + 2k halo
+    stage_p<R, TX, TZ, SP, true>(g, io.p_in, i0, k0, sm.sp);
+    __syncthreads();
+    // transposed pressure injection: hbar[n] = scale * sum_k w_k q (tile only)
+    if (a.hbar) {
+        FOR_ROWS(r, TZ) {
+            const int k = k0 + r;
+            const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+            if (w != 0.0f) {
+                FOR_COLS(c, TX) {
+                    const int i = i0 + c, jl = i - a.src.i0;
+                    if (i < g.NX && jl >= 0 && jl < a.src.n)
+                        atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
+                                  (double)(w * a.src.scale) * (double)sm.sp[r + H][c + H]);
                 }
             }
-            sm.sp[r][c] = q;
         }
     }
-    __syncthreads();
 
     // vbar_x' = vbar_x + D+ q; keep C_vx vbar_x' for the p update
-    for (int r = wy; r < TZ; r += 8) {
+    FOR_ROWS(r, TZ) {
         const int k = k0 + r;
-        for (int jj = lane; jj < VXW; jj += 32) {
+        FOR_COLS(jj, VXW) {
             const int j = i0 - R + jj;
             float val = 0.0f;
-            if (k < g.NZ && j >= 0 && j < g.NX - 1) {
+            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
-                for (int m = 1; m <= R; m++) d += g.c[m - 1] * (row[m] - row[1 - m]);
-                float A, B;
-                damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
                 const int o = k * pitch + j;
-                const float vb = ldf(a.vx_in + o) + d;
-                val = (B * g.cv) * vb;
-                if (jj >= R && jj < R + TX) a.vx_out[o] = A * vb;
+                const float vb = ldf(io.vx_in + o) + d;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                    val = (B * g.cv) * vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[o] = A * vb;
+                } else {
+                    val = g.cv * vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[o] = vb;
+                }
             }
             sm.svx[r][jj] = val;
         }
     }
     // vbar_z' likewise; read out the transposed velocity injection
-    for (int kk = wy; kk < VZH; kk += 8) {
+    FOR_ROWS(kk, VZH) {
         const int k = k0 - R + kk;
         const bool own = (kk >= R && kk < R + TZ);
-        for (int c = lane; c < TX; c += 32) {
+        FOR_COLS(c, TX) {
             const int i = i0 + c;
             float val = 0.0f;
-            if (i < g.NX && k >= 0 && k < g.NZ - 1) {
+            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
-                    d += g.c[m - 1] * (sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H]);
-                float A, B;
-                damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
                 const int o = k * pitch + i;
-                const float vb = ldf(a.vz_in + o) + d;
+                const float vb = ldf(io.vz_in + o) + d;
+                float A = 1.0f, B = 1.0f;
+                if (SP) damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
                 val = (B * g.cv) * vb;
                 if (own) {
                     if (a.fbar) {
                         const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
                         const int jl = i - a.src.i0;
                         if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                            atomicAdd(&a.fbar[(size_t)a.n * a.src.n + jl],
+                            atomicAdd(&a.fbar[(size_t)n * a.src.n + jl],
                                       (double)(w * a.src.scale) * (double)val);
                     }
-                    float out = A * vb;
-                    if (a.yv && a.n >= 1) {   // transposed sampling of step n-1
+                    float out = SP ? A * vb : vb;
+                    if (a.yv && n >= 1) {   // transposed sampling of step n-1
                         const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
                         const int jl = i - a.rec.i0;
                         if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                            out += w * (float)a.yv[(size_t)(a.n - 1) * a.rec.n + jl];
+                            out += w * (float)a.yv[(size_t)(n - 1) * a.rec.n + jl];
                     }
-                    a.vz_out[o] = out;
+                    io.vz_out[o] = out;
                 }
             }
             sm.svz[kk][c] = val;
@@ -277,43 +324,68 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, int i0, int k0,
     __syncthreads();
 
     // pbar <- A_p pbar + D- (C_v vbar')
-    for (int r = wy; r < TZ; r += 8) {
+    FOR_ROWS(r, TZ) {
         const int k = k0 + r;
-        for (int c = lane; c < TX; c += 32) {
+        FOR_COLS(c, TX) {
             const int i = i0 + c;
-            if (k < g.NZ && i < g.NX) {
+            if (!SP || (k < g.NZ && i < g.NX)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) {
-                    d += g.c[m - 1] * (sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m]);
-                    d += g.c[m - 1] * (sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c]);
+                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
-                float A, B;
-                damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
                 const int o = k * pitch + i;
-                float out = A * ldf(a.p_in + o) + d;
-                if (a.yp && a.n >= 1) {
+                float out;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                    out = A * ldf(io.p_in + o) + d;
+                } else {
+                    out = ldf(io.p_in + o) + d;
+                }
+                if (a.yp && n >= 1) {
                     const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
                     const int jl = i - a.rec.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        out += w * (float)a.yp[(size_t)(a.n - 1) * a.rec.n + jl];
+                        out += w * (float)a.yp[(size_t)(n - 1) * a.rec.n + jl];
                 }
-                a.p_out[o] = out;
+                io.p_out[o] = out;
             }
         }
     }
 }
 
 template <int R, int TX, int TZ>
+__device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
+        fwd_tile_impl<R, TX, TZ, false>(a, io, i0, k0, sm);
+    else
+        fwd_tile_impl<R, TX, TZ, true>(a, io, i0, k0, sm);
+}
+
+template <int R, int TX, int TZ>
+__device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
+        adj_tile_impl<R, TX, TZ, false>(a, io, i0, k0, sm);
+    else
+        adj_tile_impl<R, TX, TZ, true>(a, io, i0, k0, sm);
+}
+
+template <int R, int TX, int TZ>
 __global__ void __launch_bounds__(kThreads) k_fwd(const FwdArgs a) {
     __shared__ TileSmem<R, TX, TZ> sm;
-    fwd_tile<R, TX, TZ>(a, blockIdx.x * TX, blockIdx.y * TZ, sm);
+    const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
+    fwd_tile<R, TX, TZ>(a, io, blockIdx.x * TX, blockIdx.y * TZ, sm);
 }
 
 template <int R, int TX, int TZ>
 __global__ void __launch_bounds__(kThreads) k_adj(const AdjArgs a) {
     __shared__ TileSmem<R, TX, TZ> sm;
-    adj_tile<R, TX, TZ>(a, blockIdx.x * TX, blockIdx.y * TZ, sm);
+    const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
+    adj_tile<R, TX, TZ>(a, io, blockIdx.x * TX, blockIdx.y * TZ, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,8 +453,22 @@ __device__ __forceinline__ void publish(const PersistArgs &pa, int tile, unsigne
     }
 }
 
+// step io of a ping-pong sweep: even steps read buffer 0, odd steps buffer 1
+__device__ __forceinline__ StepIO ping_pong(const PersistArgs &pa, int t, int n) {
+    const bool odd = t & 1;
+    StepIO io;
+    io.p_in = odd ? pa.f[1][0] : pa.f[0][0];
+    io.vx_in = odd ? pa.f[1][1] : pa.f[0][1];
+    io.vz_in = odd ? pa.f[1][2] : pa.f[0][2];
+    io.p_out = odd ? pa.f[0][0] : pa.f[1][0];
+    io.vx_out = odd ? pa.f[0][1] : pa.f[1][1];
+    io.vz_out = odd ? pa.f[0][2] : pa.f[1][2];
+    io.n = n;
+    return io;
+}
+
 template <int R, int TX, int TZ>
-__global__ void __launch_bounds__(kThreads) k_fwd_persist(FwdArgs a, const PersistArgs pa) {
+__global__ void __launch_bounds__(kThreads) k_fwd_persist(const FwdArgs a, const PersistArgs pa) {
     __shared__ TileSmem<R, TX, TZ> sm;
     __shared__ int s_abort;
     if (threadIdx.x == 0) s_abort = 0;
@@ -391,21 +477,13 @@ __global__ void __launch_bounds__(kThreads) k_fwd_persist(FwdArgs a, const Persi
     const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
     for (int n = 0; n < pa.nt; n++) {
         if (n > 0 && !wait_neighbours(pa, tile, (unsigned)n, &s_abort)) return;
-        const int bi = n & 1, bo = bi ^ 1;
-        a.p_in = pa.f[bi][0];
-        a.vx_in = pa.f[bi][1];
-        a.vz_in = pa.f[bi][2];
-        a.p_out = pa.f[bo][0];
-        a.vx_out = pa.f[bo][1];
-        a.vz_out = pa.f[bo][2];
-        a.n = n;
-        fwd_tile<R, TX, TZ>(a, i0, k0, sm);
+        fwd_tile<R, TX, TZ>(a, ping_pong(pa, n, n), i0, k0, sm);
         publish(pa, tile, (unsigned)(n + 1));
     }
 }
 
 template <int R, int TX, int TZ>
-__global__ void __launch_bounds__(kThreads) k_adj_persist(AdjArgs a, const PersistArgs pa) {
+__global__ void __launch_bounds__(kThreads) k_adj_persist(const AdjArgs a, const PersistArgs pa) {
     __shared__ TileSmem<R, TX, TZ> sm;
     __shared__ int s_abort;
     if (threadIdx.x == 0) s_abort = 0;
@@ -414,15 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_persist(AdjArgs a, const Persi
     const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
     for (int t = 0; t < pa.nt; t++) {
         if (t > 0 && !wait_neighbours(pa, tile, (unsigned)t, &s_abort)) return;
-        const int bi = t & 1, bo = bi ^ 1;
-        a.p_in = pa.f[bi][0];
-        a.vx_in = pa.f[bi][1];
-        a.vz_in = pa.f[bi][2];
-        a.p_out = pa.f[bo][0];
-        a.vx_out = pa.f[bo][1];
-        a.vz_out = pa.f[bo][2];
-        a.n = pa.nt - 1 - t;
-        adj_tile<R, TX, TZ>(a, i0, k0, sm);
+        adj_tile<R, TX, TZ>(a, ping_pong(pa, t, pa.nt - 1 - t), i0, k0, sm);
         publish(pa, tile, (unsigned)(t + 1));
     }
 }

@@ -254,6 +254,31 @@ def test_weight_quadratic_form_identity(oracle):
     assert abs(s.dz_datum - _golden_constants()["thin_slab_dz_km"]) < 1e-15
 
 
+def test_symmetrised_lambda_tilde_is_Wminv(oracle):
+    """eqn:winvcomp is the mean of eqn:lamtilde and eqn:lamtransp:
+    (Lambda~ + Lambda~^T)/2 = W~_m^{-1} to rounding; Lambda~ and Lambda~^T are
+    transposes of each other."""
+    s = W.small(order=4, nt=150)
+    P = oracle.Problem(s, W.velocity(s))
+    a, b = W.random_gather(s.nt, s.n_line, 31), W.random_gather(s.nt, s.n_line, 32)
+    sym = 0.5 * (P.lambda_tilde(a) + P.lambda_tilde(a, transpose=True))
+    ref = P.Wminv(a)
+    assert np.abs(sym - ref).max() <= 1e-12 * np.abs(ref).max()
+    x, y = np.sum(b * P.lambda_tilde(a)), np.sum(a * P.lambda_tilde(b, transpose=True))
+    assert abs(x - y) <= 1e-12 * abs(x)
+    assert _golden_constants()["lamtilde_prefactor"] == -8
+
+
+def test_lambda_tilde_maps_pressure_trace_to_source(oracle, plane_problem):
+    """eqn:tracejump10 / eqn:lamnear: for a plane wave the pressure-to-source
+    map is multiplication by 2/Z (asymptotically symmetric, so Lambda~ and
+    Lambda~^T agree)."""
+    s, P, x, mid = plane_problem
+    Z = s.rho * s.v0
+    for tr in (False, True):
+        assert 0.85 * 2 / Z < _ratio(P.lambda_tilde(x, transpose=tr), x, mid) < 1.05 * 2 / Z
+
+
 @pytest.mark.parametrize("which", ["Wminv", "Wm", "Wd"])
 def test_weights_symmetric(oracle, which):
     """Symmetrised thin-slab weights are symmetric to rounding (eqn:winvcomp,
