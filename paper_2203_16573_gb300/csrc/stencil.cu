@@ -108,65 +108,110 @@ __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i
     }
 }
 
-// One forward step on the TX x TZ tile at (i0, k0).
+// Per-thread point sets of a tile (compile-time counts): warp w owns rows
+// w, w+8, ..; lane l owns columns l, l+32, ...
+template <int R, int TX, int TZ>
+struct TileShape {
+    static constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
+    static constexpr int NRT = (TZ + kWarps - 1) / kWarps;    // tile rows per thread
+    static constexpr int NRV = (VZH + kWarps - 1) / kWarps;   // v_z rows per thread
+    static constexpr int NCT = (TX + 31) / 32;                // tile columns per thread
+    static constexpr int NCX = (VXW + 31) / 32;               // v_x columns per thread
+};
+
+// One forward step on the TX x TZ tile at (i0, k0). Every global operand of
+// the step is loaded in one batch at the start (p into shared memory, v and
+// kappa into registers) so the step pays one memory latency, not one per loop
+// iteration.
 template <int R, int TX, int TZ, bool SP>
 __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io, int i0, int k0,
                                               TileSmem<R, TX, TZ> &sm) {
     using S = TileSmem<R, TX, TZ>;
+    using T = TileShape<R, TX, TZ>;
     constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int n = io.n;
 
+    float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rk[T::NRT][T::NCT];
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            const int k = k0 + r, j = i0 - R + jj;
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            rk[a_][b] = ok ? __ldg(g.kap + (k0 + r) * pitch + i0 + c) : 0.0f;
+        }
     stage_p<R, TX, TZ, SP, false>(g, io.p_in, i0, k0, sm.sp);
     __syncthreads();
 
     // v_x^{n+1/2} on the tile rows, columns i0-k .. i0+TX+k-2
-    FOR_ROWS(r, TZ) {
-        const int k = k0 + r;
-        FOR_COLS(jj, VXW) {
-            const int j = i0 - R + jj;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            if (r >= TZ || jj >= VXW) continue;
+            const int k = k0 + r, j = i0 - R + jj;
             float val = 0.0f;
             if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
-                const int o = k * pitch + j;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
-                    val = A * ldf(io.vx_in + o) - (B * g.cv) * d;
+                    val = A * rvx[a_][b] - (B * g.cv) * d;
                 } else {
-                    val = ldf(io.vx_in + o) - g.cv * d;
+                    val = rvx[a_][b] - g.cv * d;
                 }
-                if (jj >= R && jj < R + TX) io.vx_out[o] = val;
+                if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = val;
             }
             sm.svx[r][jj] = val;
         }
-    }
     // v_z^{n+1/2} on rows k0-k .. k0+TZ+k-2, the tile columns
-    FOR_ROWS(kk, VZH) {
-        const int k = k0 - R + kk;
-        const bool own = (kk >= R && kk < R + TZ);
-        FOR_COLS(c, TX) {
-            const int i = i0 + c;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            if (kk >= VZH || c >= TX) continue;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool own = (kk >= R && kk < R + TZ);
             float val = 0.0f;
             if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
                     d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
-                const int o = k * pitch + i;
                 float cvz = g.cv;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
                     cvz = B * g.cv;
-                    val = A * ldf(io.vz_in + o) - cvz * d;
+                    val = A * rvz[a_][b] - cvz * d;
                 } else {
-                    val = ldf(io.vz_in + o) - cvz * d;
+                    val = rvz[a_][b] - cvz * d;
                 }
                 if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
                     const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
@@ -175,7 +220,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                         val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)n * a.src.n + jl];
                 }
                 if (own) {
-                    io.vz_out[o] = val;
+                    io.vz_out[k * pitch + i] = val;
                     if (a.outv) {
                         const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
                         const int jl = i - a.rec.i0;
@@ -186,14 +231,16 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
             }
             sm.svz[kk][c] = val;
         }
-    }
     __syncthreads();
 
     // p^{n+1} on the tile
-    FOR_ROWS(r, TZ) {
-        const int k = k0 + r;
-        FOR_COLS(c, TX) {
-            const int i = i0 + c;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            if (r >= TZ || c >= TX) continue;
+            const int k = k0 + r, i = i0 + c;
             if (!SP || (k < g.NZ && i < g.NX)) {
                 float d = 0.0f;
 #pragma unroll
@@ -201,8 +248,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                     d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
                     d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
-                const int o = k * pitch + i;
-                float cp = __ldg(g.kap + o), A = 1.0f;
+                float cp = rk[a_][b], A = 1.0f;
                 if (SP) {
                     float B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
@@ -215,7 +261,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                     if (w != 0.0f && jl >= 0 && jl < a.src.n)
                         val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)n * a.src.n + jl];
                 }
-                io.p_out[o] = val;
+                io.p_out[k * pitch + i] = val;
                 if (a.outp) {
                     const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
                     const int jl = i - a.rec.i0;
@@ -224,32 +270,63 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                 }
             }
         }
-    }
 }
 
-// One transposed step on the tile at (i0, k0).
+// One transposed step on the tile at (i0, k0) (same batching of loads).
 template <int R, int TX, int TZ, bool SP>
 __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io, int i0, int k0,
                                               TileSmem<R, TX, TZ> &sm) {
     using S = TileSmem<R, TX, TZ>;
+    using T = TileShape<R, TX, TZ>;
     constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int n = io.n;
 
+    float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rp[T::NRT][T::NCT];
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            const int k = k0 + r, j = i0 - R + jj;
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            rp[a_][b] = ok ? ldf(io.p_in + (k0 + r) * pitch + i0 + c) : 0.0f;
+        }
     // q = C_p pbar over tile + 2k halo
     stage_p<R, TX, TZ, SP, true>(g, io.p_in, i0, k0, sm.sp);
     __syncthreads();
     // transposed pressure injection: hbar[n] = scale * sum_k w_k q (tile only)
     if (a.hbar) {
-        FOR_ROWS(r, TZ) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRT; a_++) {
+            const int r = wy + kWarps * a_;
             const int k = k0 + r;
-            const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+            const float w = r < TZ ? row_weight(k, a.src.kp, a.src.wp0, a.src.wp1) : 0.0f;
             if (w != 0.0f) {
-                FOR_COLS(c, TX) {
+#pragma unroll
+                for (int b = 0; b < T::NCT; b++) {
+                    const int c = lane + 32 * b;
                     const int i = i0 + c, jl = i - a.src.i0;
-                    if (i < g.NX && jl >= 0 && jl < a.src.n)
+                    if (c < TX && i < g.NX && jl >= 0 && jl < a.src.n)
                         atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
                                   (double)(w * a.src.scale) * (double)sm.sp[r + H][c + H]);
                 }
@@ -258,45 +335,48 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
     }
 
     // vbar_x' = vbar_x + D+ q; keep C_vx vbar_x' for the p update
-    FOR_ROWS(r, TZ) {
-        const int k = k0 + r;
-        FOR_COLS(jj, VXW) {
-            const int j = i0 - R + jj;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            if (r >= TZ || jj >= VXW) continue;
+            const int k = k0 + r, j = i0 - R + jj;
             float val = 0.0f;
             if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
-                const int o = k * pitch + j;
-                const float vb = ldf(io.vx_in + o) + d;
+                const float vb = rvx[a_][b] + d;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
                     val = (B * g.cv) * vb;
-                    if (jj >= R && jj < R + TX) io.vx_out[o] = A * vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = A * vb;
                 } else {
                     val = g.cv * vb;
-                    if (jj >= R && jj < R + TX) io.vx_out[o] = vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = vb;
                 }
             }
             sm.svx[r][jj] = val;
         }
-    }
     // vbar_z' likewise; read out the transposed velocity injection
-    FOR_ROWS(kk, VZH) {
-        const int k = k0 - R + kk;
-        const bool own = (kk >= R && kk < R + TZ);
-        FOR_COLS(c, TX) {
-            const int i = i0 + c;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            if (kk >= VZH || c >= TX) continue;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool own = (kk >= R && kk < R + TZ);
             float val = 0.0f;
             if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
                     d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
-                const int o = k * pitch + i;
-                const float vb = ldf(io.vz_in + o) + d;
+                const float vb = rvz[a_][b] + d;
                 float A = 1.0f, B = 1.0f;
                 if (SP) damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
                 val = (B * g.cv) * vb;
@@ -315,19 +395,21 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                         if (w != 0.0f && jl >= 0 && jl < a.rec.n)
                             out += w * (float)a.yv[(size_t)(n - 1) * a.rec.n + jl];
                     }
-                    io.vz_out[o] = out;
+                    io.vz_out[k * pitch + i] = out;
                 }
             }
             sm.svz[kk][c] = val;
         }
-    }
     __syncthreads();
 
     // pbar <- A_p pbar + D- (C_v vbar')
-    FOR_ROWS(r, TZ) {
-        const int k = k0 + r;
-        FOR_COLS(c, TX) {
-            const int i = i0 + c;
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            if (r >= TZ || c >= TX) continue;
+            const int k = k0 + r, i = i0 + c;
             if (!SP || (k < g.NZ && i < g.NX)) {
                 float d = 0.0f;
 #pragma unroll
@@ -335,14 +417,13 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                     d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
                     d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
-                const int o = k * pitch + i;
                 float out;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
-                    out = A * ldf(io.p_in + o) + d;
+                    out = A * rp[a_][b] + d;
                 } else {
-                    out = ldf(io.p_in + o) + d;
+                    out = rp[a_][b] + d;
                 }
                 if (a.yp && n >= 1) {
                     const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
@@ -350,10 +431,9 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                     if (w != 0.0f && jl >= 0 && jl < a.rec.n)
                         out += w * (float)a.yp[(size_t)(n - 1) * a.rec.n + jl];
                 }
-                io.p_out[o] = out;
+                io.p_out[k * pitch + i] = out;
             }
         }
-    }
 }
 
 template <int R, int TX, int TZ>
