@@ -95,6 +95,9 @@ typedef struct {
     double sweep_ms;             /* event-timed device time of the sweeps (timing mode)    */
     long long timed_steps;       /* step-kernel launches inside timed sweeps               */
     double timed_point_updates;  /* grid-point steps inside timed sweeps                   */
+    int tile_cfg[6];             /* chosen configuration of the full grid, z_s slab, z_r slab
+                                    (forward, adjoint each): cfg + 16 if the sweep is one
+                                    cooperative launch, -1 if not chosen yet               */
 } ssx_stats;
 
 /* Version string of the library. */
@@ -180,6 +183,13 @@ int ssx_point_source_data(ssx_ctx *ctx, double x_d, double z_d,
  *   0.2 s, so the timeout path can be exercised without a fault. */
 enum { SSX_SWEEP_AUTO = 0, SSX_SWEEP_STEP = 1, SSX_SWEEP_PERSISTENT = 2, SSX_SWEEP_TEST_STALL = 3 };
 int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
+
+/* Tile configuration of the step kernels: -1 (default) lets the library time
+ * every configuration on each grid's first sweep in each direction and keep
+ * the fastest; 0..7 fixes one (tile 64x16/256 threads, 64x16/512, 64x16/1024,
+ * 64x32/512, 64x32/1024, 128x16/512, 128x32/1024, 32x16/256). All
+ * configurations compute identical results. */
+int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
 
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the
  * launching stream; ssx_get_stats then reports their summed device time. */

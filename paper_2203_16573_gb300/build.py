@@ -13,7 +13,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libssx.so")
-SOURCES = ["stencil.cu", "krylov.cu", "runtime.cu", "noalloc.cu"]
+SOURCES = ["stencil.cu", "stencil_r1.cu", "stencil_r2.cu", "stencil_r3.cu", "stencil_r4.cu",
+           "krylov.cu", "runtime.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

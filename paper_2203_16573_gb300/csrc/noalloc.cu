@@ -172,6 +172,10 @@ extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc 
     g.szh = tabs + 2 * L.NX + L.NZ;
     g.cv = (float)(gd->dt / (rho * gd->h));
     for (int m = 0; m < kMaxR; m++) g.c[m] = kW[R][m];
+    g.in_x0 = nsp;
+    g.in_x1 = nsp + gd->nx - 1;
+    g.in_z0 = nsp;
+    g.in_z1 = nsp + gd->nz - 1;
     a.src = src;
     a.hsrc = h_dev;
     a.fsrc = nullptr;
@@ -190,7 +194,7 @@ extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc 
         a.vx_out = f[bo][1];
         a.vz_out = f[bo][2];
         a.n = n;
-        if (launch_fwd_step(a, R, s) != cudaSuccess) return SSX_ERR_CUDA;
+        if (launch_fwd_step(a, R, 0, s, false) != cudaSuccess) return SSX_ERR_CUDA;
     }
     return SSX_OK;
 }

@@ -59,7 +59,8 @@ struct DGrid {
     float *kap = nullptr;
     float *f[2][3] = {};      // origin-offset field pointers
     unsigned *flags = nullptr;  // per-tile step counters of the persistent sweep
-    int tiles_x = 0, tiles_z = 0;
+    int cfg[2] = {-1, -1};      // tile configuration per direction (fwd, adj), -1: not tuned
+    bool pers[2] = {false, false};  // whole-sweep cooperative launch per direction
     GridArgs args{};
     bool ready = false;
 };
@@ -111,7 +112,8 @@ struct ssx_ctx {
 
     int *d_err = nullptr;      // persistent-sweep wait timeout flag (device)
     int sweep_mode = SSX_SWEEP_AUTO;
-    int cap_fwd = -1, cap_adj = -1;   // co-resident CTAs of the persistent kernels
+    int cap[kNumTileCfgs][2];         // co-resident CTAs of the persistent kernels (-1: unknown)
+    int forced_cfg = -1;              // tile configuration fixed by the caller (-1: autotune)
     bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
     bool use_graphs = true;
     std::unordered_map<std::string, cudaGraphExec_t> graphs;
@@ -166,13 +168,16 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     CK(cudaMalloc(&G.mem, 7 * E * sizeof(float)));
     CK(cudaMalloc(&G.tab, 2 * (size_t)(L.NX + L.NZ) * sizeof(float)));
     CK(cudaMemsetAsync(G.mem, 0, 7 * E * sizeof(float), c->s));
-    int tx = 0, tz = 0;
-    tile_shape(c->R, &tx, &tz);
-    G.tiles_x = (L.NX + tx - 1) / tx;
-    G.tiles_z = (L.NZ + tz - 1) / tz;
+    int max_tiles = 0;
+    for (int k = 0; k < kNumTileCfgs; k++) {
+        const int t = ((L.NX + kTileCfgs[k].tx - 1) / kTileCfgs[k].tx) *
+                      ((L.NZ + kTileCfgs[k].tz - 1) / kTileCfgs[k].tz);
+        max_tiles = t > max_tiles ? t : max_tiles;
+    }
     if (G.flags) cudaFree(G.flags);
     G.flags = nullptr;
-    CK(cudaMalloc(&G.flags, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned)));
+    CK(cudaMalloc(&G.flags, (size_t)max_tiles * sizeof(unsigned)));
+    G.cfg[0] = G.cfg[1] = -1;
     G.kap = G.mem + L.origin();
     for (int b = 0; b < 2; b++)
         for (int f = 0; f < 3; f++) G.f[b][f] = G.mem + (1 + 3 * b + f) * E + L.origin();
@@ -205,24 +210,18 @@ void grid_free(DGrid &G) {
     G.flags = nullptr;
 }
 
-// Persistent sweeps need every tile's CTA resident at once (cooperative
-// launch); otherwise a sweep is nt step launches replayed from a CUDA graph.
-int use_persistent(ssx_ctx *c, const DGrid &G, bool adj) {
-    if (c->sweep_mode == SSX_SWEEP_STEP) return 0;
-    int &cap = adj ? c->cap_adj : c->cap_fwd;
-    if (cap < 0) cap = persist_capacity(c->R, adj);
-    const bool fits = G.tiles_x * G.tiles_z <= cap;
-    if (c->sweep_mode == SSX_SWEEP_PERSISTENT && !fits) return -1;
-    return fits ? 1 : 0;
+int tiles_of(const DGrid &G, int cfg) {
+    return ((G.L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx) *
+           ((G.L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz);
 }
 
-PersistArgs persist_args(ssx_ctx *c, const DGrid &G) {
+PersistArgs persist_args(ssx_ctx *c, const DGrid &G, int cfg, int nt) {
     PersistArgs pa{};
     for (int b = 0; b < 2; b++)
         for (int f = 0; f < 3; f++) pa.f[b][f] = G.f[b][f];
-    pa.nt = c->gd.nt;
-    pa.tiles_x = G.tiles_x;
-    pa.tiles_z = G.tiles_z;
+    pa.nt = nt;
+    pa.tiles_x = (G.L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx;
+    pa.tiles_z = (G.L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz;
     pa.flags = G.flags;
     pa.err = c->d_err;
     pa.timeout_ns = 2000000000ull;   // 2 s per neighbour wait
@@ -273,6 +272,18 @@ int make_line(ssx_ctx *c, const DGrid &G, double z, int ix0, int n, double scale
     L.n = n;
     L.scale = (float)scale;
     *out = L;
+    return SSX_OK;
+}
+
+// Reads (and clears) the persistent-sweep timeout flag; synchronises.
+int check_sweeps_quiet(ssx_ctx *c) {
+    int *eh = reinterpret_cast<int *>(c->sc_host + SC_COUNT);
+    CK(cudaMemcpyAsync(eh, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (*eh != 0) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
+        return fail(c, SSX_ERR_CUDA, "a persistent sweep's neighbour wait timed out");
+    }
     return SSX_OK;
 }
 
@@ -328,16 +339,137 @@ std::string ptr_key(const char *tag, const void *a, const void *b, const void *d
     return buf;
 }
 
+// Enqueue the step kernels of a sweep (direction adj) of `nt` steps, in
+// configuration cfg: one cooperative launch (pers) or nt launches chained by
+// programmatic dependent launch. The state starts in buffer 0.
+int enqueue_steps(ssx_ctx *c, DGrid &G, bool adj, int cfg, bool pers, int nt, const FwdArgs &fa,
+                  const AdjArgs &aa, cudaStream_t s) {
+    const int R = c->R;
+    if (pers) {
+        if (adj)
+            CK(launch_adj_persist(aa, persist_args(c, G, cfg, nt), R, cfg, s));
+        else
+            CK(launch_fwd_persist(fa, persist_args(c, G, cfg, nt), R, cfg, s));
+        return SSX_OK;
+    }
+    FwdArgs a = fa;
+    AdjArgs b = aa;
+    for (int t = 0; t < nt; t++) {
+        const int bi = t & 1, bo = bi ^ 1;
+        if (adj) {
+            b.p_in = G.f[bi][0];
+            b.vx_in = G.f[bi][1];
+            b.vz_in = G.f[bi][2];
+            b.p_out = G.f[bo][0];
+            b.vx_out = G.f[bo][1];
+            b.vz_out = G.f[bo][2];
+            b.n = nt - 1 - t;
+            CK(launch_adj_step(b, R, cfg, s, true));
+        } else {
+            a.p_in = G.f[bi][0];
+            a.vx_in = G.f[bi][1];
+            a.vz_in = G.f[bi][2];
+            a.p_out = G.f[bo][0];
+            a.vx_out = G.f[bo][1];
+            a.vz_out = G.f[bo][2];
+            a.n = t;
+            CK(launch_fwd_step(a, R, cfg, s, true));
+        }
+    }
+    return SSX_OK;
+}
+
+int capacity(ssx_ctx *c, int cfg, bool adj) {
+    int &cap = c->cap[cfg][adj ? 1 : 0];
+    if (cap < 0) cap = persist_capacity(c->R, cfg, adj);
+    return cap;
+}
+
+// Pick the tile configuration and launch form of a grid's sweeps in one
+// direction by timing each admissible candidate on a short source-free sweep
+// (all configurations give identical results, so only speed matters).
+int select_config(ssx_ctx *c, DGrid &G, bool adj) {
+    const int d = adj ? 1 : 0;
+    if (G.cfg[d] >= 0) return SSX_OK;
+    struct Cand {
+        int cfg;
+        bool pers;
+    };
+    std::vector<Cand> cands;
+    for (int k = 0; k < kNumTileCfgs; k++) {
+        if (c->forced_cfg >= 0 && k != c->forced_cfg) continue;
+        if (c->sweep_mode != SSX_SWEEP_PERSISTENT) cands.push_back({k, false});
+        if (c->sweep_mode != SSX_SWEEP_STEP && tiles_of(G, k) <= capacity(c, k, adj))
+            cands.push_back({k, true});
+    }
+    if (cands.empty())
+        return fail(c, SSX_ERR_ARG, "no tile configuration fits the requested sweep mode");
+    if (cands.size() > 1) {
+        const int nt = c->gd.nt < 48 ? c->gd.nt : 48;
+        FwdArgs fa{};
+        AdjArgs aa{};
+        fa.g = aa.g = G.args;
+        fa.src = aa.src = c->src;
+        fa.rec = aa.rec = c->rec;
+        fa.src.n = aa.src.n = fa.rec.n = aa.rec.n = 0;   // no injection or sampling
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bi = 0;
+        for (size_t q = 0; q < cands.size(); q++) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_steps(c, G, adj, cands[q].cfg, cands[q].pers, nt, fa, aa, c->s);
+            cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
+            if (rc != SSX_OK) return rc;
+            CK(ec);
+            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ei);
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                CK(cudaMemsetAsync(G.flags, 0, (size_t)tiles_of(G, cands[q].cfg) * sizeof(unsigned), c->s));
+                CK(cudaEventRecord(e0, c->s));
+                CK(cudaGraphLaunch(exec, c->s));
+                CK(cudaEventRecord(e1, c->s));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                if (rep > 0 && t < ms) ms = t;
+            }
+            cudaGraphExecDestroy(exec);
+            if (ms < best) {
+                best = ms;
+                bi = (int)q;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        TRY(check_sweeps_quiet(c));
+        G.cfg[d] = cands[bi].cfg;
+        G.pers[d] = cands[bi].pers;
+    } else {
+        G.cfg[d] = cands[0].cfg;
+        G.pers[d] = cands[0].pers;
+    }
+    return SSX_OK;
+}
+
 // forward sweep from rest: sources on `src` -> traces on `rec`
 int sim_fwd(ssx_ctx *c, DGrid &G, const Line &src, const double *hs, const double *fs,
             const Line &rec, double *outp, double *outv, bool cache = true) {
     if (!G.ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
-    const int nt = c->gd.nt, R = c->R;
-    auto enqueue = [&, nt, R](cudaStream_t s) -> int {
+    TRY(select_config(c, G, false));
+    const int nt = c->gd.nt, cfg = G.cfg[0];
+    const bool pers = G.pers[0];
+    auto enqueue = [&, nt, cfg, pers](cudaStream_t s) -> int {
         const size_t E = G.L.elems();
         if (outp) CK(cudaMemsetAsync(outp, 0, (size_t)nt * rec.n * sizeof(double), s));
         if (outv) CK(cudaMemsetAsync(outv, 0, (size_t)nt * rec.n * sizeof(double), s));
         CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+        if (pers) CK(cudaMemsetAsync(G.flags, 0, (size_t)tiles_of(G, cfg) * sizeof(unsigned), s));
         FwdArgs a{};
         a.g = G.args;
         a.src = src;
@@ -346,68 +478,35 @@ int sim_fwd(ssx_ctx *c, DGrid &G, const Line &src, const double *hs, const doubl
         a.rec = rec;
         a.outp = outp;
         a.outv = outv;
-        for (int n = 0; n < nt; n++) {
-            const int bi = n & 1, bo = bi ^ 1;
-            a.p_in = G.f[bi][0];
-            a.vx_in = G.f[bi][1];
-            a.vz_in = G.f[bi][2];
-            a.p_out = G.f[bo][0];
-            a.vx_out = G.f[bo][1];
-            a.vz_out = G.f[bo][2];
-            a.n = n;
-            CK(launch_fwd_step(a, R, s));
-        }
-        return SSX_OK;
+        return enqueue_steps(c, G, false, cfg, pers, nt, a, AdjArgs{}, s);
     };
     const double pts = (double)G.L.NX * G.L.NZ * nt;
-    const int pers = use_persistent(c, G, false);
-    if (pers < 0) return fail(c, SSX_ERR_ARG, "persistent sweep requested but the grid's tiles do not fit");
-    if (pers) {
-        auto enqueue_p = [&, nt](cudaStream_t s) -> int {
-            if (outp) CK(cudaMemsetAsync(outp, 0, (size_t)nt * rec.n * sizeof(double), s));
-            if (outv) CK(cudaMemsetAsync(outv, 0, (size_t)nt * rec.n * sizeof(double), s));
-            const size_t E = G.L.elems();
-            CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
-            CK(cudaMemsetAsync(G.flags, 0, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned), s));
-            FwdArgs a{};
-            a.g = G.args;
-            a.src = src;
-            a.hsrc = hs;
-            a.fsrc = fs;
-            a.rec = rec;
-            a.outp = outp;
-            a.outv = outv;
-            CK(launch_fwd_persist(a, persist_args(c, G), c->R, s));
-            return SSX_OK;
-        };
+    const long long nodes = pers ? 1 : nt;
+    if (!cache || pers) {
         const bool g0 = c->use_graphs;
         c->use_graphs = false;
-        int rc = run_cached(c, "", 1, nt, pts, enqueue_p);
+        int rc = run_cached(c, "", nodes, nt, pts, enqueue);
         c->use_graphs = g0;
         return rc;
     }
-    if (!cache) {
-        TRY(enqueue(c->s));
-        c->st.kernel_launches += nt;
-        c->st.point_updates += (long long)pts;
-        c->st.sweeps += 1;
-        return SSX_OK;
-    }
-    char tag[64];
-    snprintf(tag, sizeof tag, "fwd%p:%d:%d", (void *)&G, src.kp, rec.kp);
-    return run_cached(c, ptr_key(tag, hs, fs, outp, outv), nt, nt, pts, enqueue);
+    char tag[96];
+    snprintf(tag, sizeof tag, "fwd%p:%d:%d:c%d", (void *)&G, src.kp, rec.kp, cfg);
+    return run_cached(c, ptr_key(tag, hs, fs, outp, outv), nodes, nt, pts, enqueue);
 }
 
 // exact transpose of sim_fwd: adjoint data on `rec` -> adjoint sources on `src`
 int sim_adj(ssx_ctx *c, DGrid &G, const Line &src, double *hb, double *fb, const Line &rec,
             const double *yp, const double *yv) {
     if (!G.ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
-    const int nt = c->gd.nt, R = c->R;
-    auto enqueue = [&, nt, R](cudaStream_t s) -> int {
+    TRY(select_config(c, G, true));
+    const int nt = c->gd.nt, cfg = G.cfg[1];
+    const bool pers = G.pers[1];
+    auto enqueue = [&, nt, cfg, pers](cudaStream_t s) -> int {
         const size_t E = G.L.elems();
         if (hb) CK(cudaMemsetAsync(hb, 0, (size_t)nt * src.n * sizeof(double), s));
         if (fb) CK(cudaMemsetAsync(fb, 0, (size_t)nt * src.n * sizeof(double), s));
         CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+        if (pers) CK(cudaMemsetAsync(G.flags, 0, (size_t)tiles_of(G, cfg) * sizeof(unsigned), s));
         AdjArgs a{};
         a.g = G.args;
         a.src = src;
@@ -420,53 +519,20 @@ int sim_adj(ssx_ctx *c, DGrid &G, const Line &src, double *hb, double *fb, const
         a.vx_in = G.f[0][1];
         a.vz_in = G.f[0][2];
         CK(launch_adj_init(a, nt, s));
-        for (int n = nt - 1, t = 0; n >= 0; n--, t++) {
-            const int bi = t & 1, bo = bi ^ 1;
-            a.p_in = G.f[bi][0];
-            a.vx_in = G.f[bi][1];
-            a.vz_in = G.f[bi][2];
-            a.p_out = G.f[bo][0];
-            a.vx_out = G.f[bo][1];
-            a.vz_out = G.f[bo][2];
-            a.n = n;
-            CK(launch_adj_step(a, R, s));
-        }
-        return SSX_OK;
+        return enqueue_steps(c, G, true, cfg, pers, nt, FwdArgs{}, a, s);
     };
-    const int pers = use_persistent(c, G, true);
-    if (pers < 0) return fail(c, SSX_ERR_ARG, "persistent sweep requested but the grid's tiles do not fit");
+    const double pts = (double)G.L.NX * G.L.NZ * nt;
+    const long long nodes = (pers ? 1 : nt) + 1;
     if (pers) {
-        auto enqueue_p = [&, nt](cudaStream_t s) -> int {
-            const size_t E = G.L.elems();
-            if (hb) CK(cudaMemsetAsync(hb, 0, (size_t)nt * src.n * sizeof(double), s));
-            if (fb) CK(cudaMemsetAsync(fb, 0, (size_t)nt * src.n * sizeof(double), s));
-            CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
-            CK(cudaMemsetAsync(G.flags, 0, (size_t)G.tiles_x * G.tiles_z * sizeof(unsigned), s));
-            AdjArgs a{};
-            a.g = G.args;
-            a.src = src;
-            a.hbar = hb;
-            a.fbar = fb;
-            a.rec = rec;
-            a.yp = yp;
-            a.yv = yv;
-            a.p_in = G.f[0][0];
-            a.vx_in = G.f[0][1];
-            a.vz_in = G.f[0][2];
-            CK(launch_adj_init(a, nt, s));
-            CK(launch_adj_persist(a, persist_args(c, G), c->R, s));
-            return SSX_OK;
-        };
         const bool g0 = c->use_graphs;
         c->use_graphs = false;
-        int rc = run_cached(c, "", 2, nt, (double)G.L.NX * G.L.NZ * nt, enqueue_p);
+        int rc = run_cached(c, "", nodes, nt, pts, enqueue);
         c->use_graphs = g0;
         return rc;
     }
-    char tag[64];
-    snprintf(tag, sizeof tag, "adj%p:%d:%d:%g", (void *)&G, src.kp, rec.kp, (double)src.scale);
-    return run_cached(c, ptr_key(tag, hb, fb, yp, yv), nt + 1, nt, (double)G.L.NX * G.L.NZ * nt,
-                      enqueue);
+    char tag[96];
+    snprintf(tag, sizeof tag, "adj%p:%d:%d:%g:c%d", (void *)&G, src.kp, rec.kp, (double)src.scale, cfg);
+    return run_cached(c, ptr_key(tag, hb, fb, yp, yv), nodes, nt, pts, enqueue);
 }
 
 // ------------------------------------------------------------- operators --
@@ -573,17 +639,7 @@ int leave(ssx_ctx *c, int rc) {
         return fail(c, SSX_ERR_CUDA, "stream ordering failed");
     return rc;
 }
-// Reads (and clears) the persistent-sweep timeout flag; synchronises.
-int check_sweeps(ssx_ctx *c) {
-    int *eh = reinterpret_cast<int *>(c->sc_host + SC_COUNT);
-    CK(cudaMemcpyAsync(eh, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaStreamSynchronize(c->s));
-    if (*eh != 0) {
-        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
-        return fail(c, SSX_ERR_CUDA, "a persistent sweep's neighbour wait timed out");
-    }
-    return SSX_OK;
-}
+int check_sweeps(ssx_ctx *c) { return check_sweeps_quiet(c); }
 
 int ready(ssx_ctx *c) {
     if (!c) return SSX_ERR_ARG;
@@ -611,6 +667,10 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
     CK(cudaMalloc(&sl.tp, 2 * (size_t)c->gd.nt * n * sizeof(double)));
     sl.tv = sl.tp + (size_t)c->gd.nt * n;
     return SSX_OK;
+}
+
+void reset_choices(ssx_ctx *c) {
+    for (DGrid *G : {&c->full, &c->ss.g, &c->sr.g}) G->cfg[0] = G->cfg[1] = -1;
 }
 
 void drop_graphs(ssx_ctx *c) {
@@ -642,6 +702,8 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
     c->user = (cudaStream_t)stream;
     int rc = SSX_OK;
     auto init = [&]() -> int {
+        for (auto &row : c->cap) row[0] = row[1] = -1;
+        CK(prepare_kernels());
         CK(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -945,6 +1007,15 @@ int ssx_set_sweep_mode(ssx_ctx *c, int mode) {
     if (mode != SSX_SWEEP_AUTO && mode != SSX_SWEEP_STEP && mode != SSX_SWEEP_PERSISTENT)
         return fail(c, SSX_ERR_ARG, "unknown sweep mode");
     c->sweep_mode = mode;
+    reset_choices(c);
+    return SSX_OK;
+}
+
+int ssx_set_tile_config(ssx_ctx *c, int cfg) {
+    if (!c) return SSX_ERR_ARG;
+    if (cfg < -1 || cfg >= kNumTileCfgs) return fail(c, SSX_ERR_ARG, "unknown tile configuration");
+    c->forced_cfg = cfg;
+    reset_choices(c);
     return SSX_OK;
 }
 
@@ -968,6 +1039,10 @@ int ssx_get_stats(ssx_ctx *c, ssx_stats *out) {
         c->ev_used = 0;
     }
     *out = c->st;
+    const DGrid *gs[3] = {&c->full, &c->ss.g, &c->sr.g};
+    for (int k = 0; k < 3; k++)
+        for (int d = 0; d < 2; d++)
+            out->tile_cfg[2 * k + d] = gs[k]->cfg[d] < 0 ? -1 : gs[k]->cfg[d] + (gs[k]->pers[d] ? 16 : 0);
     return SSX_OK;
 }
 

@@ -89,19 +89,55 @@ struct PersistArgs {
     int stall_tile;              // test hook: this tile never publishes (-1: none)
 };
 
-// Kernel launchers (stencil.cu). Return cudaGetLastError() of the launch.
-cudaError_t launch_fwd_step(const FwdArgs &a, int R, cudaStream_t s);
-cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, cudaStream_t s);
-cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, cudaStream_t s);
-int persist_capacity(int R, bool adj);   // co-resident CTAs of the persistent kernels
-cudaError_t launch_adj_step(const AdjArgs &a, int R, cudaStream_t s);
+// Tile configurations of the step kernels: (id, TX, TZ, threads per CTA).
+// Every configuration computes bit-identical results; the runtime picks one
+// per grid and direction by timing them (autotune). TX, TZ >= 2k keeps the
+// halo of a persistent sweep within the four edge neighbours.
+#define SSX_TILE_CONFIGS(X) \
+    X(0, 64, 16, 256)       \
+    X(1, 64, 16, 512)       \
+    X(2, 64, 16, 1024)      \
+    X(3, 64, 32, 512)       \
+    X(4, 64, 32, 1024)      \
+    X(5, 128, 16, 512)      \
+    X(6, 128, 32, 1024)     \
+    X(7, 32, 16, 256)
+constexpr int kNumTileCfgs = 8;
+struct TileCfg {
+    int tx, tz, threads;
+};
+extern const TileCfg kTileCfgs[kNumTileCfgs];
+
+// Kernel launchers (stencil.cu). Return the launch's cudaError_t. `pdl` sets
+// programmatic dependent launch (the step waits in-kernel for the previous one).
+cudaError_t launch_fwd_step(const FwdArgs &a, int R, int cfg, cudaStream_t s, bool pdl);
+cudaError_t launch_adj_step(const AdjArgs &a, int R, int cfg, cudaStream_t s, bool pdl);
+cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, int cfg,
+                               cudaStream_t s);
+cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, int cfg,
+                               cudaStream_t s);
+int persist_capacity(int R, int cfg, bool adj);   // co-resident CTAs of a persistent kernel
+cudaError_t prepare_kernels();                     // dynamic shared-memory limits (once per device)
+
+// per-R instantiations (stencil_r<R>.cu)
+#define SSX_DECLARE_R(RR)                                                                       \
+    cudaError_t stencil_fwd_step_r##RR(const FwdArgs &, int, cudaStream_t, bool);               \
+    cudaError_t stencil_adj_step_r##RR(const AdjArgs &, int, cudaStream_t, bool);               \
+    cudaError_t stencil_fwd_persist_r##RR(const FwdArgs &, const PersistArgs &, int, cudaStream_t); \
+    cudaError_t stencil_adj_persist_r##RR(const AdjArgs &, const PersistArgs &, int, cudaStream_t); \
+    int stencil_capacity_r##RR(int, bool);                                                      \
+    cudaError_t stencil_prepare_r##RR();
+SSX_DECLARE_R(1)
+SSX_DECLARE_R(2)
+SSX_DECLARE_R(3)
+SSX_DECLARE_R(4)
+#undef SSX_DECLARE_R
 cudaError_t launch_adj_init(const AdjArgs &a, int nt, cudaStream_t s);
 cudaError_t launch_fill_kappa(float *kap, const FieldLayout &L, const float *vel, int nx, int nz,
                               int nsp, int row0, double rho, double dt_over_h, cudaStream_t s);
 cudaError_t launch_sponge_table(float *ti, float *th, int N, int n_phys, int nsp,
                                 double smax_dt_half, cudaStream_t s);
 cudaError_t launch_vmax(const float *v, int n, float *out, cudaStream_t s);
-void tile_shape(int R, int *tx, int *tz);
 
 // FP64 Krylov kernels (krylov.cu).
 constexpr int kDotBlocks = 512;

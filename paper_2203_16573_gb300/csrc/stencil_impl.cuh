@@ -1,0 +1,721 @@
+// stencil_impl.cuh -- the tile step of the staggered-grid leapfrog and its
+// exact transpose, and the whole-sweep persistent kernels, templated on the
+// half order R, the tile shape TX x TZ and the CTA size NT. Included by one
+// translation unit per R (stencil_r<R>.cu), which instantiates every tile
+// configuration of kTileCfgs.
+//
+// Forward step n (eqn:awepm discretised as in "Synthetic models and
+// simulation"; staggered grid, order 2 in time, 2k in space):
+//   v^{n+1/2} = A_v v^{n-1/2} - B_v dt/(rho h) D+ p^n        (+ f[n] on z_s)
+//   p^{n+1}   = A_p p^n - B_p kappa dt/h D- v^{n+1/2}          (+ h[n] on z_s)
+//   traces n: P p^{n+1}, P v_z^{n+1/2}      (linear interpolation in depth)
+// A = (1-s)/(1+s), B = 1/(1+s), s = (sigma_x + sigma_z) dt/2 (sponge).
+// D+ u(j+1/2) = sum_m c_m (u[j+m] - u[j-m+1]);  D- w(i) = sum_m c_m (w[i+m-1] - w[i-m]);
+// fields vanish outside the grid, so (D+)^T = -D- exactly.
+//
+// One CTA updates a TX x TZ tile in one launch: it stages p^n over the tile
+// plus a 2k halo in shared memory, recomputes v^{n+1/2} over the tile plus a
+// k halo (x halo for v_x, z halo for v_z) so that the p update needs no other
+// CTA's output, and writes p, v_x, v_z of its own tile to the other buffer of
+// a ping-pong pair. Per grid point and step that is 16 B read (p, v_x, v_z,
+// kappa) and 12 B written; halo re-reads hit L2.
+//
+// The transposed step (Appendix A's adjoint state, run in reverse time)
+// has the same shape with the coefficients moved inside the differences:
+//   q = C_p pbar;  vbar' = vbar + D+ q;  pbar <- A_p pbar + D- (C_v vbar');  vbar <- A_v vbar'
+// so one kernel of the same structure computes it exactly (FP32, identical
+// coefficient arithmetic to the forward kernel).
+#pragma once
+#include "ssx_internal.cuh"
+
+namespace ssx {
+
+namespace {
+
+// Sponge factors of a point with s = (sigma_x + sigma_z) dt/2:
+// B = 1/(1+s) (correctly rounded) and A = (1-s)/(1+s) = 2B - 1.
+__device__ __forceinline__ void damp(float s, float &A, float &B) {
+    B = __frcp_rn(1.0f + s);
+    A = fmaf(2.0f, B, -1.0f);
+}
+
+__device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
+    return (k == k0) ? w0 : ((k == k0 + 1) ? w1 : 0.0f);
+}
+
+
+// Field loads go through L2 only (ld.global.cg): in the persistent sweep a
+// neighbour CTA rewrote these lines during the previous step, and L1 is not
+// coherent across SMs.
+__device__ __forceinline__ float ldf(const float *p) { return __ldcg(p); }
+
+template <int R, int TX, int TZ>
+struct TileSmem {
+    static constexpr int H = 2 * R;
+    static constexpr int PW = TX + 2 * H, PH = TZ + 2 * H;
+    static constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
+    float sp[PH][PW];      // p^n (forward) or q = C_p pbar (transpose), tile + 2k halo
+    float svx[TZ][VXW];    // v_x^{n+1/2} (forward) or C_vx vbar_x' (transpose)
+    float svz[VZH][TX];    // v_z^{n+1/2} (forward) or C_vz vbar_z' (transpose)
+};
+
+// The field buffers and step index of one step (kept in registers).
+struct StepIO {
+    const float *p_in, *vx_in, *vz_in;
+    float *p_out, *vx_out, *vz_out;
+    int n;
+};
+
+// A tile is "interior" when its whole 2k-wide neighbourhood lies where every
+// sponge factor is exactly 1 and every staggered point is valid: there the
+// update needs neither damping factors nor bounds tests, and gives the same
+// bits as the general path.
+template <int R, int TX, int TZ>
+__device__ __forceinline__ bool interior_tile(const GridArgs &g, int i0, int k0) {
+    return i0 - 2 * R >= g.in_x0 && i0 + TX + 2 * R <= g.in_x1 && k0 - 2 * R >= g.in_z0 &&
+           k0 + TZ + 2 * R <= g.in_z1;
+}
+
+// Loops over the shared-memory regions: warp w takes rows w, w+8, ...; lanes
+// take columns lane, lane+32, ... (trip counts are compile-time constants).
+#define FOR_ROWS(r, n) for (int r = wy; r < (n); r += NT / 32)
+#define FOR_COLS(c, n) _Pragma("unroll") for (int c##_u = 0; c##_u < ((n) + 31) / 32; c##_u++) \
+    if (const int c = lane + 32 * c##_u; c < (n))
+
+// Stage a field over tile + 2k halo (corners are never used and not loaded);
+// with PRE the staged value is C_p * field (transpose step).
+template <int R, int TX, int TZ, int NT, bool SP, bool PRE>
+__device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i0, int k0,
+                                        float (&sp)[TZ + 4 * R][TX + 4 * R]) {
+    constexpr int H = 2 * R, PW = TX + 2 * H;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int pitch = g.pitch;
+    auto val = [&](int k, int i) -> float {
+        const int o = k * pitch + i;
+        if (!PRE) return ldf(f + o);
+        if (!SP) return __ldg(g.kap + o) * ldf(f + o);
+        if (k < 0 || k >= g.NZ || i < 0 || i >= g.NX) return 0.0f;
+        float A, B;
+        damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+        return (B * __ldg(g.kap + o)) * ldf(f + o);
+    };
+    // tile rows with the x halo
+    FOR_ROWS(r, TZ) {
+        FOR_COLS(c, PW) { sp[r + H][c] = val(k0 + r, i0 - H + c); }
+    }
+    // z halo rows, tile columns
+    FOR_ROWS(r, 2 * H) {
+        const int rr = r < H ? r : r + TZ;
+        FOR_COLS(c, TX) { sp[rr][c + H] = val(k0 - H + rr, i0 + c); }
+    }
+}
+
+// Per-thread point sets of a tile (compile-time counts): warp w owns rows
+// w, w+8, ..; lane l owns columns l, l+32, ...
+template <int R, int TX, int TZ, int NT>
+struct TileShape {
+    static constexpr int kWarps = NT / 32;
+    static constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
+    static constexpr int NRT = (TZ + kWarps - 1) / kWarps;    // tile rows per thread
+    static constexpr int NRV = (VZH + kWarps - 1) / kWarps;   // v_z rows per thread
+    static constexpr int NCT = (TX + 31) / 32;                // tile columns per thread
+    static constexpr int NCX = (VXW + 31) / 32;               // v_x columns per thread
+};
+
+// One forward step on the TX x TZ tile at (i0, k0). Every global operand of
+// the step is loaded in one batch at the start (p into shared memory, v and
+// kappa into registers) so the step pays one memory latency, not one per loop
+// iteration.
+template <int R, int TX, int TZ, int NT, bool SP>
+__device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                              TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    using T = TileShape<R, TX, TZ, NT>;
+    constexpr int kWarps = NT / 32;
+    constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = io.n;
+
+    float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rk[T::NRT][T::NCT];
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            const int k = k0 + r, j = i0 - R + jj;
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            rk[a_][b] = ok ? __ldg(g.kap + (k0 + r) * pitch + i0 + c) : 0.0f;
+        }
+    stage_p<R, TX, TZ, NT, SP, false>(g, io.p_in, i0, k0, sm.sp);
+    __syncthreads();
+
+    // v_x^{n+1/2} on the tile rows, columns i0-k .. i0+TX+k-2
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            if (r >= TZ || jj >= VXW) continue;
+            const int k = k0 + r, j = i0 - R + jj;
+            float val = 0.0f;
+            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
+                const float *row = &sm.sp[r + H][jj + R];
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                    val = A * rvx[a_][b] - (B * g.cv) * d;
+                } else {
+                    val = rvx[a_][b] - g.cv * d;
+                }
+                if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = val;
+            }
+            sm.svx[r][jj] = val;
+        }
+    // v_z^{n+1/2} on rows k0-k .. k0+TZ+k-2, the tile columns
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            if (kk >= VZH || c >= TX) continue;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool own = (kk >= R && kk < R + TZ);
+            float val = 0.0f;
+            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++)
+                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+                float cvz = g.cv;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                    cvz = B * g.cv;
+                    val = A * rvz[a_][b] - cvz * d;
+                } else {
+                    val = rvz[a_][b] - cvz * d;
+                }
+                if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
+                    const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+                    const int jl = i - a.src.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                        val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)n * a.src.n + jl];
+                }
+                if (own) {
+                    io.vz_out[k * pitch + i] = val;
+                    if (a.outv) {
+                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+                        const int jl = i - a.rec.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                            atomicAdd(&a.outv[(size_t)n * a.rec.n + jl], (double)w * (double)val);
+                    }
+                }
+            }
+            sm.svz[kk][c] = val;
+        }
+    __syncthreads();
+
+    // p^{n+1} on the tile
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            if (r >= TZ || c >= TX) continue;
+            const int k = k0 + r, i = i0 + c;
+            if (!SP || (k < g.NZ && i < g.NX)) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) {
+                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
+                }
+                float cp = rk[a_][b], A = 1.0f;
+                if (SP) {
+                    float B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                    cp *= B;
+                }
+                float val = SP ? A * sm.sp[r + H][c + H] - cp * d : sm.sp[r + H][c + H] - cp * d;
+                if (a.hsrc) {   // constitutive defect h delta(z - z_s)
+                    const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+                    const int jl = i - a.src.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                        val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)n * a.src.n + jl];
+                }
+                io.p_out[k * pitch + i] = val;
+                if (a.outp) {
+                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+                    const int jl = i - a.rec.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                        atomicAdd(&a.outp[(size_t)n * a.rec.n + jl], (double)w * (double)val);
+                }
+            }
+        }
+}
+
+// One transposed step on the tile at (i0, k0) (same batching of loads).
+template <int R, int TX, int TZ, int NT, bool SP>
+__device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                              TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    using T = TileShape<R, TX, TZ, NT>;
+    constexpr int kWarps = NT / 32;
+    constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = io.n;
+
+    float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rp[T::NRT][T::NCT];
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            const int k = k0 + r, j = i0 - R + jj;
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
+        }
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            rp[a_][b] = ok ? ldf(io.p_in + (k0 + r) * pitch + i0 + c) : 0.0f;
+        }
+    // q = C_p pbar over tile + 2k halo
+    stage_p<R, TX, TZ, NT, SP, true>(g, io.p_in, i0, k0, sm.sp);
+    __syncthreads();
+    // transposed pressure injection: hbar[n] = scale * sum_k w_k q (tile only)
+    if (a.hbar) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRT; a_++) {
+            const int r = wy + kWarps * a_;
+            const int k = k0 + r;
+            const float w = r < TZ ? row_weight(k, a.src.kp, a.src.wp0, a.src.wp1) : 0.0f;
+            if (w != 0.0f) {
+#pragma unroll
+                for (int b = 0; b < T::NCT; b++) {
+                    const int c = lane + 32 * b;
+                    const int i = i0 + c, jl = i - a.src.i0;
+                    if (c < TX && i < g.NX && jl >= 0 && jl < a.src.n)
+                        atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
+                                  (double)(w * a.src.scale) * (double)sm.sp[r + H][c + H]);
+                }
+            }
+        }
+    }
+
+    // vbar_x' = vbar_x + D+ q; keep C_vx vbar_x' for the p update
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCX; b++) {
+            const int r = wy + kWarps * a_, jj = lane + 32 * b;
+            if (r >= TZ || jj >= VXW) continue;
+            const int k = k0 + r, j = i0 - R + jj;
+            float val = 0.0f;
+            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
+                const float *row = &sm.sp[r + H][jj + R];
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
+                const float vb = rvx[a_][b] + d;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
+                    val = (B * g.cv) * vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = A * vb;
+                } else {
+                    val = g.cv * vb;
+                    if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = vb;
+                }
+            }
+            sm.svx[r][jj] = val;
+        }
+    // vbar_z' likewise; read out the transposed velocity injection
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRV; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int kk = wy + kWarps * a_, c = lane + 32 * b;
+            if (kk >= VZH || c >= TX) continue;
+            const int k = k0 - R + kk, i = i0 + c;
+            const bool own = (kk >= R && kk < R + TZ);
+            float val = 0.0f;
+            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++)
+                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+                const float vb = rvz[a_][b] + d;
+                float A = 1.0f, B = 1.0f;
+                if (SP) damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                val = (B * g.cv) * vb;
+                if (own) {
+                    if (a.fbar) {
+                        const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+                        const int jl = i - a.src.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                            atomicAdd(&a.fbar[(size_t)n * a.src.n + jl],
+                                      (double)(w * a.src.scale) * (double)val);
+                    }
+                    float out = SP ? A * vb : vb;
+                    if (a.yv && n >= 1) {   // transposed sampling of step n-1
+                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+                        const int jl = i - a.rec.i0;
+                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                            out += w * (float)a.yv[(size_t)(n - 1) * a.rec.n + jl];
+                    }
+                    io.vz_out[k * pitch + i] = out;
+                }
+            }
+            sm.svz[kk][c] = val;
+        }
+    __syncthreads();
+
+    // pbar <- A_p pbar + D- (C_v vbar')
+#pragma unroll
+    for (int a_ = 0; a_ < T::NRT; a_++)
+#pragma unroll
+        for (int b = 0; b < T::NCT; b++) {
+            const int r = wy + kWarps * a_, c = lane + 32 * b;
+            if (r >= TZ || c >= TX) continue;
+            const int k = k0 + r, i = i0 + c;
+            if (!SP || (k < g.NZ && i < g.NX)) {
+                float d = 0.0f;
+#pragma unroll
+                for (int m = 1; m <= R; m++) {
+                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
+                }
+                float out;
+                if (SP) {
+                    float A, B;
+                    damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
+                    out = A * rp[a_][b] + d;
+                } else {
+                    out = rp[a_][b] + d;
+                }
+                if (a.yp && n >= 1) {
+                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+                    const int jl = i - a.rec.i0;
+                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
+                        out += w * (float)a.yp[(size_t)(n - 1) * a.rec.n + jl];
+                }
+                io.p_out[k * pitch + i] = out;
+            }
+        }
+}
+
+template <int R, int TX, int TZ, int NT>
+__device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
+        fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
+    else
+        fwd_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+}
+
+template <int R, int TX, int TZ, int NT>
+__device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                         TileSmem<R, TX, TZ> &sm) {
+    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
+        adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
+    else
+        adj_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+}
+
+// Programmatic dependent launch: let the next step's grid become resident
+// while this one runs, and wait here until the previous step's grid has
+// finished and its writes are visible (a no-op without the launch attribute).
+__device__ __forceinline__ void griddep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <int R, int TX, int TZ>
+__device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
+    extern __shared__ __align__(16) unsigned char ssx_smem[];
+    return *reinterpret_cast<TileSmem<R, TX, TZ> *>(ssx_smem);
+}
+
+template <int R, int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_fwd(const FwdArgs a) {
+    griddep_launch();
+    griddep_wait();
+    const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
+    fwd_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
+}
+
+template <int R, int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_adj(const AdjArgs a) {
+    griddep_launch();
+    griddep_wait();
+    const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
+    adj_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweep: one cooperative launch runs all nt steps. CTA b owns tile
+// b for the whole sweep. Before step n it waits until its four edge
+// neighbours have published "n steps done" (their step n-1 outputs, which
+// its halo reads, are complete, and they no longer read the buffer it is
+// about to overwrite); after the step it publishes n+1. The tile is at least
+// 2k wide in both directions, so the halo never reaches beyond those four
+// neighbours. Waits are bounded: past `timeout_ns` of %globaltimer the CTA
+// records an error and every CTA leaves the sweep.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true = go on; false = leave the sweep (timeout here or elsewhere)
+__device__ __forceinline__ bool wait_neighbours(const PersistArgs &pa, int tile, unsigned need,
+                                                int *s_abort) {
+    if (threadIdx.x < 4) {
+        const int tx = tile % pa.tiles_x, tz = tile / pa.tiles_x;
+        int nb = -1;
+        if (threadIdx.x == 0 && tx > 0) nb = tile - 1;
+        if (threadIdx.x == 1 && tx + 1 < pa.tiles_x) nb = tile + 1;
+        if (threadIdx.x == 2 && tz > 0) nb = tile - pa.tiles_x;
+        if (threadIdx.x == 3 && tz + 1 < pa.tiles_z) nb = tile + pa.tiles_x;
+        if (nb >= 0 && ld_acquire(pa.flags + nb) < need) {
+            const unsigned long long t0 = globaltimer();
+            unsigned spins = 0;
+            while (ld_acquire(pa.flags + nb) < need) {
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)pa.err != 0) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    if (globaltimer() - t0 > pa.timeout_ns) {
+                        atomicExch(pa.err, 1);
+                        *s_abort = 1;
+                        break;
+                    }
+                }
+                __nanosleep(20);
+            }
+        }
+    }
+    __syncthreads();
+    return *s_abort == 0;
+}
+
+__device__ __forceinline__ void publish(const PersistArgs &pa, int tile, unsigned done) {
+    __syncthreads();
+    if (threadIdx.x == 0 && tile != pa.stall_tile) {
+        __threadfence();
+        st_release(pa.flags + tile, done);
+    }
+}
+
+// step io of a ping-pong sweep: even steps read buffer 0, odd steps buffer 1
+__device__ __forceinline__ StepIO ping_pong(const PersistArgs &pa, int t, int n) {
+    const bool odd = t & 1;
+    StepIO io;
+    io.p_in = odd ? pa.f[1][0] : pa.f[0][0];
+    io.vx_in = odd ? pa.f[1][1] : pa.f[0][1];
+    io.vz_in = odd ? pa.f[1][2] : pa.f[0][2];
+    io.p_out = odd ? pa.f[0][0] : pa.f[1][0];
+    io.vx_out = odd ? pa.f[0][1] : pa.f[1][1];
+    io.vz_out = odd ? pa.f[0][2] : pa.f[1][2];
+    io.n = n;
+    return io;
+}
+
+template <int R, int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_fwd_persist(const FwdArgs a, const PersistArgs pa) {
+    TileSmem<R, TX, TZ> &sm = tile_smem<R, TX, TZ>();
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const int tile = blockIdx.x;
+    const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
+    for (int n = 0; n < pa.nt; n++) {
+        if (n > 0 && !wait_neighbours(pa, tile, (unsigned)n, &s_abort)) return;
+        fwd_tile<R, TX, TZ, NT>(a, ping_pong(pa, n, n), i0, k0, sm);
+        publish(pa, tile, (unsigned)(n + 1));
+    }
+}
+
+template <int R, int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const PersistArgs pa) {
+    TileSmem<R, TX, TZ> &sm = tile_smem<R, TX, TZ>();
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const int tile = blockIdx.x;
+    const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
+    for (int t = 0; t < pa.nt; t++) {
+        if (t > 0 && !wait_neighbours(pa, tile, (unsigned)t, &s_abort)) return;
+        adj_tile<R, TX, TZ, NT>(a, ping_pong(pa, t, pa.nt - 1 - t), i0, k0, sm);
+        publish(pa, tile, (unsigned)(t + 1));
+    }
+}
+
+// ----------------------------------------------------------- launchers --
+template <int R>
+struct Stencil {
+    template <int TX, int TZ>
+    static size_t smem() { return sizeof(TileSmem<R, TX, TZ>); }
+
+    template <class Args>
+    static cudaError_t launch(void (*kern)(Args), dim3 grid, int nt, size_t sm, cudaStream_t s,
+                              bool pdl, const Args &a) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(nt);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl ? at : nullptr;
+        cfg.numAttrs = pdl ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, kern, a);
+    }
+
+    template <int TX, int TZ, int NT>
+    static cudaError_t fwd_step(const FwdArgs &a, cudaStream_t s, bool pdl) {
+        dim3 grid((a.g.NX + TX - 1) / TX, (a.g.NZ + TZ - 1) / TZ);
+        return launch<FwdArgs>(k_fwd<R, TX, TZ, NT>, grid, NT, smem<TX, TZ>(), s, pdl, a);
+    }
+    template <int TX, int TZ, int NT>
+    static cudaError_t adj_step(const AdjArgs &a, cudaStream_t s, bool pdl) {
+        dim3 grid((a.g.NX + TX - 1) / TX, (a.g.NZ + TZ - 1) / TZ);
+        return launch<AdjArgs>(k_adj<R, TX, TZ, NT>, grid, NT, smem<TX, TZ>(), s, pdl, a);
+    }
+    template <int TX, int TZ, int NT>
+    static cudaError_t fwd_persist(const FwdArgs &a, const PersistArgs &pa, cudaStream_t s) {
+        FwdArgs aa = a;
+        PersistArgs pp = pa;
+        void *args[] = {&aa, &pp};
+        return cudaLaunchCooperativeKernel((void *)k_fwd_persist<R, TX, TZ, NT>,
+                                           dim3(pa.tiles_x * pa.tiles_z), dim3(NT), args,
+                                           smem<TX, TZ>(), s);
+    }
+    template <int TX, int TZ, int NT>
+    static cudaError_t adj_persist(const AdjArgs &a, const PersistArgs &pa, cudaStream_t s) {
+        AdjArgs aa = a;
+        PersistArgs pp = pa;
+        void *args[] = {&aa, &pp};
+        return cudaLaunchCooperativeKernel((void *)k_adj_persist<R, TX, TZ, NT>,
+                                           dim3(pa.tiles_x * pa.tiles_z), dim3(NT), args,
+                                           smem<TX, TZ>(), s);
+    }
+    template <int TX, int TZ, int NT>
+    static cudaError_t prepare() {
+        const int sm = (int)smem<TX, TZ>();
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_fwd<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_adj<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_fwd_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_adj_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    }
+    template <int TX, int TZ, int NT>
+    static int capacity(bool adj) {
+        int dev = 0, sms = 0, per_sm = 0, coop = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        const void *fn = adj ? (const void *)k_adj_persist<R, TX, TZ, NT> : (const void *)k_fwd_persist<R, TX, TZ, NT>;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem<TX, TZ>()) != cudaSuccess) return 0;
+        return per_sm * sms;
+    }
+};
+
+}  // namespace
+
+// Dispatch over kTileCfgs for one R (defines stencil_*_r<R> of ssx_internal.cuh).
+#define SSX_DEFINE_DISPATCH(RR)                                                                    \
+    cudaError_t stencil_fwd_step_r##RR(const FwdArgs &a, int cfg, cudaStream_t s, bool pdl) {      \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_FWD_STEP)                                                    \
+            default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                          \
+    }                                                                                              \
+    cudaError_t stencil_adj_step_r##RR(const AdjArgs &a, int cfg, cudaStream_t s, bool pdl) {      \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_ADJ_STEP)                                                    \
+            default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                          \
+    }                                                                                              \
+    cudaError_t stencil_fwd_persist_r##RR(const FwdArgs &a, const PersistArgs &pa, int cfg,        \
+                                          cudaStream_t s) {                                        \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_FWD_PERSIST)                                                 \
+            default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                          \
+    }                                                                                              \
+    cudaError_t stencil_adj_persist_r##RR(const AdjArgs &a, const PersistArgs &pa, int cfg,        \
+                                          cudaStream_t s) {                                        \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_ADJ_PERSIST)                                                 \
+            default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                          \
+    }                                                                                              \
+    int stencil_capacity_r##RR(int cfg, bool adj) {                                                \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_CAPACITY)                                                    \
+            default: return 0;                                                                     \
+        }                                                                                          \
+    }                                                                                              \
+    cudaError_t stencil_prepare_r##RR() {                                                          \
+        cudaError_t e = cudaSuccess;                                                               \
+        SSX_TILE_CONFIGS(SSX_CASE_PREPARE)                                                         \
+        return e;                                                                                  \
+    }
+
+#define SSX_CASE_FWD_STEP(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_step<TX, TZ, NT>(a, s, pdl);
+#define SSX_CASE_ADJ_STEP(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_step<TX, TZ, NT>(a, s, pdl);
+#define SSX_CASE_FWD_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_persist<TX, TZ, NT>(a, pa, s);
+#define SSX_CASE_ADJ_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_persist<TX, TZ, NT>(a, pa, s);
+#define SSX_CASE_CAPACITY(id, TX, TZ, NT) case id: return Stencil<SSX_R>::capacity<TX, TZ, NT>(adj);
+#define SSX_CASE_PREPARE(id, TX, TZ, NT) if (e == cudaSuccess) e = Stencil<SSX_R>::prepare<TX, TZ, NT>();
+
+}  // namespace ssx

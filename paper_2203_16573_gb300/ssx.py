@@ -27,7 +27,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_velocity_model", "ssx_set_geometry", "ssx_forward", "ssx_adjoint",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
-           "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode"]
+           "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode",
+           "ssx_set_tile_config"]
 
 
 class SSXError(RuntimeError):
@@ -52,10 +53,13 @@ class GeomDesc(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("point_updates", ctypes.c_longlong),
                 ("sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double),
-                ("timed_steps", ctypes.c_longlong), ("timed_point_updates", ctypes.c_double)]
+                ("timed_steps", ctypes.c_longlong), ("timed_point_updates", ctypes.c_double),
+                ("tile_cfg", ctypes.c_int * 6)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["tile_cfg"] = list(self.tile_cfg)
+        return d
 
 
 _lib = None
@@ -89,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_reset_stats": ([vp], i),
         "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
         "ssx_set_sweep_mode": ([vp, i], i),
+        "ssx_set_tile_config": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -224,6 +229,9 @@ class Context:
 
     def set_sweep_mode(self, mode: int):
         self._check(self._lib.ssx_set_sweep_mode(self._c, int(mode)))
+
+    def set_tile_config(self, cfg: int):
+        self._check(self._lib.ssx_set_tile_config(self._c, int(cfg)))
 
     # -- instrumentation ------------------------------------------------------
     def set_timing(self, on: bool):

@@ -278,3 +278,28 @@ def test_persistent_wait_timeout_is_reported_and_context_survives(ssx, oracle):
         ctx.forward(dev(h))
     assert e.value.code == 2 and "timed out" in e.value.msg
     assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_every_tile_configuration_gives_identical_results(ssx, order):
+    """All tile shapes / CTA sizes and both launch forms run the same per-point
+    arithmetic: bitwise-identical sweeps (ragged tiles on both grid edges)."""
+    spec = frac_spec(order, nt=120)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 19))
+    y = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 20))
+    ref = None
+    for mode in (ssx.SWEEP_STEP, ssx.SWEEP_PERSISTENT):
+        ctx.set_sweep_mode(mode)
+        for cfg in range(8):
+            ctx.set_tile_config(cfg)
+            got = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
+                   ctx.weight_apply(ssx.W_D, y).clone())
+            if ref is None:
+                ref = got
+            for a, b in zip(got, ref):
+                assert torch.equal(a, b), (mode, cfg)
+    ctx.set_tile_config(-1)
+    ctx.set_sweep_mode(ssx.SWEEP_AUTO)
+    st = ctx.stats()
+    assert len(st["tile_cfg"]) == 6
