@@ -93,11 +93,11 @@ __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i
     auto val = [&](int k, int i) -> float {
         const int o = k * pitch + i;
         if (!PRE) return ldf(f + o);
-        if (!SP) return __ldg(g.kap + o) * ldf(f + o);
+        if (!SP) return __fmul_rn(__ldg(g.kap + o), ldf(f + o));
         if (k < 0 || k >= g.NZ || i < 0 || i >= g.NX) return 0.0f;
         float A, B;
         damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
-        return (B * __ldg(g.kap + o)) * ldf(f + o);
+        return __fmul_rn(__fmul_rn(B, __ldg(g.kap + o)), ldf(f + o));
     };
     // tile rows with the x halo
     FOR_ROWS(r, TZ) {
@@ -185,9 +185,9 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
-                    val = A * rvx[a_][b] - (B * g.cv) * d;
+                    val = fmaf(-(B * g.cv), d, A * rvx[a_][b]);
                 } else {
-                    val = rvx[a_][b] - g.cv * d;
+                    val = fmaf(-g.cv, d, rvx[a_][b]);
                 }
                 if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = val;
             }
@@ -213,15 +213,15 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
                     cvz = B * g.cv;
-                    val = A * rvz[a_][b] - cvz * d;
+                    val = fmaf(-cvz, d, A * rvz[a_][b]);
                 } else {
-                    val = rvz[a_][b] - cvz * d;
+                    val = fmaf(-cvz, d, rvz[a_][b]);
                 }
                 if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
                     const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
                     const int jl = i - a.src.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val += cvz * (w * a.src.scale) * (float)a.fsrc[(size_t)n * a.src.n + jl];
+                        val = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + jl], val);
                 }
                 if (own) {
                     io.vz_out[k * pitch + i] = val;
@@ -258,12 +258,12 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                     damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
                     cp *= B;
                 }
-                float val = SP ? A * sm.sp[r + H][c + H] - cp * d : sm.sp[r + H][c + H] - cp * d;
+                float val = fmaf(-cp, d, SP ? A * sm.sp[r + H][c + H] : sm.sp[r + H][c + H]);
                 if (a.hsrc) {   // constitutive defect h delta(z - z_s)
                     const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
                     const int jl = i - a.src.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val += cp * (w * a.src.scale) * (float)a.hsrc[(size_t)n * a.src.n + jl];
+                        val = fmaf(cp * (w * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + jl], val);
                 }
                 io.p_out[k * pitch + i] = val;
                 if (a.outp) {
@@ -398,7 +398,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                         const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
                         const int jl = i - a.rec.i0;
                         if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                            out += w * (float)a.yv[(size_t)(n - 1) * a.rec.n + jl];
+                            out = fmaf(w, (float)a.yv[(size_t)(n - 1) * a.rec.n + jl], out);
                     }
                     io.vz_out[k * pitch + i] = out;
                 }
@@ -426,7 +426,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
-                    out = A * rp[a_][b] + d;
+                    out = fmaf(A, rp[a_][b], d);
                 } else {
                     out = rp[a_][b] + d;
                 }
@@ -434,7 +434,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                     const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
                     const int jl = i - a.rec.i0;
                     if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        out += w * (float)a.yp[(size_t)(n - 1) * a.rec.n + jl];
+                        out = fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jl], out);
                 }
                 io.p_out[k * pitch + i] = out;
             }
