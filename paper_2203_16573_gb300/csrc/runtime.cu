@@ -98,7 +98,16 @@ struct ssx_ctx {
     ssx_geom_desc geom{};
     Line src{}, rec{};
     double sgn = 1.0;          // +1 in the paper's examples' geometry
-    Slab ss, sr;               // z_s slab (W~_m, W~_m^{-1}), z_r slab (W~_d)
+    Slab ss, sr;               // z_s slab (W~_m^{-1}), z_r slab (W~_d)
+    Slab sm;                   // second z_s slab for W~_m, so it can share a launch with W~_d
+
+    // multi-sweep phases: tile configuration and device job table per phase
+    struct PhaseInfo {
+        int cfg = -1;
+        Job *jobs = nullptr;
+        int njobs = 0, total = 0, T = 0;
+    };
+    std::unordered_map<std::string, PhaseInfo> phases;
 
     // gathers: line-shaped [nt][n_line], receiver-shaped [nt][n_rec]
     double *gbuf = nullptr;
@@ -535,27 +544,241 @@ int sim_adj(ssx_ctx *c, DGrid &G, const Line &src, double *hb, double *fb, const
     return run_cached(c, ptr_key(tag, hb, fb, yp, yv), nodes, nt, pts, enqueue);
 }
 
+// ---------------------------------------------------------------- phases --
+// A phase runs several sweeps in the same launches (kernel k_multi): sweeps
+// that are independent share each time step's launch, and a sweep that
+// consumes another's trace gather runs in lockstep a step or two behind it.
+struct Sweep {
+    DGrid *G;
+    bool adj;
+    int offset;
+    Line src, rec;
+    const double *hs, *fs;       // forward sources
+    double *outp, *outv;         // forward traces
+    double *hb, *fb;             // transposed injections
+    const double *yp, *yv;       // transposed data
+};
+
+Sweep fwd_sweep(DGrid &G, const Line &src, const double *hs, const double *fs, const Line &rec,
+                double *outp, double *outv, int offset = 0) {
+    return Sweep{&G, false, offset, src, rec, hs, fs, outp, outv, nullptr, nullptr, nullptr, nullptr};
+}
+Sweep adj_sweep(DGrid &G, const Line &src, double *hb, double *fb, const Line &rec,
+                const double *yp, const double *yv, int offset = 0) {
+    return Sweep{&G, true, offset, src, rec, nullptr, nullptr, nullptr, nullptr, hb, fb, yp, yv};
+}
+
+std::vector<Job> make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet) {
+    std::vector<Job> jobs(sw.size());
+    int base = 0;
+    for (size_t j = 0; j < sw.size(); j++) {
+        const Sweep &w = sw[j];
+        Job &J = jobs[j];
+        memset(&J, 0, sizeof J);
+        J.adj = w.adj ? 1 : 0;
+        J.offset = w.offset;
+        J.nt = c->gd.nt;
+        J.tiles_x = (w.G->L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx;
+        J.tiles = J.tiles_x * ((w.G->L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz);
+        J.tile_base = base;
+        base += J.tiles;
+        for (int b = 0; b < 2; b++)
+            for (int f = 0; f < 3; f++) J.f[b][f] = w.G->f[b][f];
+        Line src = w.src, rec = w.rec;
+        if (quiet) src.n = rec.n = 0;   // timing runs: no injection, no sampling
+        if (w.adj) {
+            J.aa.g = w.G->args;
+            J.aa.src = src;
+            J.aa.rec = rec;
+            J.aa.hbar = w.hb;
+            J.aa.fbar = w.fb;
+            J.aa.yp = w.yp;
+            J.aa.yv = w.yv;
+        } else {
+            J.fa.g = w.G->args;
+            J.fa.src = src;
+            J.fa.rec = rec;
+            J.fa.hsrc = w.hs;
+            J.fa.fsrc = w.fs;
+            J.fa.outp = w.outp;
+            J.fa.outv = w.outv;
+        }
+    }
+    return jobs;
+}
+
+int phase_len(ssx_ctx *c, const std::vector<Sweep> &sw) {
+    int T = 0;
+    for (const Sweep &w : sw) T = std::max(T, w.offset + c->gd.nt);
+    return T;
+}
+
+// the launches of a phase: transposed sweeps get their initial state (the
+// transposed sampling of their last data sample) just before their first step
+int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const Job *djobs, int total, int T,
+                  int cfg, cudaStream_t s, bool with_init) {
+    for (int t = 0; t < T; t++) {
+        if (with_init)
+            for (const Sweep &w : sw)
+                if (w.adj && w.offset == t) {
+                    AdjArgs a{};
+                    a.g = w.G->args;
+                    a.rec = w.rec;
+                    a.yp = w.yp;
+                    a.yv = w.yv;
+                    a.p_in = w.G->f[0][0];
+                    a.vx_in = w.G->f[0][1];
+                    a.vz_in = w.G->f[0][2];
+                    CK(launch_adj_init(a, c->gd.nt, s));
+                }
+        CK(launch_multi(djobs, (int)sw.size(), total, t, c->R, cfg, s, true));
+    }
+    return SSX_OK;
+}
+
+int upload_jobs(ssx_ctx *c, const std::vector<Job> &jobs, Job **dst) {
+    if (!*dst) CK(cudaMalloc(dst, kMaxJobs * sizeof(Job)));
+    CK(cudaMemcpyAsync(*dst, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return SSX_OK;
+}
+
+// time each admissible tile configuration on a short source-free run of the phase
+int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
+    if (c->forced_cfg >= 0) {
+        *best_cfg = c->forced_cfg;
+        return SSX_OK;
+    }
+    Job *tmp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int T = std::min(phase_len(c, sw), 48);
+    float best = 1e30f;
+    int rc = SSX_OK;
+    for (int k = 0; k < kNumTileCfgs && rc == SSX_OK; k++) {
+        std::vector<Job> jobs = make_jobs(c, sw, k, true);
+        int total = 0;
+        for (auto &J : jobs) total += J.tiles;
+        rc = upload_jobs(c, jobs, &tmp);
+        if (rc != SSX_OK) break;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_phase(c, sw, tmp, total, T, k, c->s, false);
+        cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
+        if (rc != SSX_OK) break;
+        CK(ec);
+        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            CK(cudaEventRecord(e0, c->s));
+            CK(cudaGraphLaunch(exec, c->s));
+            CK(cudaEventRecord(e1, c->s));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        cudaGraphExecDestroy(exec);
+        if (ms < best) {
+            best = ms;
+            *best_cfg = k;
+        }
+    }
+    if (tmp) cudaFree(tmp);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int run_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw) {
+    for (const Sweep &w : sw)
+        if (!w.G->ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
+    std::string key = name;
+    for (const Sweep &w : sw) {
+        char b[200];
+        snprintf(b, sizeof b, "|%p%d%d:%d:%d:%g:%p:%p:%p:%p:%p:%p:%p:%p", (void *)w.G, w.adj,
+                 w.offset, w.src.kp, w.rec.kp, (double)w.src.scale, (const void *)w.hs,
+                 (const void *)w.fs, (void *)w.outp, (void *)w.outv, (void *)w.hb, (void *)w.fb,
+                 (const void *)w.yp, (const void *)w.yv);
+        key += b;
+    }
+    auto it = c->phases.find(key);
+    if (it == c->phases.end()) {
+        ssx_ctx::PhaseInfo info;
+        TRY(tune_phase(c, sw, &info.cfg));
+        std::vector<Job> jobs = make_jobs(c, sw, info.cfg, false);
+        info.njobs = (int)jobs.size();
+        for (auto &J : jobs) info.total += J.tiles;
+        info.T = phase_len(c, sw);
+        TRY(upload_jobs(c, jobs, &info.jobs));
+        it = c->phases.emplace(key, info).first;
+    }
+    const ssx_ctx::PhaseInfo info = it->second;
+    const int nt = c->gd.nt;
+    auto enqueue = [&, nt](cudaStream_t s) -> int {
+        for (const Sweep &w : sw) {
+            const size_t E = w.G->L.elems();
+            const size_t nr = (size_t)nt * w.rec.n * sizeof(double);
+            const size_t ns = (size_t)nt * w.src.n * sizeof(double);
+            if (w.outp) CK(cudaMemsetAsync(w.outp, 0, nr, s));
+            if (w.outv) CK(cudaMemsetAsync(w.outv, 0, nr, s));
+            if (w.hb) CK(cudaMemsetAsync(w.hb, 0, ns, s));
+            if (w.fb) CK(cudaMemsetAsync(w.fb, 0, ns, s));
+            CK(cudaMemsetAsync(w.G->mem + E, 0, 3 * E * sizeof(float), s));
+        }
+        return enqueue_phase(c, sw, info.jobs, info.total, info.T, info.cfg, s, true);
+    };
+    double pts = 0;
+    long long inits = 0;
+    for (const Sweep &w : sw) {
+        pts += (double)w.G->L.NX * w.G->L.NZ * nt;
+        inits += w.adj ? 1 : 0;
+    }
+    c->st.sweeps += (long long)sw.size() - 1;   // run_cached counts one
+    return run_cached(c, "phase" + key, info.T + inits, info.T, pts, enqueue);
+}
+
+bool fused(ssx_ctx *c) { return c->sweep_mode != SSX_SWEEP_PERSISTENT; }
+
 // ------------------------------------------------------------- operators --
 int op_S(ssx_ctx *c, const double *in, double *out) {
-    return sim_fwd(c, c->full, c->src, in, nullptr, c->rec, out, nullptr);
+    if (!fused(c)) return sim_fwd(c, c->full, c->src, in, nullptr, c->rec, out, nullptr);
+    return run_phase(c, "S", {fwd_sweep(c->full, c->src, in, nullptr, c->rec, out, nullptr)});
 }
 int op_ST(ssx_ctx *c, const double *in, double *out) {
-    return sim_adj(c, c->full, c->src, out, nullptr, c->rec, in, nullptr);
+    if (!fused(c)) return sim_adj(c, c->full, c->src, out, nullptr, c->rec, in, nullptr);
+    return run_phase(c, "ST", {adj_sweep(c->full, c->src, out, nullptr, c->rec, in, nullptr)});
 }
-// -4 Pi_1 S^T J S Pi_1^T on a slab (eqn:winvcomp)
+// -4 Pi_1 S^T J S Pi_1^T on a slab (eqn:winvcomp): velocity injection on the
+// plane, both traces at the datum, exchanged, transposed sweep
+Line scaled(const Line &l, double f) {
+    Line o = l;
+    o.scale = (float)f;
+    return o;
+}
 int op_sym_lambda(ssx_ctx *c, Slab &sl, const double *in, double *out) {
-    TRY(sim_fwd(c, sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv));
-    Line pl = sl.plane;
-    pl.scale = (float)(-4.0 * c->sgn);
-    return sim_adj(c, sl.g, pl, nullptr, out, sl.datum, sl.tv, sl.tp);
+    const Line pl = scaled(sl.plane, -4.0 * c->sgn);
+    if (!fused(c)) {
+        TRY(sim_fwd(c, sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv));
+        return sim_adj(c, sl.g, pl, nullptr, out, sl.datum, sl.tv, sl.tp);
+    }
+    TRY(run_phase(c, "Lf", {fwd_sweep(sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv)}));
+    return run_phase(c, "La", {adj_sweep(sl.g, pl, nullptr, out, sl.datum, sl.tv, sl.tp)});
 }
 // -Pi_0 S^T J S Pi_0^T on the z_s slab (wcomp)
 int op_Wm(ssx_ctx *c, const double *in, double *out) {
-    Slab &sl = c->ss;
-    TRY(sim_fwd(c, sl.g, sl.plane, in, nullptr, sl.datum, sl.tp, sl.tv));
-    Line pl = sl.plane;
-    pl.scale = (float)(-1.0 * c->sgn);
-    return sim_adj(c, sl.g, pl, out, nullptr, sl.datum, sl.tv, sl.tp);
+    Slab &sl = c->sm;
+    const Line pl = scaled(sl.plane, -1.0 * c->sgn);
+    if (!fused(c)) {
+        TRY(sim_fwd(c, sl.g, sl.plane, in, nullptr, sl.datum, sl.tp, sl.tv));
+        return sim_adj(c, sl.g, pl, out, nullptr, sl.datum, sl.tv, sl.tp);
+    }
+    TRY(run_phase(c, "Mf", {fwd_sweep(sl.g, sl.plane, in, nullptr, sl.datum, sl.tp, sl.tv)}));
+    return run_phase(c, "Ma", {adj_sweep(sl.g, pl, out, nullptr, sl.datum, sl.tv, sl.tp)});
 }
 int op_W(ssx_ctx *c, int which, const double *in, double *out) {
     switch (which) {
@@ -595,35 +818,64 @@ int op_Minv(ssx_ctx *c, int mode, double alpha, const double *r, double *g) {
     return SSX_OK;
 }
 
-// q = N p (eqn:normpart) or the Euclidean normal operator
+// q = N p (eqn:normpart) or the Euclidean normal operator. Fused: phase 1
+// runs S p, the W~_d slab's forward sweep one step behind it (it consumes
+// S p sample n - 1) and, for alpha > 0, W~_m's forward sweep on A p; phase 2
+// runs the W~_d slab's transposed sweep, S^T two steps behind it (it needs the
+// slab's output sample m - 1 at the end of its reverse step m) and W~_m's
+// transposed sweep.
 int op_N(ssx_ctx *c, int mode, double alpha, const double *p, double *q) {
     const int nt = c->gd.nt, nl = c->geom.n_line;
-    TRY(op_S(c, p, c->tr1));
-    if (mode == SSX_MODE_PCG) {
-        TRY(op_sym_lambda(c, c->sr, c->tr1, c->tr2));
-        TRY(op_ST(c, c->tr2, q));
+    if (alpha != 0.0 && mode == SSX_MODE_PCG) {
+        CK(launch_colscale(c->tl1, p, c->dist, nt, nl, c->s));
+        c->st.kernel_launches += 1;
+    }
+    if (mode == SSX_MODE_PCG && fused(c)) {
+        Slab &r = c->sr, &m = c->sm;
+        std::vector<Sweep> ph1 = {fwd_sweep(c->full, c->src, p, nullptr, c->rec, c->tr1, nullptr),
+                                  fwd_sweep(r.g, r.plane, nullptr, c->tr1, r.datum, r.tp, r.tv, 1)};
+        std::vector<Sweep> ph2 = {adj_sweep(r.g, scaled(r.plane, -4.0 * c->sgn), nullptr, c->tr2,
+                                            r.datum, r.tv, r.tp),
+                                  adj_sweep(c->full, c->src, q, nullptr, c->rec, c->tr2, nullptr, 2)};
         if (alpha != 0.0) {
-            CK(launch_colscale(c->tl1, p, c->dist, nt, nl, c->s));
-            TRY(op_Wm(c, c->tl1, c->tl2));
-            CK(launch_colscale_add(q, c->tl2, c->dist, alpha, nt, nl, c->s));
-            c->st.kernel_launches += 2;
+            ph1.push_back(fwd_sweep(m.g, m.plane, c->tl1, nullptr, m.datum, m.tp, m.tv));
+            ph2.push_back(adj_sweep(m.g, scaled(m.plane, -1.0 * c->sgn), c->tl2, nullptr, m.datum,
+                                    m.tv, m.tp));
         }
+        TRY(run_phase(c, "N1", ph1));
+        TRY(run_phase(c, "N2", ph2));
     } else {
-        TRY(op_ST(c, c->tr1, q));
-        if (alpha != 0.0) {
-            CK(launch_colscale_add(q, p, c->dist2, alpha, nt, nl, c->s));
-            c->st.kernel_launches += 1;
+        TRY(op_S(c, p, c->tr1));
+        if (mode == SSX_MODE_PCG) {
+            TRY(op_sym_lambda(c, c->sr, c->tr1, c->tr2));
+            TRY(op_ST(c, c->tr2, q));
+            if (alpha != 0.0) TRY(op_Wm(c, c->tl1, c->tl2));
+        } else {
+            TRY(op_ST(c, c->tr1, q));
         }
+    }
+    if (alpha != 0.0) {
+        if (mode == SSX_MODE_PCG)
+            CK(launch_colscale_add(q, c->tl2, c->dist, alpha, nt, nl, c->s));
+        else
+            CK(launch_colscale_add(q, p, c->dist2, alpha, nt, nl, c->s));
+        c->st.kernel_launches += 1;
     }
     return SSX_OK;
 }
 
+// r = S^* d: S^T W~_d d (the slab's transposed sweep and S^T in one phase)
 int op_rhs(ssx_ctx *c, int mode, const double *d, double *r) {
-    if (mode == SSX_MODE_PCG) {
+    if (mode != SSX_MODE_PCG) return op_ST(c, d, r);
+    if (!fused(c)) {
         TRY(op_sym_lambda(c, c->sr, d, c->tr2));
         return op_ST(c, c->tr2, r);
     }
-    return op_ST(c, d, r);
+    Slab &s = c->sr;
+    TRY(run_phase(c, "R1", {fwd_sweep(s.g, s.plane, nullptr, d, s.datum, s.tp, s.tv)}));
+    return run_phase(c, "R2", {adj_sweep(s.g, scaled(s.plane, -4.0 * c->sgn), nullptr, c->tr2,
+                                         s.datum, s.tv, s.tp),
+                               adj_sweep(c->full, c->src, r, nullptr, c->rec, c->tr2, nullptr, 2)});
 }
 
 // ------------------------------------------------------------- plumbing --
@@ -669,11 +921,19 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
     return SSX_OK;
 }
 
+void drop_phases(ssx_ctx *c) {
+    for (auto &kv : c->phases)
+        if (kv.second.jobs) cudaFree(kv.second.jobs);
+    c->phases.clear();
+}
+
 void reset_choices(ssx_ctx *c) {
-    for (DGrid *G : {&c->full, &c->ss.g, &c->sr.g}) G->cfg[0] = G->cfg[1] = -1;
+    for (DGrid *G : {&c->full, &c->ss.g, &c->sr.g, &c->sm.g}) G->cfg[0] = G->cfg[1] = -1;
+    drop_phases(c);
 }
 
 void drop_graphs(ssx_ctx *c) {
+    drop_phases(c);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     c->graph_nodes.clear();
@@ -737,6 +997,8 @@ int ssx_destroy(ssx_ctx *c) {
     }
     grid_free(c->full);
     grid_free(c->ss.g);
+    grid_free(c->sm.g);
+    if (c->sm.tp) cudaFree(c->sm.tp);
     grid_free(c->sr.g);
     if (c->ss.tp) cudaFree(c->ss.tp);
     if (c->sr.tp) cudaFree(c->sr.tp);
@@ -777,6 +1039,7 @@ int ssx_set_velocity_model(ssx_ctx *c, const float *v_dev, double rho) {
         if (c->have_geom) {
             TRY(grid_fill(c, c->ss.g));
             TRY(grid_fill(c, c->sr.g));
+            TRY(grid_fill(c, c->sm.g));
         }
         c->have_model = true;
         return SSX_OK;
@@ -804,6 +1067,7 @@ int ssx_set_geometry(ssx_ctx *c, const ssx_geom_desc *gm) {
         c->sgn = -dir;
         TRY(slab_setup(c, c->ss, gm->z_s, gm->z_s + dir * gm->dz_datum, gm->ix_line0, gm->n_line));
         TRY(slab_setup(c, c->sr, gm->z_r, gm->z_r + dir * gm->dz_datum, gm->ix_rec0, gm->n_rec));
+        TRY(slab_setup(c, c->sm, gm->z_s, gm->z_s + dir * gm->dz_datum, gm->ix_line0, gm->n_line));
         if (c->gbuf) cudaFree(c->gbuf);
         c->gbuf = nullptr;
         const size_t nl = (size_t)c->gd.nt * gm->n_line, nr = (size_t)c->gd.nt * gm->n_rec;
@@ -832,6 +1096,7 @@ int ssx_set_geometry(ssx_ctx *c, const ssx_geom_desc *gm) {
         if (c->have_model) {
             TRY(grid_fill(c, c->ss.g));
             TRY(grid_fill(c, c->sr.g));
+            TRY(grid_fill(c, c->sm.g));
         }
         CK(cudaStreamSynchronize(c->s));
         c->have_geom = true;

@@ -89,6 +89,23 @@ struct PersistArgs {
     int stall_tile;              // test hook: this tile never publishes (-1: none)
 };
 
+// One sweep of a multi-sweep launch ("phase"): sweep j advances one time
+// step in launch t when 0 <= t - offset < nt. Sweeps of a phase may be
+// forward or transposed, on different grids; the CTAs of launch t are split
+// over the sweeps' tiles (tile_base = first CTA of the sweep). A sweep with
+// offset > 0 consumes, at its step s, gather samples another sweep of the
+// same phase produced in an earlier launch (lockstep chaining).
+struct Job {
+    int adj;                 // 0: forward sweep, 1: transposed sweep
+    int offset;              // launch index of the sweep's first step
+    int nt;
+    int tiles_x, tile_base, tiles;
+    FwdArgs fa;              // forward: grid, lines, gathers (field pointers unused)
+    AdjArgs aa;              // transposed: grid, lines, gathers
+    float *f[2][3];          // ping-pong field triples (origin-offset pointers)
+};
+constexpr int kMaxJobs = 8;
+
 // Tile configurations of the step kernels: (id, TX, TZ, threads per CTA).
 // Every configuration computes bit-identical results; the runtime picks one
 // per grid and direction by timing them (autotune). TX, TZ >= 2k keeps the
@@ -117,6 +134,9 @@ cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, i
 cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, int cfg,
                                cudaStream_t s);
 int persist_capacity(int R, int cfg, bool adj);   // co-resident CTAs of a persistent kernel
+// launch t of a phase: jobs (device array) with njobs entries, total_tiles CTAs
+cudaError_t launch_multi(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
+                         cudaStream_t s, bool pdl);
 cudaError_t prepare_kernels();                     // dynamic shared-memory limits (once per device)
 
 // per-R instantiations (stencil_r<R>.cu)
@@ -125,6 +145,7 @@ cudaError_t prepare_kernels();                     // dynamic shared-memory limi
     cudaError_t stencil_adj_step_r##RR(const AdjArgs &, int, cudaStream_t, bool);               \
     cudaError_t stencil_fwd_persist_r##RR(const FwdArgs &, const PersistArgs &, int, cudaStream_t); \
     cudaError_t stencil_adj_persist_r##RR(const AdjArgs &, const PersistArgs &, int, cudaStream_t); \
+    cudaError_t stencil_multi_r##RR(const Job *, int, int, int, int, cudaStream_t, bool);       \
     int stencil_capacity_r##RR(int, bool);                                                      \
     cudaError_t stencil_prepare_r##RR();
 SSX_DECLARE_R(1)
