@@ -739,7 +739,8 @@ int run_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw) {
         inits += w.adj ? 1 : 0;
     }
     c->st.sweeps += (long long)sw.size() - 1;   // run_cached counts one
-    return run_cached(c, "phase" + key, info.T + inits, info.T, pts, enqueue);
+    return run_cached(c, "phase" + std::to_string(info.cfg) + key, info.T + inits, info.T, pts,
+                      enqueue);
 }
 
 bool fused(ssx_ctx *c) { return c->sweep_mode != SSX_SWEEP_PERSISTENT; }
@@ -927,17 +928,21 @@ void drop_phases(ssx_ctx *c) {
     c->phases.clear();
 }
 
-void reset_choices(ssx_ctx *c) {
-    for (DGrid *G : {&c->full, &c->ss.g, &c->sr.g, &c->sm.g}) G->cfg[0] = G->cfg[1] = -1;
-    drop_phases(c);
-}
-
 void drop_graphs(ssx_ctx *c) {
     drop_phases(c);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     c->graph_nodes.clear();
 }
+
+// Forget tuned configurations. The captured graphs embed the configuration
+// and the phase job tables, so they go too (before the tables are freed).
+void reset_choices(ssx_ctx *c) {
+    if (c->s) cudaStreamSynchronize(c->s);
+    for (DGrid *G : {&c->full, &c->ss.g, &c->sr.g, &c->sm.g}) G->cfg[0] = G->cfg[1] = -1;
+    drop_graphs(c);
+}
+
 
 }  // namespace
 
@@ -1035,6 +1040,7 @@ int ssx_set_velocity_model(ssx_ctx *c, const float *v_dev, double rho) {
         }
         c->v_max = vm;
         c->rho = rho;
+        drop_graphs(c);   // captured sweeps and job tables hold the old coefficients
         TRY(grid_fill(c, c->full));
         if (c->have_geom) {
             TRY(grid_fill(c, c->ss.g));

@@ -303,3 +303,18 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     ctx.set_sweep_mode(ssx.SWEEP_AUTO)
     st = ctx.stats()
     assert len(st["tile_cfg"]) == 6
+
+
+def test_model_change_refreshes_captured_sweeps(ssx, oracle):
+    """Captured sweeps hold the grid coefficients: a new model (and density)
+    on the same context must give the new operator."""
+    spec = W.small(order=4, nt=150)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 21)
+    ctx.forward(dev(h))
+    spec2 = dataclasses.replace(spec, rho=2.5, model="homogeneous", v0=1.8)
+    ctx.set_velocity_model(torch.as_tensor(W.velocity(spec2), dtype=torch.float32, device="cuda"),
+                           spec2.rho)
+    P2 = oracle.Problem(spec2, W.velocity(spec2))
+    assert rel(ctx.forward(dev(h)), P2.S(h)) <= TOL
+    assert rel(ctx.normal_apply(ssx.MODE_PCG, 0.1, dev(h)), P2.N(h, 0.1)) <= TOL
