@@ -104,8 +104,8 @@ struct ssx_ctx {
     // multi-sweep phases: tile configuration and device job table per phase
     struct PhaseInfo {
         int cfg = -1;
-        Job *jobs = nullptr;
-        int njobs = 0, total = 0, T = 0;
+        JobSet jobs{};
+        int total = 0, T = 0;
     };
     std::unordered_map<std::string, PhaseInfo> phases;
 
@@ -568,12 +568,14 @@ Sweep adj_sweep(DGrid &G, const Line &src, double *hb, double *fb, const Line &r
     return Sweep{&G, true, offset, src, rec, nullptr, nullptr, nullptr, nullptr, hb, fb, yp, yv};
 }
 
-std::vector<Job> make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet) {
-    std::vector<Job> jobs(sw.size());
+JobSet make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, int *total) {
+    JobSet jobs;
+    memset(&jobs, 0, sizeof jobs);
+    jobs.njobs = (int)sw.size();
     int base = 0;
     for (size_t j = 0; j < sw.size(); j++) {
         const Sweep &w = sw[j];
-        Job &J = jobs[j];
+        Job &J = jobs.job[j];
         memset(&J, 0, sizeof J);
         J.adj = w.adj ? 1 : 0;
         J.offset = w.offset;
@@ -604,6 +606,7 @@ std::vector<Job> make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bo
             J.fa.outv = w.outv;
         }
     }
+    *total = base;
     return jobs;
 }
 
@@ -615,7 +618,7 @@ int phase_len(ssx_ctx *c, const std::vector<Sweep> &sw) {
 
 // the launches of a phase: transposed sweeps get their initial state (the
 // transposed sampling of their last data sample) just before their first step
-int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const Job *djobs, int total, int T,
+int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const JobSet &jobs, int total, int T,
                   int cfg, cudaStream_t s, bool with_init) {
     for (int t = 0; t < T; t++) {
         if (with_init)
@@ -631,15 +634,8 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const Job *djobs, in
                     a.vz_in = w.G->f[0][2];
                     CK(launch_adj_init(a, c->gd.nt, s));
                 }
-        CK(launch_multi(djobs, (int)sw.size(), total, t, c->R, cfg, s, true));
+        CK(launch_multi(jobs, total, t, c->R, cfg, s, true));
     }
-    return SSX_OK;
-}
-
-int upload_jobs(ssx_ctx *c, const std::vector<Job> &jobs, Job **dst) {
-    if (!*dst) CK(cudaMalloc(dst, kMaxJobs * sizeof(Job)));
-    CK(cudaMemcpyAsync(*dst, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, c->s));
-    CK(cudaStreamSynchronize(c->s));
     return SSX_OK;
 }
 
@@ -649,7 +645,6 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
         *best_cfg = c->forced_cfg;
         return SSX_OK;
     }
-    Job *tmp = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -657,15 +652,12 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
     float best = 1e30f;
     int rc = SSX_OK;
     for (int k = 0; k < kNumTileCfgs && rc == SSX_OK; k++) {
-        std::vector<Job> jobs = make_jobs(c, sw, k, true);
         int total = 0;
-        for (auto &J : jobs) total += J.tiles;
-        rc = upload_jobs(c, jobs, &tmp);
-        if (rc != SSX_OK) break;
+        const JobSet jobs = make_jobs(c, sw, k, true, &total);
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_phase(c, sw, tmp, total, T, k, c->s, false);
+        rc = enqueue_phase(c, sw, jobs, total, T, k, c->s, false);
         cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
         if (rc != SSX_OK) break;
         CK(ec);
@@ -688,7 +680,6 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
             *best_cfg = k;
         }
     }
-    if (tmp) cudaFree(tmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
@@ -710,14 +701,12 @@ int run_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw) {
     if (it == c->phases.end()) {
         ssx_ctx::PhaseInfo info;
         TRY(tune_phase(c, sw, &info.cfg));
-        std::vector<Job> jobs = make_jobs(c, sw, info.cfg, false);
-        info.njobs = (int)jobs.size();
-        for (auto &J : jobs) info.total += J.tiles;
+        if (sw.size() > (size_t)kMaxJobs) return fail(c, SSX_ERR_ARG, "too many sweeps in a phase");
+        info.jobs = make_jobs(c, sw, info.cfg, false, &info.total);
         info.T = phase_len(c, sw);
-        TRY(upload_jobs(c, jobs, &info.jobs));
         it = c->phases.emplace(key, info).first;
     }
-    const ssx_ctx::PhaseInfo info = it->second;
+    const ssx_ctx::PhaseInfo &info = it->second;
     const int nt = c->gd.nt;
     auto enqueue = [&, nt](cudaStream_t s) -> int {
         for (const Sweep &w : sw) {
@@ -922,11 +911,7 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
     return SSX_OK;
 }
 
-void drop_phases(ssx_ctx *c) {
-    for (auto &kv : c->phases)
-        if (kv.second.jobs) cudaFree(kv.second.jobs);
-    c->phases.clear();
-}
+void drop_phases(ssx_ctx *c) { c->phases.clear(); }
 
 void drop_graphs(ssx_ctx *c) {
     drop_phases(c);

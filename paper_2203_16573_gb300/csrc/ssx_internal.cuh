@@ -104,7 +104,13 @@ struct Job {
     AdjArgs aa;              // transposed: grid, lines, gathers
     float *f[2][3];          // ping-pong field triples (origin-offset pointers)
 };
-constexpr int kMaxJobs = 8;
+constexpr int kMaxJobs = 4;
+// The sweeps of a phase, passed by value as the kernel parameter (constant
+// bank): a CTA reads its sweep's arguments without a global-memory round trip.
+struct JobSet {
+    Job job[kMaxJobs];
+    int njobs;
+};
 
 // Tile configurations of the step kernels: (id, TX, TZ, threads per CTA).
 // Every configuration computes bit-identical results; the runtime picks one
@@ -134,8 +140,8 @@ cudaError_t launch_fwd_persist(const FwdArgs &a, const PersistArgs &pa, int R, i
 cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, int cfg,
                                cudaStream_t s);
 int persist_capacity(int R, int cfg, bool adj);   // co-resident CTAs of a persistent kernel
-// launch t of a phase: jobs (device array) with njobs entries, total_tiles CTAs
-cudaError_t launch_multi(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
+// launch t of a phase (total_tiles CTAs)
+cudaError_t launch_multi(const JobSet &jobs, int total_tiles, int t, int R, int cfg,
                          cudaStream_t s, bool pdl);
 cudaError_t prepare_kernels();                     // dynamic shared-memory limits (once per device)
 
@@ -145,7 +151,7 @@ cudaError_t prepare_kernels();                     // dynamic shared-memory limi
     cudaError_t stencil_adj_step_r##RR(const AdjArgs &, int, cudaStream_t, bool);               \
     cudaError_t stencil_fwd_persist_r##RR(const FwdArgs &, const PersistArgs &, int, cudaStream_t); \
     cudaError_t stencil_adj_persist_r##RR(const AdjArgs &, const PersistArgs &, int, cudaStream_t); \
-    cudaError_t stencil_multi_r##RR(const Job *, int, int, int, int, cudaStream_t, bool);       \
+    cudaError_t stencil_multi_r##RR(const JobSet &, int, int, int, cudaStream_t, bool);         \
     int stencil_capacity_r##RR(int, bool);                                                      \
     cudaError_t stencil_prepare_r##RR();
 SSX_DECLARE_R(1)

@@ -104,9 +104,9 @@ cudaError_t launch_adj_persist(const AdjArgs &a, const PersistArgs &pa, int R, i
     SSX_BY_R(stencil_adj_persist, a, pa, cfg, s)
     return cudaErrorInvalidValue;
 }
-cudaError_t launch_multi(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
+cudaError_t launch_multi(const JobSet &jobs, int total_tiles, int t, int R, int cfg,
                          cudaStream_t s, bool pdl) {
-    SSX_BY_R(stencil_multi, jobs, njobs, total_tiles, t, cfg, s, pdl)
+    SSX_BY_R(stencil_multi, jobs, total_tiles, t, cfg, s, pdl)
     return cudaErrorInvalidValue;
 }
 int persist_capacity(int R, int cfg, bool adj) {

@@ -598,45 +598,35 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
     }
 }
 
-// One time step of every sweep of a phase (launch t). The CTA finds its
-// sweep, copies that sweep's arguments to shared memory (so the tile code
-// reads them without global loads that stores could alias), and steps its
-// tile if the sweep is active in this launch.
+// One time step of every sweep of a phase (launch t). The sweeps arrive as
+// the kernel parameter; the CTA finds its sweep and steps its tile if that
+// sweep is active in this launch.
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_multi(const Job *__restrict__ jobs, int njobs, int t) {
+__global__ void __launch_bounds__(NT) k_multi(const JobSet P, int t) {
     griddep_launch();
-    __shared__ Job sj;
-    __shared__ int s_j;
-    if (threadIdx.x == 0) {
-        int j = 0;
-        while (j + 1 < njobs && (int)blockIdx.x >= __ldg(&jobs[j + 1].tile_base)) j++;
-        s_j = j;
-    }
-    __syncthreads();
-    {
-        const int *src = reinterpret_cast<const int *>(jobs + s_j);
-        int *dst = reinterpret_cast<int *>(&sj);
-        for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
-    }
-    __syncthreads();
-    const int st = t - sj.offset;
-    if (st < 0 || st >= sj.nt) return;
-    const int tl = blockIdx.x - sj.tile_base;
-    const int i0 = (tl % sj.tiles_x) * TX, k0 = (tl / sj.tiles_x) * TZ;
+    int j = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxJobs; q++)
+        if (q < P.njobs && (int)blockIdx.x >= P.job[q].tile_base) j = q;
+    const Job &J = P.job[j];
+    const int st = t - J.offset;
+    if (st < 0 || st >= J.nt) return;
+    const int tl = blockIdx.x - J.tile_base;
+    const int i0 = (tl % J.tiles_x) * TX, k0 = (tl / J.tiles_x) * TZ;
     const bool odd = st & 1;
     StepIO io;
-    io.p_in = odd ? sj.f[1][0] : sj.f[0][0];
-    io.vx_in = odd ? sj.f[1][1] : sj.f[0][1];
-    io.vz_in = odd ? sj.f[1][2] : sj.f[0][2];
-    io.p_out = odd ? sj.f[0][0] : sj.f[1][0];
-    io.vx_out = odd ? sj.f[0][1] : sj.f[1][1];
-    io.vz_out = odd ? sj.f[0][2] : sj.f[1][2];
-    io.n = sj.adj ? sj.nt - 1 - st : st;
+    io.p_in = odd ? J.f[1][0] : J.f[0][0];
+    io.vx_in = odd ? J.f[1][1] : J.f[0][1];
+    io.vz_in = odd ? J.f[1][2] : J.f[0][2];
+    io.p_out = odd ? J.f[0][0] : J.f[1][0];
+    io.vx_out = odd ? J.f[0][1] : J.f[1][1];
+    io.vz_out = odd ? J.f[0][2] : J.f[1][2];
+    io.n = J.adj ? J.nt - 1 - st : st;
     griddep_wait();
-    if (sj.adj)
-        adj_tile<R, TX, TZ, NT>(sj.aa, io, i0, k0, tile_smem<R, TX, TZ>());
+    if (J.adj)
+        adj_tile<R, TX, TZ, NT>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>());
     else
-        fwd_tile<R, TX, TZ, NT>(sj.fa, io, i0, k0, tile_smem<R, TX, TZ>());
+        fwd_tile<R, TX, TZ, NT>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>());
 }
 
 // ----------------------------------------------------------- launchers --
@@ -672,7 +662,7 @@ struct Stencil {
         return launch<AdjArgs>(k_adj<R, TX, TZ, NT>, grid, NT, smem<TX, TZ>(), s, pdl, a);
     }
     template <int TX, int TZ, int NT>
-    static cudaError_t multi(const Job *jobs, int njobs, int total, int t, cudaStream_t s, bool pdl) {
+    static cudaError_t multi(const JobSet &jobs, int total, int t, cudaStream_t s, bool pdl) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(total);
         cfg.blockDim = dim3(NT);
@@ -683,7 +673,7 @@ struct Stencil {
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = pdl ? at : nullptr;
         cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT>, jobs, njobs, t);
+        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT>, jobs, t);
     }
     template <int TX, int TZ, int NT>
     static cudaError_t fwd_persist(const FwdArgs &a, const PersistArgs &pa, cudaStream_t s) {
@@ -755,8 +745,8 @@ struct Stencil {
             default: return cudaErrorInvalidValue;                                                 \
         }                                                                                          \
     }                                                                                              \
-    cudaError_t stencil_multi_r##RR(const Job *jobs, int njobs, int total, int t, int cfg,         \
-                                    cudaStream_t s, bool pdl) {                                    \
+    cudaError_t stencil_multi_r##RR(const JobSet &jobs, int total, int t, int cfg, cudaStream_t s, \
+                                    bool pdl) {                                                    \
         switch (cfg) {                                                                             \
             SSX_TILE_CONFIGS(SSX_CASE_MULTI)                                                       \
             default: return cudaErrorInvalidValue;                                                 \
@@ -778,7 +768,7 @@ struct Stencil {
 #define SSX_CASE_ADJ_STEP(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_step<TX, TZ, NT>(a, s, pdl);
 #define SSX_CASE_FWD_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_persist<TX, TZ, NT>(a, pa, s);
 #define SSX_CASE_ADJ_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_persist<TX, TZ, NT>(a, pa, s);
-#define SSX_CASE_MULTI(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi<TX, TZ, NT>(jobs, njobs, total, t, s, pdl);
+#define SSX_CASE_MULTI(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi<TX, TZ, NT>(jobs, total, t, s, pdl);
 #define SSX_CASE_CAPACITY(id, TX, TZ, NT) case id: return Stencil<SSX_R>::capacity<TX, TZ, NT>(adj);
 #define SSX_CASE_PREPARE(id, TX, TZ, NT) if (e == cudaSuccess) e = Stencil<SSX_R>::prepare<TX, TZ, NT>();
 
