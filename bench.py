@@ -110,6 +110,23 @@ def config_of(spec, n_gpus, extra=None):
     return cfg
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job rate of N independent replicas: every rank solves `steps`
+    problems; the job takes as long as its slowest rank."""
+    return world * steps / (t_max_ms / 1000.0)
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -242,14 +259,9 @@ def run_ours(args):
     clk = clocks.stop()
     ctx.set_timing(False)
     st = ctx.stats()
-    t_max = t_dev
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = reduce_max(t_dev, dev)
     ms_per_step = t_max / args.steps
-    value = world * args.steps / (t_max / 1000.0)
+    value = replica_throughput(world, args.steps, t_max)
 
     # ---- end to end through the public API with host buffers ----
     d_host = d.cpu().pin_memory()
@@ -268,12 +280,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         t_e2e += e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = world * e2e_steps / (t_e2e / 1000.0)
+    t_e2e = reduce_max(t_e2e, dev)
+    e2e_value = replica_throughput(world, e2e_steps, t_e2e)
 
     # ---- roofline of the stencil step kernels (event-timed sweeps) ----
     hbm, peak_kind = peaks()

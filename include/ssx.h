@@ -139,6 +139,18 @@ int ssx_adjoint(ssx_ctx *ctx, const double *d_dev, double *h_dev);
  * Gathers are [nt][n_rec] for SSX_W_D, [nt][n_line] otherwise. */
 int ssx_weight_apply(ssx_ctx *ctx, int which, const double *in_dev, double *out_dev);
 
+/* out = Lambda~ in (transpose = 0, eqn:lamtilde) or Lambda~^T in (transpose =
+ * 1, eqn:lamtransp): the unsymmetrised thin-slab pressure-to-source map on
+ * the source line, -8 (V+_{zs,zs+dz})^T Pi_0 S+ Pi_1^T and its exact
+ * transpose. Their mean is W~_m^{-1}. Gathers [nt][n_line]. */
+int ssx_lambda_apply(ssx_ctx *ctx, int transpose, const double *in_dev, double *out_dev);
+
+/* h = 4 (V+_{zs,zr})^T d: the time-reversal approximate inverse of S
+ * (eqn:approxinv; "multiply by -2, apply the transpose of V+, multiply by
+ * -2"): d [nt][n_rec] injected as a vertical load at the receivers, one
+ * reverse-time sweep, v_z read out on the source line into h [nt][n_line]. */
+int ssx_time_reversal_inverse(ssx_ctx *ctx, const double *d_dev, double *h_dev);
+
 /* g = M^{-1} r = D W~_m^{-1} D r, D = (I + alpha A^T A)^{-1/2}
  * (eqn:defprecond). alpha >= 0 multiplies ||A h||^2. */
 int ssx_precond_apply(ssx_ctx *ctx, double alpha, const double *r_dev, double *g_dev);

@@ -779,6 +779,30 @@ int op_W(ssx_ctx *c, int which, const double *in, double *out) {
     }
 }
 
+// Lambda~ (eqn:lamtilde) or its transpose (eqn:lamtransp) on the z_s slab:
+// velocity injection of r, one datum trace taken back through the other
+// trace's transposed injection, -8 (orientation sign as for the weights).
+int op_lambda(ssx_ctx *c, bool transpose, const double *in, double *out) {
+    Slab &sl = c->ss;
+    const Line pl = scaled(sl.plane, -8.0 * c->sgn);
+    if (!fused(c)) {
+        TRY(sim_fwd(c, sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv));
+        return transpose ? sim_adj(c, sl.g, pl, nullptr, out, sl.datum, sl.tv, nullptr)
+                         : sim_adj(c, sl.g, pl, nullptr, out, sl.datum, nullptr, sl.tp);
+    }
+    TRY(run_phase(c, "Lf", {fwd_sweep(sl.g, sl.plane, nullptr, in, sl.datum, sl.tp, sl.tv)}));
+    return transpose ? run_phase(c, "LTa", {adj_sweep(sl.g, pl, nullptr, out, sl.datum, sl.tv, nullptr)})
+                     : run_phase(c, "LNa", {adj_sweep(sl.g, pl, nullptr, out, sl.datum, nullptr, sl.tp)});
+}
+
+// 4 (V+_{zs,zr})^T d (eqn:approxinv): the data as a vertical load at the
+// receivers, one transposed sweep, the velocity-injection read-out on z_s
+int op_trinv(ssx_ctx *c, const double *d, double *h) {
+    const Line sl = scaled(c->src, 4.0);
+    if (!fused(c)) return sim_adj(c, c->full, sl, nullptr, h, c->rec, nullptr, d);
+    return run_phase(c, "TR", {adj_sweep(c->full, sl, nullptr, h, c->rec, nullptr, d)});
+}
+
 int set_D(ssx_ctx *c, double alpha) {
     if (c->D_alpha == alpha) return SSX_OK;
     const int n = c->geom.n_line;
@@ -1136,6 +1160,32 @@ int ssx_weight_apply(ssx_ctx *c, int which, const double *in, double *out) {
         CK(cudaMemcpyAsync(bi, in, bytes, cudaMemcpyDeviceToDevice, c->s));
         TRY(op_W(c, which, bi, bo));
         CK(cudaMemcpyAsync(out, bo, bytes, cudaMemcpyDeviceToDevice, c->s));
+        return check_sweeps(c);
+    };
+    return leave(c, body());
+}
+
+int ssx_lambda_apply(ssx_ctx *c, int transpose, const double *in, double *out) {
+    TRY(ready(c));
+    if (!in || !out) return fail(c, SSX_ERR_ARG, "null gather");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->tl1, in, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_lambda(c, transpose != 0, c->tl1, c->tl2));
+        CK(cudaMemcpyAsync(out, c->tl2, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        return check_sweeps(c);
+    };
+    return leave(c, body());
+}
+
+int ssx_time_reversal_inverse(ssx_ctx *c, const double *d_dev, double *h_dev) {
+    TRY(ready(c));
+    if (!d_dev || !h_dev) return fail(c, SSX_ERR_ARG, "null gather");
+    TRY(enter(c));
+    auto body = [&]() -> int {
+        CK(cudaMemcpyAsync(c->tr1, d_dev, rec_bytes(c), cudaMemcpyDeviceToDevice, c->s));
+        TRY(op_trinv(c, c->tr1, c->tl2));
+        CK(cudaMemcpyAsync(h_dev, c->tl2, line_bytes(c), cudaMemcpyDeviceToDevice, c->s));
         return check_sweeps(c);
     };
     return leave(c, body());

@@ -28,7 +28,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
            "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode",
-           "ssx_set_tile_config"]
+           "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse"]
 
 
 class SSXError(RuntimeError):
@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH):
         "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
         "ssx_set_sweep_mode": ([vp, i], i),
         "ssx_set_tile_config": ([vp, i], i),
+        "ssx_lambda_apply": ([vp, i, vp, vp], i),
+        "ssx_time_reversal_inverse": ([vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -193,6 +195,18 @@ class Context:
         chk = self._rec if which == W_D else self._line
         out = self._empty(self.n_rec if which == W_D else self.n_line) if out is None else out
         self._check(self._lib.ssx_weight_apply(self._c, which, chk(x, "in"), chk(out, "out")))
+        return out
+
+    def lambda_apply(self, x, transpose=False, out=None):
+        out = self._empty(self.n_line) if out is None else out
+        self._check(self._lib.ssx_lambda_apply(self._c, 1 if transpose else 0, self._line(x, "in"),
+                                               self._line(out, "out")))
+        return out
+
+    def time_reversal_inverse(self, d, out=None):
+        out = self._empty(self.n_line) if out is None else out
+        self._check(self._lib.ssx_time_reversal_inverse(self._c, self._rec(d, "d"),
+                                                        self._line(out, "h")))
         return out
 
     def precond_apply(self, alpha, r, out=None):

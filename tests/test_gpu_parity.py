@@ -318,3 +318,19 @@ def test_model_change_refreshes_captured_sweeps(ssx, oracle):
     P2 = oracle.Problem(spec2, W.velocity(spec2))
     assert rel(ctx.forward(dev(h)), P2.S(h)) <= TOL
     assert rel(ctx.normal_apply(ssx.MODE_PCG, 0.1, dev(h)), P2.N(h, 0.1)) <= TOL
+
+
+# -------------------------------------------------- diagnostics (NEXT-4) --
+@pytest.mark.parametrize("transpose", [False, True])
+def test_lambda_tilde_parity(ssx, oracle, transpose):
+    spec = frac_spec(8)
+    ctx, P = make(ssx, oracle, spec)
+    x = W.smooth_random_gather(spec.nt, spec.n_line, 22)
+    assert rel(ctx.lambda_apply(dev(x), transpose), P.lambda_tilde(x, transpose)) <= TOL
+
+
+def test_time_reversal_inverse_parity(ssx, oracle):
+    spec = W.small(order=8, nt=400)
+    ctx, P = make(ssx, oracle, spec)
+    d = P.point_source_data(W.ricker(spec), spec.x_d, spec.z_d)
+    assert rel(ctx.time_reversal_inverse(dev(d)), P.time_reversal_inverse(d)) <= TOL
