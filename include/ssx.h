@@ -173,6 +173,23 @@ int ssx_solve_source_subproblem(ssx_ctx *ctx, const double *d_dev, double alpha,
                                 int maxit, double rtol, int mode, double *h_out_dev,
                                 double *resid_hist_host, int *iters_out);
 
+/* Solve n independent source subproblems at once (a survey's shots, or the
+ * requests of a server), one per context (ctxs[i]: model and geometry set;
+ * grids, nt and geometry may differ, the space order may not; no context twice).
+ * Every phase of Algorithm 1 runs as one kernel launch per time step over all
+ * active shots' sweeps (one shot's forward and adjoint sweeps advance in
+ * lockstep inside those launches); the Krylov vectors, scalars and stopping
+ * tests are per shot and a shot leaves the launches once it has stopped, so
+ * each result equals the shot's solo ssx_solve_source_subproblem.
+ * d_dev[i] / h_out_dev[i]: device gathers of shot i; alphas[i] host array;
+ * hist (host, may be NULL): n x (maxit + 1) residual norms, row i for shot i;
+ * iters / status (host, may be NULL): per-shot updates and ssx_status.
+ * All work runs on ctxs[0]'s stream, ordered after every shot's stream.
+ * Returns SSX_OK if the batch ran (per-shot outcomes in status). */
+int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, const double *alphas,
+                    int maxit, double rtol, int mode, double *const *h_out_dev, double *hist,
+                    int *iters, int *status);
+
 /* d = pressure gather on z_r of a point pressure source w(t) delta(x - x_d)
  * delta(z - z_d) (fixture of the section "Creating downgoing fields").
  * wavelet_dev: nt float64 samples (device), sample n integrated over the

@@ -104,8 +104,9 @@ struct ssx_ctx {
     // multi-sweep phases: tile configuration and device job table per phase
     struct PhaseInfo {
         int cfg = -1;
-        JobSet jobs{};
-        int total = 0, T = 0;
+        JobSet jobs{};          // small phases: by-value kernel parameter
+        Job *dtab = nullptr;    // large phases (batches): device table
+        int njobs = 0, total = 0, T = 0;
     };
     std::unordered_map<std::string, PhaseInfo> phases;
 
@@ -557,29 +558,28 @@ struct Sweep {
     double *outp, *outv;         // forward traces
     double *hb, *fb;             // transposed injections
     const double *yp, *yv;       // transposed data
+    int nt;                      // time steps (0: the context's)
 };
 
 Sweep fwd_sweep(DGrid &G, const Line &src, const double *hs, const double *fs, const Line &rec,
                 double *outp, double *outv, int offset = 0) {
-    return Sweep{&G, false, offset, src, rec, hs, fs, outp, outv, nullptr, nullptr, nullptr, nullptr};
+    return Sweep{&G, false, offset, src, rec, hs, fs, outp, outv, nullptr, nullptr, nullptr, nullptr, 0};
 }
 Sweep adj_sweep(DGrid &G, const Line &src, double *hb, double *fb, const Line &rec,
                 const double *yp, const double *yv, int offset = 0) {
-    return Sweep{&G, true, offset, src, rec, nullptr, nullptr, nullptr, nullptr, hb, fb, yp, yv};
+    return Sweep{&G, true, offset, src, rec, nullptr, nullptr, nullptr, nullptr, hb, fb, yp, yv, 0};
 }
 
-JobSet make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, int *total) {
-    JobSet jobs;
-    memset(&jobs, 0, sizeof jobs);
-    jobs.njobs = (int)sw.size();
+std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, int *total) {
+    std::vector<Job> jobs(sw.size());
     int base = 0;
     for (size_t j = 0; j < sw.size(); j++) {
         const Sweep &w = sw[j];
-        Job &J = jobs.job[j];
+        Job &J = jobs[j];
         memset(&J, 0, sizeof J);
         J.adj = w.adj ? 1 : 0;
         J.offset = w.offset;
-        J.nt = c->gd.nt;
+        J.nt = w.nt;
         J.tiles_x = (w.G->L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx;
         J.tiles = J.tiles_x * ((w.G->L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz);
         J.tile_base = base;
@@ -610,16 +610,41 @@ JobSet make_jobs(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, 
     return jobs;
 }
 
-int phase_len(ssx_ctx *c, const std::vector<Sweep> &sw) {
+// Kernel arguments of a phase: small phases by value, large ones in a device table.
+struct PhaseArgs {
+    JobSet set{};
+    Job *dtab = nullptr;
+    int njobs = 0, total = 0;
+};
+
+int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
+               Job **dtab) {
+    std::vector<Job> jobs = make_jobs(sw, cfg, quiet, &pa->total);
+    pa->njobs = (int)jobs.size();
+    if (jobs.size() <= (size_t)kMaxJobs) {
+        memset(&pa->set, 0, sizeof pa->set);
+        pa->set.njobs = pa->njobs;
+        for (size_t j = 0; j < jobs.size(); j++) pa->set.job[j] = jobs[j];
+        pa->dtab = nullptr;
+        return SSX_OK;
+    }
+    if (!*dtab) CK(cudaMalloc(dtab, jobs.size() * sizeof(Job)));
+    CK(cudaMemcpyAsync(*dtab, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    pa->dtab = *dtab;
+    return SSX_OK;
+}
+
+int phase_len(const std::vector<Sweep> &sw) {
     int T = 0;
-    for (const Sweep &w : sw) T = std::max(T, w.offset + c->gd.nt);
+    for (const Sweep &w : sw) T = std::max(T, w.offset + w.nt);
     return T;
 }
 
 // the launches of a phase: transposed sweeps get their initial state (the
 // transposed sampling of their last data sample) just before their first step
-int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const JobSet &jobs, int total, int T,
-                  int cfg, cudaStream_t s, bool with_init) {
+int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int T, int cfg,
+                  cudaStream_t s, bool with_init) {
     for (int t = 0; t < T; t++) {
         if (with_init)
             for (const Sweep &w : sw)
@@ -632,9 +657,12 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const JobSet &jobs, 
                     a.p_in = w.G->f[0][0];
                     a.vx_in = w.G->f[0][1];
                     a.vz_in = w.G->f[0][2];
-                    CK(launch_adj_init(a, c->gd.nt, s));
+                    CK(launch_adj_init(a, w.nt, s));
                 }
-        CK(launch_multi(jobs, total, t, c->R, cfg, s, true));
+        if (pa.dtab)
+            CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, true));
+        else
+            CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, true));
     }
     return SSX_OK;
 }
@@ -648,16 +676,18 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int T = std::min(phase_len(c, sw), 48);
+    const int T = std::min(phase_len(sw), 48);
     float best = 1e30f;
     int rc = SSX_OK;
+    Job *tmp = nullptr;
     for (int k = 0; k < kNumTileCfgs && rc == SSX_OK; k++) {
-        int total = 0;
-        const JobSet jobs = make_jobs(c, sw, k, true, &total);
+        PhaseArgs pa;
+        rc = phase_args(c, sw, k, true, &pa, &tmp);
+        if (rc != SSX_OK) break;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_phase(c, sw, jobs, total, T, k, c->s, false);
+        rc = enqueue_phase(c, sw, pa, T, k, c->s, false);
         cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
         if (rc != SSX_OK) break;
         CK(ec);
@@ -680,19 +710,22 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
             *best_cfg = k;
         }
     }
+    if (tmp) cudaFree(tmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
 }
 
-int run_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw) {
-    for (const Sweep &w : sw)
+int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
+    for (Sweep &w : sw) {
         if (!w.G->ready) return fail(c, SSX_ERR_ARG, "velocity model not set");
+        if (w.nt == 0) w.nt = c->gd.nt;
+    }
     std::string key = name;
     for (const Sweep &w : sw) {
         char b[200];
-        snprintf(b, sizeof b, "|%p%d%d:%d:%d:%g:%p:%p:%p:%p:%p:%p:%p:%p", (void *)w.G, w.adj,
-                 w.offset, w.src.kp, w.rec.kp, (double)w.src.scale, (const void *)w.hs,
+        snprintf(b, sizeof b, "|%p%d%d:%d:%d:%d:%g:%p:%p:%p:%p:%p:%p:%p:%p", (void *)w.G, w.adj,
+                 w.offset, w.nt, w.src.kp, w.rec.kp, (double)w.src.scale, (const void *)w.hs,
                  (const void *)w.fs, (void *)w.outp, (void *)w.outv, (void *)w.hb, (void *)w.fb,
                  (const void *)w.yp, (const void *)w.yv);
         key += b;
@@ -701,30 +734,37 @@ int run_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw) {
     if (it == c->phases.end()) {
         ssx_ctx::PhaseInfo info;
         TRY(tune_phase(c, sw, &info.cfg));
-        if (sw.size() > (size_t)kMaxJobs) return fail(c, SSX_ERR_ARG, "too many sweeps in a phase");
-        info.jobs = make_jobs(c, sw, info.cfg, false, &info.total);
-        info.T = phase_len(c, sw);
+        PhaseArgs pa;
+        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab));
+        info.jobs = pa.set;
+        info.njobs = pa.njobs;
+        info.total = pa.total;
+        info.T = phase_len(sw);
         it = c->phases.emplace(key, info).first;
     }
     const ssx_ctx::PhaseInfo &info = it->second;
-    const int nt = c->gd.nt;
-    auto enqueue = [&, nt](cudaStream_t s) -> int {
+    PhaseArgs pa;
+    pa.set = info.jobs;
+    pa.dtab = info.dtab;
+    pa.njobs = info.njobs;
+    pa.total = info.total;
+    auto enqueue = [&](cudaStream_t s) -> int {
         for (const Sweep &w : sw) {
             const size_t E = w.G->L.elems();
-            const size_t nr = (size_t)nt * w.rec.n * sizeof(double);
-            const size_t ns = (size_t)nt * w.src.n * sizeof(double);
+            const size_t nr = (size_t)w.nt * w.rec.n * sizeof(double);
+            const size_t ns = (size_t)w.nt * w.src.n * sizeof(double);
             if (w.outp) CK(cudaMemsetAsync(w.outp, 0, nr, s));
             if (w.outv) CK(cudaMemsetAsync(w.outv, 0, nr, s));
             if (w.hb) CK(cudaMemsetAsync(w.hb, 0, ns, s));
             if (w.fb) CK(cudaMemsetAsync(w.fb, 0, ns, s));
             CK(cudaMemsetAsync(w.G->mem + E, 0, 3 * E * sizeof(float), s));
         }
-        return enqueue_phase(c, sw, info.jobs, info.total, info.T, info.cfg, s, true);
+        return enqueue_phase(c, sw, pa, info.T, info.cfg, s, true);
     };
     double pts = 0;
     long long inits = 0;
     for (const Sweep &w : sw) {
-        pts += (double)w.G->L.NX * w.G->L.NZ * nt;
+        pts += (double)w.G->L.NX * w.G->L.NZ * w.nt;
         inits += w.adj ? 1 : 0;
     }
     c->st.sweeps += (long long)sw.size() - 1;   // run_cached counts one
@@ -935,7 +975,11 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
     return SSX_OK;
 }
 
-void drop_phases(ssx_ctx *c) { c->phases.clear(); }
+void drop_phases(ssx_ctx *c) {
+    for (auto &kv : c->phases)
+        if (kv.second.dtab) cudaFree(kv.second.dtab);
+    c->phases.clear();
+}
 
 void drop_graphs(ssx_ctx *c) {
     drop_phases(c);
@@ -954,6 +998,232 @@ void reset_choices(ssx_ctx *c) {
 
 
 }  // namespace
+
+// ----------------------------------------------------------- batch solve --
+// Algorithm 1 for several independent source subproblems at once (shots of
+// a survey, or requests of a server), each on its own context: every PCG
+// phase is one launch per time step over the union of all active shots'
+// sweeps; the Krylov recurrences, scalars and stopping tests stay per shot,
+// and a shot leaves the launches once it stops. Each shot's arithmetic is the
+// same as in a solo solve.
+struct ShotRun {
+    ssx_ctx *c = nullptr;
+    double alpha = 0;
+    const double *d = nullptr;
+    double *h_out = nullptr;
+    double *hist = nullptr;   // host, maxit + 1 entries, may be null
+    int iters = 0;
+    int status = SSX_OK;
+    bool active = true;
+    double r0 = 0;
+    std::string msg;
+};
+
+enum PhaseKind { PK_R1, PK_R2, PK_RC, PK_M1, PK_M2, PK_N1, PK_N2, PK_NC1, PK_NC2 };
+
+void add_sweeps(ssx_ctx *c, int kind, double alpha, std::vector<Sweep> &out) {
+    Slab &r = c->sr, &s = c->ss, &m = c->sm;
+    const double sg = c->sgn;
+    auto push = [&](Sweep w) {
+        w.nt = c->gd.nt;
+        out.push_back(w);
+    };
+    switch (kind) {
+        case PK_R1: push(fwd_sweep(r.g, r.plane, nullptr, c->tr1, r.datum, r.tp, r.tv)); break;
+        case PK_R2:
+            push(adj_sweep(r.g, scaled(r.plane, -4.0 * sg), nullptr, c->tr2, r.datum, r.tv, r.tp));
+            push(adj_sweep(c->full, c->src, c->r, nullptr, c->rec, c->tr2, nullptr, 2));
+            break;
+        case PK_RC: push(adj_sweep(c->full, c->src, c->r, nullptr, c->rec, c->tr1, nullptr)); break;
+        case PK_M1: push(fwd_sweep(s.g, s.plane, nullptr, c->tl1, s.datum, s.tp, s.tv)); break;
+        case PK_M2:
+            push(adj_sweep(s.g, scaled(s.plane, -4.0 * sg), nullptr, c->tl2, s.datum, s.tv, s.tp));
+            break;
+        case PK_N1:
+            push(fwd_sweep(c->full, c->src, c->p, nullptr, c->rec, c->tr1, nullptr));
+            push(fwd_sweep(r.g, r.plane, nullptr, c->tr1, r.datum, r.tp, r.tv, 1));
+            if (alpha != 0.0) push(fwd_sweep(m.g, m.plane, c->tl1, nullptr, m.datum, m.tp, m.tv));
+            break;
+        case PK_N2:
+            push(adj_sweep(r.g, scaled(r.plane, -4.0 * sg), nullptr, c->tr2, r.datum, r.tv, r.tp));
+            push(adj_sweep(c->full, c->src, c->q, nullptr, c->rec, c->tr2, nullptr, 2));
+            if (alpha != 0.0)
+                push(adj_sweep(m.g, scaled(m.plane, -1.0 * sg), c->tl2, nullptr, m.datum, m.tv, m.tp));
+            break;
+        case PK_NC1: push(fwd_sweep(c->full, c->src, c->p, nullptr, c->rec, c->tr1, nullptr)); break;
+        case PK_NC2: push(adj_sweep(c->full, c->src, c->q, nullptr, c->rec, c->tr1, nullptr)); break;
+    }
+}
+
+int solve_batch(std::vector<ShotRun> &shots, int maxit, double rtol, int mode) {
+    ssx_ctx *L = shots[0].c;   // the lead context runs the launches on its stream
+    ssx_ctx *c = L;            // for CK/TRY error reporting
+    cudaStream_t s = L->s;
+    const bool pcg = mode == SSX_MODE_PCG;
+    auto nl = [](ShotRun &sh) { return (size_t)sh.c->gd.nt * sh.c->geom.n_line; };
+    auto phase = [&](const char *name, int kind) -> int {
+        std::vector<Sweep> sw;
+        for (auto &sh : shots)
+            if (sh.active) add_sweeps(sh.c, kind, sh.alpha, sw);
+        return sw.empty() ? SSX_OK : run_phase(L, name, sw);
+    };
+    auto each = [&](const std::function<int(ShotRun &)> &f) -> int {
+        for (auto &sh : shots)
+            if (sh.active) TRY(f(sh));
+        return SSX_OK;
+    };
+    auto read_scalars = [&]() -> int {
+        TRY(each([&](ShotRun &sh) -> int {
+            CK(cudaMemcpyAsync(sh.c->sc_host, sh.c->sc, SC_COUNT * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+            return SSX_OK;
+        }));
+        CK(cudaStreamSynchronize(s));
+        return SSX_OK;
+    };
+    // M^{-1}: g = D W~_m^{-1} D r (identity for plain CG)
+    auto precond = [&]() -> int {
+        if (!pcg)
+            return each([&](ShotRun &sh) -> int {
+                CK(cudaMemcpyAsync(sh.c->g, sh.c->r, nl(sh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                return SSX_OK;
+            });
+        TRY(each([&](ShotRun &sh) -> int {
+            CK(launch_colscale(sh.c->tl1, sh.c->r, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+            return SSX_OK;
+        }));
+        TRY(phase("bM1", PK_M1));
+        TRY(phase("bM2", PK_M2));
+        return each([&](ShotRun &sh) -> int {
+            CK(launch_colscale(sh.c->g, sh.c->tl2, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+            return SSX_OK;
+        });
+    };
+    // q = N p
+    auto normal = [&]() -> int {
+        if (pcg)
+            TRY(each([&](ShotRun &sh) -> int {
+                if (sh.alpha != 0.0) {
+                    CK(launch_colscale(sh.c->tl1, sh.c->p, sh.c->dist, sh.c->gd.nt, sh.c->geom.n_line, s));
+                    L->st.kernel_launches += 1;
+                }
+                return SSX_OK;
+            }));
+        TRY(phase(pcg ? "bN1" : "bNc1", pcg ? PK_N1 : PK_NC1));
+        TRY(phase(pcg ? "bN2" : "bNc2", pcg ? PK_N2 : PK_NC2));
+        return each([&](ShotRun &sh) -> int {
+            if (sh.alpha != 0.0) {
+                if (pcg)
+                    CK(launch_colscale_add(sh.c->q, sh.c->tl2, sh.c->dist, sh.alpha, sh.c->gd.nt,
+                                           sh.c->geom.n_line, s));
+                else
+                    CK(launch_colscale_add(sh.c->q, sh.c->p, sh.c->dist2, sh.alpha, sh.c->gd.nt,
+                                           sh.c->geom.n_line, s));
+                L->st.kernel_launches += 1;
+            }
+            return SSX_OK;
+        });
+    };
+    auto stop = [&](ShotRun &sh, int status, const std::string &msg) {
+        sh.status = status;
+        sh.msg = msg;
+        sh.active = false;
+    };
+
+    // set-up: h_0 = 0, r_0 = S^* d, g_0 = p_0 = M^{-1} r_0, q_0 = N p_0
+    for (auto &sh : shots)
+        if (pcg) TRY(set_D(sh.c, sh.alpha));
+    TRY(each([&](ShotRun &sh) -> int {
+        CK(cudaMemcpyAsync(sh.c->tr1, sh.d, rec_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(sh.c->h, 0, line_bytes(sh.c), s));
+        return SSX_OK;
+    }));
+    if (pcg) {
+        TRY(phase("bR1", PK_R1));
+        TRY(phase("bR2", PK_R2));
+    } else {
+        TRY(phase("bRc", PK_RC));
+    }
+    TRY(each([&](ShotRun &sh) -> int {   // r_0 = 0: done before any direction is formed
+        CK(launch_dot(sh.c->r, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_RR, s));
+        L->st.kernel_launches += 2;
+        return SSX_OK;
+    }));
+    TRY(read_scalars());
+    for (auto &sh : shots) {
+        sh.r0 = std::sqrt(sh.c->sc_host[SC_RR]);
+        if (sh.hist) sh.hist[0] = sh.r0;
+        if (!std::isfinite(sh.r0)) stop(sh, SSX_ERR_NONFINITE, "non-finite initial residual");
+        else if (sh.r0 == 0.0) stop(sh, SSX_OK, "");
+        else if (maxit == 0) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
+    }
+    TRY(precond());
+    TRY(each([&](ShotRun &sh) -> int {
+        CK(cudaMemcpyAsync(sh.c->p, sh.c->g, line_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
+        return SSX_OK;
+    }));
+    TRY(normal());
+    TRY(each([&](ShotRun &sh) -> int {
+        CK(launch_dot(sh.c->g, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_GR, s));
+        L->st.kernel_launches += 2;
+        return SSX_OK;
+    }));
+    for (int k = 0; k < maxit; k++) {
+        // alpha_k = <g,r>/<p,q>; h += alpha p; r -= alpha q; ||r||^2
+        TRY(each([&](ShotRun &sh) -> int {
+            double *sc = sh.c->sc;
+            CK(launch_dot(sh.c->p, sh.c->q, nl(sh), sh.c->partials, sc + SC_PQ, s));
+            CK(launch_pcg_alpha(sc, s));
+            CK(launch_pcg_update(sh.c->h, sh.c->r, sh.c->p, sh.c->q, nl(sh), sc, sh.c->partials, s));
+            L->st.kernel_launches += 5;
+            return SSX_OK;
+        }));
+        TRY(read_scalars());
+        bool any = false;
+        for (auto &sh : shots) {
+            if (!sh.active) continue;
+            const double *sh_sc = sh.c->sc_host;
+            if (sh_sc[SC_FLAG] != 0.0) {
+                if (!std::isfinite(sh_sc[SC_PQ]) || !std::isfinite(sh_sc[SC_GR])) {
+                    stop(sh, SSX_ERR_NONFINITE, "non-finite Krylov scalar");
+                } else {
+                    char b[160];
+                    snprintf(b, sizeof b, "PCG breakdown at k=%d: <p,q>=%.6e <g,r>=%.6e", k,
+                             sh_sc[SC_PQ], sh_sc[SC_GR]);
+                    stop(sh, SSX_ERR_BREAKDOWN, b);
+                }
+                continue;
+            }
+            const double rn = std::sqrt(sh_sc[SC_RR]);
+            sh.iters = k + 1;
+            if (sh.hist) sh.hist[k + 1] = rn;
+            if (!std::isfinite(rn)) stop(sh, SSX_ERR_NONFINITE, "non-finite residual");
+            else if (rn <= rtol * sh.r0) stop(sh, SSX_OK, "");
+            else if (k == maxit - 1) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
+            any = any || sh.active;
+        }
+        if (!any) break;
+        // g = M^{-1} r; beta = <g,r>_new/<g,r>; p = g + beta p; q = N p
+        TRY(precond());
+        TRY(each([&](ShotRun &sh) -> int {
+            double *sc = sh.c->sc;
+            CK(launch_dot(sh.c->g, sh.c->r, nl(sh), sh.c->partials, sc + SC_GRNEW, s));
+            CK(launch_pcg_beta(sc, s));
+            CK(launch_xpby(sh.c->p, sh.c->g, nl(sh), sc, s));
+            L->st.kernel_launches += 4;
+            return SSX_OK;
+        }));
+        TRY(normal());
+    }
+    for (auto &sh : shots) {
+        if (sh.h_out)
+            CK(cudaMemcpyAsync(sh.h_out, sh.c->h, line_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
+        if (sh.status != SSX_OK) sh.c->err = sh.msg;
+    }
+    return SSX_OK;
+}
 
 // ================================================================ C ABI ==
 extern "C" {
@@ -1225,68 +1495,61 @@ int ssx_solve_source_subproblem(ssx_ctx *c, const double *d_dev, double alpha, i
         (mode != SSX_MODE_PCG && mode != SSX_MODE_CG))
         return fail(c, SSX_ERR_ARG, "bad arguments");
     TRY(enter(c));
-    int done = 0;
-    auto body = [&]() -> int {
-        const size_t nl = (size_t)c->gd.nt * c->geom.n_line;
-        double *sc = c->sc, *sh = c->sc_host;
-        cudaStream_t s = c->s;
-        CK(cudaMemcpyAsync(c->tr1, d_dev, rec_bytes(c), cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(c->h, 0, line_bytes(c), s));
-        // r_0 = S^* d ; p_0 = g_0 = M^{-1} r_0 ; q_0 = N p_0
-        TRY(op_rhs(c, mode, c->tr1, c->r));
-        TRY(op_Minv(c, mode, alpha, c->r, c->g));
-        CK(cudaMemcpyAsync(c->p, c->g, line_bytes(c), cudaMemcpyDeviceToDevice, s));
-        TRY(op_N(c, mode, alpha, c->p, c->q));
-        CK(launch_dot(c->g, c->r, nl, c->partials, sc + SC_GR, s));
-        CK(launch_dot(c->r, c->r, nl, c->partials, sc + SC_RR, s));
-        c->st.kernel_launches += 4;
-        TRY(check_sweeps(c));
-        CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const double r0 = std::sqrt(sh[SC_RR]);
-        if (hist) hist[0] = r0;
-        if (!std::isfinite(r0)) return fail(c, SSX_ERR_NONFINITE, "non-finite initial residual");
-        if (r0 == 0.0) return SSX_OK;
-        for (int k = 0; k < maxit; k++) {
-            // alpha_k = <g,r>/<p,q>; h += alpha p; r -= alpha q
-            CK(launch_dot(c->p, c->q, nl, c->partials, sc + SC_PQ, s));
-            CK(launch_pcg_alpha(sc, s));
-            CK(launch_pcg_update(c->h, c->r, c->p, c->q, nl, sc, c->partials, s));
-            c->st.kernel_launches += 5;
-            TRY(check_sweeps(c));   // copies the sweep flag and synchronises
-            CK(cudaMemcpyAsync(sh, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            if (sh[SC_FLAG] != 0.0) {
-                if (!std::isfinite(sh[SC_PQ]) || !std::isfinite(sh[SC_GR]))
-                    return fail(c, SSX_ERR_NONFINITE, "non-finite Krylov scalar");
-                char b[160];
-                snprintf(b, sizeof b, "PCG breakdown at k=%d: <p,q>=%.6e <g,r>=%.6e", k,
-                         sh[SC_PQ], sh[SC_GR]);
-                return fail(c, SSX_ERR_BREAKDOWN, b);
-            }
-            const double rn = std::sqrt(sh[SC_RR]);
-            done = k + 1;
-            if (hist) hist[k + 1] = rn;
-            if (!std::isfinite(rn)) return fail(c, SSX_ERR_NONFINITE, "non-finite residual");
-            if (rn <= rtol * r0) return SSX_OK;
-            if (k == maxit - 1) break;
-            // g = M^{-1} r; beta = <g,r>_new/<g,r>; p = g + beta p; q = N p
-            TRY(op_Minv(c, mode, alpha, c->r, c->g));
-            CK(launch_dot(c->g, c->r, nl, c->partials, sc + SC_GRNEW, s));
-            CK(launch_pcg_beta(sc, s));
-            CK(launch_xpby(c->p, c->g, nl, sc, s));
-            c->st.kernel_launches += 4;
-            TRY(op_N(c, mode, alpha, c->p, c->q));
-        }
-        return fail(c, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
-    };
-    int rc = body();
-    if (iters) *iters = done;
-    if (rc == SSX_OK || rc == SSX_ERR_NOT_CONVERGED || rc == SSX_ERR_BREAKDOWN) {
-        cudaError_t e = cudaMemcpyAsync(h_out, c->h, line_bytes(c), cudaMemcpyDeviceToDevice, c->s);
-        if (e != cudaSuccess && rc == SSX_OK) rc = fail(c, SSX_ERR_CUDA, cudaGetErrorString(e));
-    }
+    std::vector<ShotRun> shots(1);
+    shots[0].c = c;
+    shots[0].alpha = alpha;
+    shots[0].d = d_dev;
+    shots[0].h_out = h_out;
+    shots[0].hist = hist;
+    int rc = solve_batch(shots, maxit, rtol, mode);
+    if (iters) *iters = shots[0].iters;
+    if (rc == SSX_OK) rc = shots[0].status;
     return leave(c, rc);
+}
+
+int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, const double *alphas,
+                    int maxit, double rtol, int mode, double *const *h_out_dev, double *hist,
+                    int *iters, int *status) {
+    if (!ctxs || n < 1 || !d_dev || !alphas || !h_out_dev || maxit < 0 || !(rtol >= 0) ||
+        (mode != SSX_MODE_PCG && mode != SSX_MODE_CG))
+        return SSX_ERR_ARG;
+    ssx_ctx *L = ctxs[0];
+    if (!L) return SSX_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i] || !d_dev[i] || !h_out_dev[i] || !(alphas[i] >= 0)) return fail(L, SSX_ERR_ARG, "bad shot arguments");
+        TRY(ready(ctxs[i]));
+        if (ctxs[i]->R != L->R) return fail(L, SSX_ERR_ARG, "all shots need the same space order");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return fail(L, SSX_ERR_ARG, "a context appears twice in the batch");
+    }
+    // order the lead stream after every shot's caller stream and internal stream
+    auto c = L;
+    for (int i = 0; i < n; i++) {
+        CK(cudaEventRecord(ctxs[i]->ev_in, ctxs[i]->user));
+        CK(cudaStreamWaitEvent(L->s, ctxs[i]->ev_in, 0));
+        CK(cudaEventRecord(ctxs[i]->ev_in, ctxs[i]->s));
+        CK(cudaStreamWaitEvent(L->s, ctxs[i]->ev_in, 0));
+    }
+    std::vector<ShotRun> shots(n);
+    for (int i = 0; i < n; i++) {
+        shots[i].c = ctxs[i];
+        shots[i].alpha = alphas[i];
+        shots[i].d = d_dev[i];
+        shots[i].h_out = h_out_dev[i];
+        shots[i].hist = hist ? hist + (size_t)i * (maxit + 1) : nullptr;
+    }
+    int rc = solve_batch(shots, maxit, rtol, mode);
+    for (int i = 0; i < n; i++) {
+        if (iters) iters[i] = shots[i].iters;
+        if (status) status[i] = rc == SSX_OK ? shots[i].status : rc;
+    }
+    // every shot's later work (caller stream and internal stream) after the batch
+    cudaEventRecord(L->ev_out, L->s);
+    for (int i = 0; i < n; i++) {
+        cudaStreamWaitEvent(ctxs[i]->user, L->ev_out, 0);
+        cudaStreamWaitEvent(ctxs[i]->s, L->ev_out, 0);
+    }
+    return rc;
 }
 
 int ssx_point_source_data(ssx_ctx *c, double x_d, double z_d, const double *w, double *d_dev) {

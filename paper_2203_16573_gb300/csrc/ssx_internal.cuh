@@ -143,6 +143,9 @@ int persist_capacity(int R, int cfg, bool adj);   // co-resident CTAs of a persi
 // launch t of a phase (total_tiles CTAs)
 cudaError_t launch_multi(const JobSet &jobs, int total_tiles, int t, int R, int cfg,
                          cudaStream_t s, bool pdl);
+// the same with the sweeps in a device table (any number of sweeps; batches)
+cudaError_t launch_multi_tab(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
+                             cudaStream_t s, bool pdl);
 cudaError_t prepare_kernels();                     // dynamic shared-memory limits (once per device)
 
 // per-R instantiations (stencil_r<R>.cu)
@@ -152,6 +155,7 @@ cudaError_t prepare_kernels();                     // dynamic shared-memory limi
     cudaError_t stencil_fwd_persist_r##RR(const FwdArgs &, const PersistArgs &, int, cudaStream_t); \
     cudaError_t stencil_adj_persist_r##RR(const AdjArgs &, const PersistArgs &, int, cudaStream_t); \
     cudaError_t stencil_multi_r##RR(const JobSet &, int, int, int, cudaStream_t, bool);         \
+    cudaError_t stencil_multi_tab_r##RR(const Job *, int, int, int, int, cudaStream_t, bool);   \
     int stencil_capacity_r##RR(int, bool);                                                      \
     cudaError_t stencil_prepare_r##RR();
 SSX_DECLARE_R(1)

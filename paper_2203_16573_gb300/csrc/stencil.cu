@@ -109,6 +109,11 @@ cudaError_t launch_multi(const JobSet &jobs, int total_tiles, int t, int R, int 
     SSX_BY_R(stencil_multi, jobs, total_tiles, t, cfg, s, pdl)
     return cudaErrorInvalidValue;
 }
+cudaError_t launch_multi_tab(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
+                             cudaStream_t s, bool pdl) {
+    SSX_BY_R(stencil_multi_tab, jobs, njobs, total_tiles, t, cfg, s, pdl)
+    return cudaErrorInvalidValue;
+}
 int persist_capacity(int R, int cfg, bool adj) {
     SSX_BY_R(stencil_capacity, cfg, adj)
     return 0;

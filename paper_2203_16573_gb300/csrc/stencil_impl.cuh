@@ -629,6 +629,49 @@ __global__ void __launch_bounds__(NT) k_multi(const JobSet P, int t) {
         fwd_tile<R, TX, TZ, NT>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>());
 }
 
+// The same for a phase whose sweeps live in a device table (batches of many
+// shots, each launch streams far more data than the look-up costs): binary
+// search of the CTA's sweep, its arguments copied to shared memory.
+template <int R, int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
+    griddep_launch();
+    __shared__ Job sj;
+    __shared__ int s_j;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {   // last sweep whose tile_base <= blockIdx.x
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&jobs[mid].tile_base) <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_j = lo;
+    }
+    __syncthreads();
+    {
+        const int *src = reinterpret_cast<const int *>(jobs + s_j);
+        int *dst = reinterpret_cast<int *>(&sj);
+        for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    const int st = t - sj.offset;
+    if (st < 0 || st >= sj.nt) return;
+    const int tl = blockIdx.x - sj.tile_base;
+    const int i0 = (tl % sj.tiles_x) * TX, k0 = (tl / sj.tiles_x) * TZ;
+    const bool odd = st & 1;
+    StepIO io;
+    io.p_in = odd ? sj.f[1][0] : sj.f[0][0];
+    io.vx_in = odd ? sj.f[1][1] : sj.f[0][1];
+    io.vz_in = odd ? sj.f[1][2] : sj.f[0][2];
+    io.p_out = odd ? sj.f[0][0] : sj.f[1][0];
+    io.vx_out = odd ? sj.f[0][1] : sj.f[1][1];
+    io.vz_out = odd ? sj.f[0][2] : sj.f[1][2];
+    io.n = sj.adj ? sj.nt - 1 - st : st;
+    griddep_wait();
+    if (sj.adj)
+        adj_tile<R, TX, TZ, NT>(sj.aa, io, i0, k0, tile_smem<R, TX, TZ>());
+    else
+        fwd_tile<R, TX, TZ, NT>(sj.fa, io, i0, k0, tile_smem<R, TX, TZ>());
+}
+
 // ----------------------------------------------------------- launchers --
 template <int R>
 struct Stencil {
@@ -676,6 +719,21 @@ struct Stencil {
         return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT>, jobs, t);
     }
     template <int TX, int TZ, int NT>
+    static cudaError_t multi_tab(const Job *jobs, int njobs, int total, int t, cudaStream_t s,
+                                 bool pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(total);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = smem<TX, TZ>();
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl ? at : nullptr;
+        cfg.numAttrs = pdl ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k_multi_tab<R, TX, TZ, NT>, jobs, njobs, t);
+    }
+    template <int TX, int TZ, int NT>
     static cudaError_t fwd_persist(const FwdArgs &a, const PersistArgs &pa, cudaStream_t s) {
         FwdArgs aa = a;
         PersistArgs pp = pa;
@@ -701,6 +759,7 @@ struct Stencil {
         if ((e = cudaFuncSetAttribute(k_adj<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_fwd_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi_tab<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_adj_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
     template <int TX, int TZ, int NT>
@@ -752,6 +811,13 @@ struct Stencil {
             default: return cudaErrorInvalidValue;                                                 \
         }                                                                                          \
     }                                                                                              \
+    cudaError_t stencil_multi_tab_r##RR(const Job *jobs, int njobs, int total, int t, int cfg,     \
+                                        cudaStream_t s, bool pdl) {                                \
+        switch (cfg) {                                                                             \
+            SSX_TILE_CONFIGS(SSX_CASE_MULTI_TAB)                                                   \
+            default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                          \
+    }                                                                                              \
     int stencil_capacity_r##RR(int cfg, bool adj) {                                                \
         switch (cfg) {                                                                             \
             SSX_TILE_CONFIGS(SSX_CASE_CAPACITY)                                                    \
@@ -769,6 +835,7 @@ struct Stencil {
 #define SSX_CASE_FWD_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_persist<TX, TZ, NT>(a, pa, s);
 #define SSX_CASE_ADJ_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_persist<TX, TZ, NT>(a, pa, s);
 #define SSX_CASE_MULTI(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi<TX, TZ, NT>(jobs, total, t, s, pdl);
+#define SSX_CASE_MULTI_TAB(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi_tab<TX, TZ, NT>(jobs, njobs, total, t, s, pdl);
 #define SSX_CASE_CAPACITY(id, TX, TZ, NT) case id: return Stencil<SSX_R>::capacity<TX, TZ, NT>(adj);
 #define SSX_CASE_PREPARE(id, TX, TZ, NT) if (e == cudaSuccess) e = Stencil<SSX_R>::prepare<TX, TZ, NT>();
 

@@ -28,7 +28,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
            "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode",
-           "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse"]
+           "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
+           "ssx_solve_batch"]
 
 
 class SSXError(RuntimeError):
@@ -96,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_set_tile_config": ([vp, i], i),
         "ssx_lambda_apply": ([vp, i, vp, vp], i),
         "ssx_time_reversal_inverse": ([vp, vp, vp], i),
+        "ssx_solve_batch": ([P(vp), i, P(vp), P(d), i, d, i, P(vp), P(d), P(i), P(i)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -258,6 +260,28 @@ class Context:
 
     def reset_stats(self):
         self._check(self._lib.ssx_reset_stats(self._c))
+
+
+def solve_batch(ctxs, ds, alphas, maxit, rtol, mode=MODE_PCG, outs=None):
+    """Solve one source subproblem per context in shared launches
+    (ssx_solve_batch). Returns (list of h, list of residual histories,
+    iterations, status names)."""
+    n = len(ctxs)
+    lib = load_library()
+    outs = [c._empty(c.n_line) for c in ctxs] if outs is None else outs
+    cptr = (ctypes.c_void_p * n)(*[c._c.value for c in ctxs])
+    dptr = (ctypes.c_void_p * n)(*[c._rec(d, "d").value for c, d in zip(ctxs, ds)])
+    hptr = (ctypes.c_void_p * n)(*[c._line(h, "h").value for c, h in zip(ctxs, outs)])
+    al = (ctypes.c_double * n)(*[float(a) for a in alphas])
+    hist = (ctypes.c_double * (n * (maxit + 1)))()
+    iters = (ctypes.c_int * n)()
+    status = (ctypes.c_int * n)()
+    rc = lib.ssx_solve_batch(cptr, n, dptr, al, int(maxit), float(rtol), int(mode), hptr, hist,
+                             iters, status)
+    if rc != SSX_OK:
+        raise SSXError(rc, lib.ssx_last_error(ctxs[0]._c).decode())
+    hs = [np.array(hist[i * (maxit + 1): i * (maxit + 1) + iters[i] + 1]) for i in range(n)]
+    return outs, hs, list(iters), [STATUS[st] for st in status]
 
 
 def version() -> str:

@@ -334,3 +334,55 @@ def test_time_reversal_inverse_parity(ssx, oracle):
     ctx, P = make(ssx, oracle, spec)
     d = P.point_source_data(W.ricker(spec), spec.x_d, spec.z_d)
     assert rel(ctx.time_reversal_inverse(dev(d)), P.time_reversal_inverse(d)) <= TOL
+
+
+# ------------------------------------------------------ batching (NEXT-1) --
+def _shot(base, k, **kw):
+    """shot k of a small survey: its own source position, line window, alpha"""
+    xs = base.h * (20 + 30 * k)
+    return dataclasses.replace(base, x_s=xs, x_d=xs, ix_line0=5 + 10 * k, n_line=90,
+                               alpha=(1e-3, 1e-2, 1e-1)[k % 3], **kw)
+
+
+@pytest.mark.parametrize("mode", ["pcg", "cg"])
+def test_batched_solves_equal_solo_solves(ssx, oracle, mode):
+    """Three shots in shared launches give bit-for-bit the solo results, and
+    one of them matches the oracle."""
+    base = W.small(order=8, nt=300)
+    specs = [_shot(base, k) for k in range(3)]
+    m = ssx.MODE_PCG if mode == "pcg" else ssx.MODE_CG
+    ctxs, ds, Ps = [], [], []
+    for sp in specs:
+        c, P = make(ssx, oracle, sp)
+        ctxs.append(c)
+        Ps.append(P)
+        ds.append(dev(P.point_source_data(W.ricker(sp), sp.x_d, sp.z_d)))
+    hb, hists, iters, status = ssx.solve_batch(ctxs, ds, [sp.alpha for sp in specs], 6, 0.0, m)
+    for c, d, sp, h, hh, it in zip(ctxs, ds, specs, hb, hists, iters):
+        h1, hh1, it1, st1 = c.solve(d, sp.alpha, 6, 0.0, m)
+        assert it == it1 == 6
+        assert torch.equal(h, h1)
+        np.testing.assert_array_equal(hh, hh1)
+    h_or, hist_or = oracle_pcg(Ps[1], ds[1].cpu().numpy(), specs[1].alpha, 6, 0.0, mode)
+    assert rel(hb[1], h_or) <= TOL
+    np.testing.assert_array_less(np.abs(hists[1] - hist_or) / hist_or, HIST_TOL)
+
+
+def test_batched_uneven_grids_and_stopping(ssx, oracle):
+    """Shots of different grid sizes, lengths and orders of stopping share the
+    launches; each keeps its solo result (one stops early on its rtol)."""
+    a = W.small(order=4, nt=260)
+    b = dataclasses.replace(W.small(order=4, nt=180), nx=97, nz=61, n_line=90, n_rec=97,
+                            z_s=0.45, x_s=0.5, x_d=0.5, ix_line0=2)
+    ctxs, ds = [], []
+    for sp in (a, b):
+        c, P = make(ssx, oracle, sp)
+        ctxs.append(c)
+        ds.append(dev(P.point_source_data(W.ricker(sp), sp.x_d, sp.z_d)))
+    rtol = 0.05
+    hb, hists, iters, status = ssx.solve_batch(ctxs, ds, [a.alpha, b.alpha], 10, rtol)
+    for c, d, sp, h, hh, it, stt in zip(ctxs, ds, (a, b), hb, hists, iters, status):
+        h1, hh1, it1, st1 = c.solve(d, sp.alpha, 10, rtol)
+        assert (it, stt) == (it1, st1)
+        assert torch.equal(h, h1)
+        np.testing.assert_array_equal(hh, hh1)
