@@ -336,6 +336,66 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The batched survey (64 shots on one 2001 x 801 lens model, 5000 steps):
+    one ssx_solve_batch call, all shots' sweeps of each PCG phase in shared
+    launches. Reports the stencil throughput and its HBM roofline fraction;
+    `--maxit` bounds the iterations timed (the set-up phases plus maxit
+    iterations)."""
+    import torch
+    from paper_2203_16573_gb300 import build, ssx, workloads as W
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = W.c3_shots(args.shots, args.nt)
+    vel = torch.as_tensor(W.velocity(specs[0]), dtype=torch.float32, device=dev)
+    ctxs, ds = [], []
+    for sp in specs:
+        c = ssx.Context.from_spec(sp)
+        c.set_velocity_model(vel, sp.rho)
+        c.set_geometry(sp.z_s, sp.ix_line0, sp.n_line, sp.z_r, sp.ix_rec0, sp.n_rec, sp.x_s,
+                       sp.dz_datum)
+        ds.append(c.point_source_data(sp.x_d, sp.z_d, torch.as_tensor(W.ricker(sp), device=dev)))
+        ctxs.append(c)
+    alphas = [sp.alpha for sp in specs]
+    outs = [c._empty(c.n_line) for c in ctxs]
+    lead = ctxs[0]
+    # warm-up: tunes and captures the batched phases
+    ssx.solve_batch(ctxs, ds, alphas, args.maxit, 0.0, ssx.MODE_PCG, outs)
+    torch.cuda.synchronize()
+    lead.reset_stats()
+    lead.set_timing(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    _, hist, iters, status = ssx.solve_batch(ctxs, ds, alphas, args.maxit, 0.0, ssx.MODE_PCG, outs)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    lead.set_timing(False)
+    st = lead.stats()
+    ms = ev0.elapsed_time(ev1)
+    hbm, peak_kind = peaks()
+    gpts = st["timed_point_updates"] / (st["sweep_ms"] / 1000.0) / 1e9
+    line = {"metric": "batched survey: stencil Gpt-updates/s & HBM % of peak", "value": gpts,
+            "unit": "Gpt-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 fields, f64 krylov", "data": "synthetic (seeded lens model, Ricker point sources)",
+            "config": {"workload": f"c3 survey: {args.shots} shots, 2001x801 lens model, h 5 m, "
+                                   f"order 8, nt {args.nt}, set-up + {args.maxit} PCG iterations",
+                       "l2": "inputs larger than L2 (per-step state of all shots ~4 GB)"},
+            "iterations": iters, "status": sorted(set(status)),
+            "point_updates": st["point_updates"],
+            "roofline": {"bound": "hbm", "achieved": gpts * BYTES_PER_POINT, "peak": hbm,
+                         "unit": "GB/s", "frac": gpts * BYTES_PER_POINT / hbm, "traffic": None,
+                         "peak_kind": peak_kind, "kernel": "k_multi_tab (all shots' sweeps per launch)",
+                         "avg_launch_us": 1000.0 * st["sweep_ms"] / max(st["timed_steps"], 1)},
+            "gpu_launches": st["kernel_launches"], "tile_cfg_lead": st["tile_cfg"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _stencil_hash():
     import hashlib
     with open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "stencil.cu"), "rb") as f:
@@ -350,9 +410,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the single-shot solve (default bench line); c3: the batched survey")
+    ap.add_argument("--shots", type=int, default=64)
+    ap.add_argument("--nt", type=int, default=5000)
+    ap.add_argument("--maxit", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -83,6 +83,29 @@ def c2() -> Spec:
                 alpha=1e-2, maxit=30, rtol=1e-3, model="gradient_lens")
 
 
+def c3_shots(n_shots: int = 64, nt: int = 5000) -> list[Spec]:
+    """Batched survey on one 2001 x 801 lens model (h = 5 m, 10 km x 4 km,
+    order 8, 40-point sponge, dt = 0.4 ms, 5000 steps): shot i is a 15 Hz
+    Ricker point source at x_i = (i + 1/2) 10 km / n at 50 m depth; its
+    extended source lives on the line z = 50 m within 1 km of x_i (clipped to
+    the model); every shot records on 2001 receivers on the line z = 3.5 km;
+    alpha cycles through 1e-3, 1e-2, 1e-1."""
+    out = []
+    for i in range(n_shots):
+        xs = (i + 0.5) * 10.0 / n_shots
+        ixs = int(round(xs / 0.005))
+        xs = ixs * 0.005
+        i0 = max(0, ixs - 200)
+        i1 = min(2000, ixs + 200)
+        out.append(Spec(name=f"c3_shot{i:02d}_2001x801_o8_nt{nt}", nx=2001, nz=801, h=0.005,
+                        dt=0.4e-3, nt=nt, order=8, n_sponge=40, rho=1.0, z_s=0.05,
+                        ix_line0=i0, n_line=i1 - i0 + 1, z_r=3.5, ix_rec0=0, n_rec=2001,
+                        x_s=xs, x_d=xs, z_d=0.05, f_peak=15.0,
+                        alpha=(1e-3, 1e-2, 1e-1)[i % 3], maxit=30, rtol=1e-3,
+                        model="gradient_lens"))
+    return out
+
+
 def small(order: int = 4, nt: int = 400, model: str = "gradient_lens",
           n_sponge: int = 12) -> Spec:
     """A reduced c2-like case (same structure, ~1/5 linear size) that the
