@@ -190,6 +190,31 @@ int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, con
                     int maxit, double rtol, int mode, double *const *h_out_dev, double *hist,
                     int *iters, int *status);
 
+/* A solve server with continuous batching. Requests (each a full source
+ * subproblem: grid, geometry, model, data, alpha, stopping rule, output
+ * buffer) queue in submission order and are admitted while their estimated
+ * device memory fits hbm_budget_bytes; admitted requests join the solves
+ * already running at the next round and share every kernel launch with them
+ * (ssx_solve_batch's engine); a finished request releases its memory for the
+ * queue. Each result equals the request's solo ssx_solve_source_subproblem.
+ * All requests use the server's space order. Caller-owned buffers (model,
+ * data, output) must stay valid until the request is done. Not thread-safe. */
+typedef struct ssx_server ssx_server;
+int ssx_server_create(ssx_server **out, int space_order, size_t hbm_budget_bytes, void *stream);
+/* Queue one request; *id_out identifies it. No device work until admission. */
+int ssx_server_submit(ssx_server *sv, const ssx_grid_desc *grid, const ssx_geom_desc *geom,
+                      const float *v_dev, double rho, const double *d_dev, double alpha, int maxit,
+                      double rtol, int mode, double *h_out_dev, int *id_out);
+/* Admit what fits, run one round (four phases) of every admitted solve,
+ * retire the finished ones. Synchronises. */
+int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued);
+/* done = 1 once the request's h is in its output buffer; status, iterations,
+ * submit-to-done latency and submit-to-admit wait in ms (host clock). */
+int ssx_server_poll(ssx_server *sv, int id, int *done, int *status, int *iters, double *latency_ms,
+                    double *queue_ms);
+int ssx_server_destroy(ssx_server *sv);
+const char *ssx_server_last_error(const ssx_server *sv);
+
 /* d = pressure gather on z_r of a point pressure source w(t) delta(x - x_d)
  * delta(z - z_d) (fixture of the section "Creating downgoing fields").
  * wavelet_dev: nt float64 samples (device), sample n integrated over the

@@ -25,6 +25,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <deque>
 #include <functional>
 #include <string>
 #include <unordered_map>
@@ -1009,14 +1011,18 @@ void reset_choices(ssx_ctx *c) {
 struct ShotRun {
     ssx_ctx *c = nullptr;
     double alpha = 0;
+    int maxit = 0;
+    double rtol = 0;
+    int mode = SSX_MODE_PCG;
     const double *d = nullptr;
     double *h_out = nullptr;
     double *hist = nullptr;   // host, maxit + 1 entries, may be null
     int iters = 0;
     int status = SSX_OK;
-    bool active = true;
+    enum { NEW, RHS, FIRST, ITER, DONE } state = NEW;
     double r0 = 0;
     std::string msg;
+    bool active() const { return state != DONE; }
 };
 
 enum PhaseKind { PK_R1, PK_R2, PK_RC, PK_M1, PK_M2, PK_N1, PK_N2, PK_NC1, PK_NC2 };
@@ -1055,175 +1061,258 @@ void add_sweeps(ssx_ctx *c, int kind, double alpha, std::vector<Sweep> &out) {
     }
 }
 
-int solve_batch(std::vector<ShotRun> &shots, int maxit, double rtol, int mode) {
-    ssx_ctx *L = shots[0].c;   // the lead context runs the launches on its stream
-    ssx_ctx *c = L;            // for CK/TRY error reporting
+// One round of the solve engine for a set of shots (each at its own stage of
+// Algorithm 1). A shot's stages: NEW (set-up of r_0 = S^* d: the two R
+// phases), FIRST (g_0 = M^{-1} r_0, p_0 = g_0, q_0 = N p_0) and ITER (one
+// update h += alpha p, r -= alpha q with its stopping test, then
+// g = M^{-1} r, p = g + beta p, q = N p). Every round runs the same four
+// phases; each shot contributes the sweeps of its stage (the R phases of new
+// shots share launches with the M phases of the others), so shots can join at
+// any round. The per-shot arithmetic is the same whatever else shares the
+// launches.
+int engine_round(ssx_ctx *L, std::vector<ShotRun *> &shots) {
+    ssx_ctx *c = L;   // for CK/TRY error reporting
     cudaStream_t s = L->s;
-    const bool pcg = mode == SSX_MODE_PCG;
     auto nl = [](ShotRun &sh) { return (size_t)sh.c->gd.nt * sh.c->geom.n_line; };
-    auto phase = [&](const char *name, int kind) -> int {
-        std::vector<Sweep> sw;
-        for (auto &sh : shots)
-            if (sh.active) add_sweeps(sh.c, kind, sh.alpha, sw);
-        return sw.empty() ? SSX_OK : run_phase(L, name, sw);
-    };
-    auto each = [&](const std::function<int(ShotRun &)> &f) -> int {
-        for (auto &sh : shots)
-            if (sh.active) TRY(f(sh));
-        return SSX_OK;
-    };
-    auto read_scalars = [&]() -> int {
-        TRY(each([&](ShotRun &sh) -> int {
-            CK(cudaMemcpyAsync(sh.c->sc_host, sh.c->sc, SC_COUNT * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
-            return SSX_OK;
-        }));
-        CK(cudaStreamSynchronize(s));
-        return SSX_OK;
-    };
-    // M^{-1}: g = D W~_m^{-1} D r (identity for plain CG)
-    auto precond = [&]() -> int {
-        if (!pcg)
-            return each([&](ShotRun &sh) -> int {
-                CK(cudaMemcpyAsync(sh.c->g, sh.c->r, nl(sh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                return SSX_OK;
-            });
-        TRY(each([&](ShotRun &sh) -> int {
-            CK(launch_colscale(sh.c->tl1, sh.c->r, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
-            L->st.kernel_launches += 1;
-            return SSX_OK;
-        }));
-        TRY(phase("bM1", PK_M1));
-        TRY(phase("bM2", PK_M2));
-        return each([&](ShotRun &sh) -> int {
-            CK(launch_colscale(sh.c->g, sh.c->tl2, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
-            L->st.kernel_launches += 1;
-            return SSX_OK;
-        });
-    };
-    // q = N p
-    auto normal = [&]() -> int {
-        if (pcg)
-            TRY(each([&](ShotRun &sh) -> int {
-                if (sh.alpha != 0.0) {
-                    CK(launch_colscale(sh.c->tl1, sh.c->p, sh.c->dist, sh.c->gd.nt, sh.c->geom.n_line, s));
-                    L->st.kernel_launches += 1;
-                }
-                return SSX_OK;
-            }));
-        TRY(phase(pcg ? "bN1" : "bNc1", pcg ? PK_N1 : PK_NC1));
-        TRY(phase(pcg ? "bN2" : "bNc2", pcg ? PK_N2 : PK_NC2));
-        return each([&](ShotRun &sh) -> int {
-            if (sh.alpha != 0.0) {
-                if (pcg)
-                    CK(launch_colscale_add(sh.c->q, sh.c->tl2, sh.c->dist, sh.alpha, sh.c->gd.nt,
-                                           sh.c->geom.n_line, s));
-                else
-                    CK(launch_colscale_add(sh.c->q, sh.c->p, sh.c->dist2, sh.alpha, sh.c->gd.nt,
-                                           sh.c->geom.n_line, s));
-                L->st.kernel_launches += 1;
-            }
-            return SSX_OK;
-        });
-    };
     auto stop = [&](ShotRun &sh, int status, const std::string &msg) {
         sh.status = status;
         sh.msg = msg;
-        sh.active = false;
+        sh.state = ShotRun::DONE;
     };
-
-    // set-up: h_0 = 0, r_0 = S^* d, g_0 = p_0 = M^{-1} r_0, q_0 = N p_0
-    for (auto &sh : shots)
-        if (pcg) TRY(set_D(sh.c, sh.alpha));
-    TRY(each([&](ShotRun &sh) -> int {
-        CK(cudaMemcpyAsync(sh.c->tr1, sh.d, rec_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(sh.c->h, 0, line_bytes(sh.c), s));
-        return SSX_OK;
-    }));
-    if (pcg) {
-        TRY(phase("bR1", PK_R1));
-        TRY(phase("bR2", PK_R2));
-    } else {
-        TRY(phase("bRc", PK_RC));
-    }
-    TRY(each([&](ShotRun &sh) -> int {   // r_0 = 0: done before any direction is formed
-        CK(launch_dot(sh.c->r, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_RR, s));
-        L->st.kernel_launches += 2;
-        return SSX_OK;
-    }));
-    TRY(read_scalars());
-    for (auto &sh : shots) {
-        sh.r0 = std::sqrt(sh.c->sc_host[SC_RR]);
-        if (sh.hist) sh.hist[0] = sh.r0;
-        if (!std::isfinite(sh.r0)) stop(sh, SSX_ERR_NONFINITE, "non-finite initial residual");
-        else if (sh.r0 == 0.0) stop(sh, SSX_OK, "");
-        else if (maxit == 0) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
-    }
-    TRY(precond());
-    TRY(each([&](ShotRun &sh) -> int {
-        CK(cudaMemcpyAsync(sh.c->p, sh.c->g, line_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
-        return SSX_OK;
-    }));
-    TRY(normal());
-    TRY(each([&](ShotRun &sh) -> int {
-        CK(launch_dot(sh.c->g, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_GR, s));
-        L->st.kernel_launches += 2;
-        return SSX_OK;
-    }));
-    for (int k = 0; k < maxit; k++) {
-        // alpha_k = <g,r>/<p,q>; h += alpha p; r -= alpha q; ||r||^2
-        TRY(each([&](ShotRun &sh) -> int {
+    // --- update step of iterating shots and the residual norms -------------
+    bool any_read = false;
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        if (sh.state == ShotRun::ITER) {
             double *sc = sh.c->sc;
             CK(launch_dot(sh.c->p, sh.c->q, nl(sh), sh.c->partials, sc + SC_PQ, s));
             CK(launch_pcg_alpha(sc, s));
             CK(launch_pcg_update(sh.c->h, sh.c->r, sh.c->p, sh.c->q, nl(sh), sc, sh.c->partials, s));
             L->st.kernel_launches += 5;
-            return SSX_OK;
-        }));
-        TRY(read_scalars());
-        bool any = false;
-        for (auto &sh : shots) {
-            if (!sh.active) continue;
-            const double *sh_sc = sh.c->sc_host;
-            if (sh_sc[SC_FLAG] != 0.0) {
-                if (!std::isfinite(sh_sc[SC_PQ]) || !std::isfinite(sh_sc[SC_GR])) {
+        }
+        if (sh.state == ShotRun::ITER || sh.state == ShotRun::RHS) {
+            CK(cudaMemcpyAsync(sh.c->sc_host, sh.c->sc, SC_COUNT * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+            any_read = true;
+        }
+    }
+    if (any_read) CK(cudaStreamSynchronize(s));
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        const double *h = sh.c->sc_host;
+        if (sh.state == ShotRun::RHS) {   // r_0 known
+            sh.r0 = std::sqrt(h[SC_RR]);
+            if (sh.hist) sh.hist[0] = sh.r0;
+            if (!std::isfinite(sh.r0)) stop(sh, SSX_ERR_NONFINITE, "non-finite initial residual");
+            else if (sh.r0 == 0.0) stop(sh, SSX_OK, "");
+            else if (sh.maxit == 0) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
+            else sh.state = ShotRun::FIRST;
+        } else if (sh.state == ShotRun::ITER) {
+            const int k = sh.iters;
+            if (h[SC_FLAG] != 0.0) {
+                if (!std::isfinite(h[SC_PQ]) || !std::isfinite(h[SC_GR])) {
                     stop(sh, SSX_ERR_NONFINITE, "non-finite Krylov scalar");
                 } else {
                     char b[160];
                     snprintf(b, sizeof b, "PCG breakdown at k=%d: <p,q>=%.6e <g,r>=%.6e", k,
-                             sh_sc[SC_PQ], sh_sc[SC_GR]);
+                             h[SC_PQ], h[SC_GR]);
                     stop(sh, SSX_ERR_BREAKDOWN, b);
                 }
                 continue;
             }
-            const double rn = std::sqrt(sh_sc[SC_RR]);
+            const double rn = std::sqrt(h[SC_RR]);
             sh.iters = k + 1;
             if (sh.hist) sh.hist[k + 1] = rn;
             if (!std::isfinite(rn)) stop(sh, SSX_ERR_NONFINITE, "non-finite residual");
-            else if (rn <= rtol * sh.r0) stop(sh, SSX_OK, "");
-            else if (k == maxit - 1) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
-            any = any || sh.active;
+            else if (rn <= sh.rtol * sh.r0) stop(sh, SSX_OK, "");
+            else if (k == sh.maxit - 1) stop(sh, SSX_ERR_NOT_CONVERGED, "maxit reached above rtol");
         }
-        if (!any) break;
-        // g = M^{-1} r; beta = <g,r>_new/<g,r>; p = g + beta p; q = N p
-        TRY(precond());
-        TRY(each([&](ShotRun &sh) -> int {
+    }
+    // --- the four phases ----------------------------------------------------
+    auto want_M = [](const ShotRun &sh) {
+        return sh.state == ShotRun::FIRST || sh.state == ShotRun::ITER;
+    };
+    auto phase = [&](const char *name, const std::function<void(ShotRun &, std::vector<Sweep> &)> &f) -> int {
+        std::vector<Sweep> sw;
+        for (ShotRun *p : shots) f(*p, sw);
+        return sw.empty() ? SSX_OK : run_phase(L, name, sw);
+    };
+    // new shots: d -> tr1, h = 0
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        if (sh.state != ShotRun::NEW) continue;
+        if (sh.mode == SSX_MODE_PCG) TRY(set_D(sh.c, sh.alpha));
+        CK(cudaMemcpyAsync(sh.c->tr1, sh.d, rec_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(sh.c->h, 0, line_bytes(sh.c), s));
+    }
+    // M^{-1} input D r (PCG)
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        if (want_M(sh) && sh.mode == SSX_MODE_PCG) {
+            CK(launch_colscale(sh.c->tl1, sh.c->r, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+        }
+    }
+    TRY(phase("e1", [&](ShotRun &sh, std::vector<Sweep> &sw) {
+        if (sh.state == ShotRun::NEW) add_sweeps(sh.c, sh.mode == SSX_MODE_PCG ? PK_R1 : PK_RC, sh.alpha, sw);
+        else if (want_M(sh) && sh.mode == SSX_MODE_PCG) add_sweeps(sh.c, PK_M1, sh.alpha, sw);
+    }));
+    TRY(phase("e2", [&](ShotRun &sh, std::vector<Sweep> &sw) {
+        if (sh.state == ShotRun::NEW && sh.mode == SSX_MODE_PCG) add_sweeps(sh.c, PK_R2, sh.alpha, sw);
+        else if (want_M(sh) && sh.mode == SSX_MODE_PCG) add_sweeps(sh.c, PK_M2, sh.alpha, sw);
+    }));
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        if (sh.state == ShotRun::NEW) {   // ||r_0||^2, read next round
+            CK(launch_dot(sh.c->r, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_RR, s));
+            L->st.kernel_launches += 2;
+            continue;
+        }
+        if (!want_M(sh)) continue;
+        if (sh.mode == SSX_MODE_PCG) {
+            CK(launch_colscale(sh.c->g, sh.c->tl2, sh.c->D, sh.c->gd.nt, sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+        } else {
+            CK(cudaMemcpyAsync(sh.c->g, sh.c->r, nl(sh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        if (sh.state == ShotRun::FIRST) {   // p_0 = g_0, <g_0, r_0>
+            CK(cudaMemcpyAsync(sh.c->p, sh.c->g, line_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
+            CK(launch_dot(sh.c->g, sh.c->r, nl(sh), sh.c->partials, sh.c->sc + SC_GR, s));
+            L->st.kernel_launches += 2;
+        } else {                            // beta, p = g + beta p
             double *sc = sh.c->sc;
             CK(launch_dot(sh.c->g, sh.c->r, nl(sh), sh.c->partials, sc + SC_GRNEW, s));
             CK(launch_pcg_beta(sc, s));
             CK(launch_xpby(sh.c->p, sh.c->g, nl(sh), sc, s));
             L->st.kernel_launches += 4;
-            return SSX_OK;
-        }));
-        TRY(normal());
+        }
+        if (sh.mode == SSX_MODE_PCG && sh.alpha != 0.0) {   // A p for W~_m
+            CK(launch_colscale(sh.c->tl1, sh.c->p, sh.c->dist, sh.c->gd.nt, sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+        }
     }
-    for (auto &sh : shots) {
-        if (sh.h_out)
-            CK(cudaMemcpyAsync(sh.h_out, sh.c->h, line_bytes(sh.c), cudaMemcpyDeviceToDevice, s));
-        if (sh.status != SSX_OK) sh.c->err = sh.msg;
+    TRY(phase("e3", [&](ShotRun &sh, std::vector<Sweep> &sw) {
+        if (want_M(sh)) add_sweeps(sh.c, sh.mode == SSX_MODE_PCG ? PK_N1 : PK_NC1, sh.alpha, sw);
+    }));
+    TRY(phase("e4", [&](ShotRun &sh, std::vector<Sweep> &sw) {
+        if (want_M(sh)) add_sweeps(sh.c, sh.mode == SSX_MODE_PCG ? PK_N2 : PK_NC2, sh.alpha, sw);
+    }));
+    for (ShotRun *p : shots) {
+        ShotRun &sh = *p;
+        if (want_M(sh) && sh.alpha != 0.0) {
+            if (sh.mode == SSX_MODE_PCG)
+                CK(launch_colscale_add(sh.c->q, sh.c->tl2, sh.c->dist, sh.alpha, sh.c->gd.nt,
+                                       sh.c->geom.n_line, s));
+            else
+                CK(launch_colscale_add(sh.c->q, sh.c->p, sh.c->dist2, sh.alpha, sh.c->gd.nt,
+                                       sh.c->geom.n_line, s));
+            L->st.kernel_launches += 1;
+        }
+        if (sh.state == ShotRun::NEW) sh.state = ShotRun::RHS;
+        else if (sh.state == ShotRun::FIRST) sh.state = ShotRun::ITER;
     }
     return SSX_OK;
 }
+
+// finished shots: the last iterate to the caller's buffer
+int engine_retire(ssx_ctx *L, ShotRun &sh) {
+    ssx_ctx *c = L;
+    if (sh.h_out)
+        CK(cudaMemcpyAsync(sh.h_out, sh.c->h, line_bytes(sh.c), cudaMemcpyDeviceToDevice, L->s));
+    if (sh.status != SSX_OK) sh.c->err = sh.msg;
+    return SSX_OK;
+}
+
+int solve_batch(std::vector<ShotRun> &shots) {
+    ssx_ctx *L = shots[0].c;
+    std::vector<ShotRun *> act;
+    for (auto &sh : shots) act.push_back(&sh);
+    while (true) {
+        bool any = false;
+        for (auto &sh : shots) any = any || sh.active();
+        if (!any) break;
+        TRY(engine_round(L, act));
+    }
+    for (auto &sh : shots) TRY(engine_retire(L, sh));
+    return SSX_OK;
+}
+
+// ---------------------------------------------------------------- server --
+// Continuous batching of source-subproblem solves: requests queue up, are
+// admitted while their estimated device memory fits the budget, join the
+// engine at the next round (sharing every launch with the solves already
+// running), and leave when they stop, freeing their memory for the queue.
+static size_t estimate_bytes(const ssx_grid_desc &g, const ssx_geom_desc &m) {
+    const int nsp = g.n_sponge;
+    auto grid_bytes = [&](int nx, int nz) {
+        const int NX = nx + 2 * nsp, NZ = nz + 2 * nsp;
+        const size_t pitch = ((((NX + TILE_X_MAX - 1) / TILE_X_MAX) * TILE_X_MAX + 2 * GX + 31) / 32) * 32;
+        const size_t rows = ((NZ + TILE_Z_MAX - 1) / TILE_Z_MAX) * TILE_Z_MAX + 2 * GZ;
+        return 7 * pitch * rows * 4 + (size_t)4096 * 4;
+    };
+    const int slab_rows = (int)std::ceil(m.dz_datum / g.h) + 3 + g.space_order;
+    const size_t nl = (size_t)g.nt * m.n_line, nr = (size_t)g.nt * m.n_rec;
+    return grid_bytes(g.nx, g.nz) + 3 * grid_bytes(g.nx, slab_rows) +
+           (7 * nl + 2 * nr + 4 * nl + 2 * nr) * 8 + (size_t)g.nx * g.nz * 4 + ((size_t)1 << 20);
+}
+
+struct ssx_server {
+    struct Req {
+        int id = 0;
+        ssx_grid_desc g{};
+        ssx_geom_desc m{};
+        const float *v = nullptr;
+        double rho = 1.0;
+        ShotRun run;
+        ssx_ctx *c = nullptr;
+        size_t bytes = 0;
+        double t_submit = 0, t_admit = 0, t_done = 0;
+        bool done = false;
+    };
+    ssx_ctx *lead = nullptr;       // owns the stream, the phase launches and their statistics
+    size_t budget = 0, used = 0;
+    int order = 8;
+    int next_id = 1;
+    std::deque<Req *> queue;
+    std::vector<Req *> active;
+    std::unordered_map<int, Req *> all;
+    std::string err;
+};
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int server_admit(ssx_server *sv) {
+    while (!sv->queue.empty()) {
+        ssx_server::Req *q = sv->queue.front();
+        if (sv->used + q->bytes > sv->budget && !sv->active.empty()) break;   // wait for memory
+        sv->queue.pop_front();
+        ssx_ctx *c = nullptr;
+        int rc = ssx_create(&c, &q->g, sv->lead->user);
+        if (rc == SSX_OK) rc = ssx_set_velocity_model(c, q->v, q->rho);
+        if (rc == SSX_OK) rc = ssx_set_geometry(c, &q->m);
+        if (rc != SSX_OK) {
+            q->run.status = rc;
+            q->run.msg = c ? c->err : "context creation failed";
+            q->done = true;
+            q->t_done = now_ms();
+            if (c) ssx_destroy(c);
+            continue;
+        }
+        q->c = c;
+        q->run.c = c;
+        q->t_admit = now_ms();
+        sv->used += q->bytes;
+        sv->active.push_back(q);
+    }
+    return SSX_OK;
+}
+
+}  // namespace
 
 // ================================================================ C ABI ==
 extern "C" {
@@ -1498,10 +1587,13 @@ int ssx_solve_source_subproblem(ssx_ctx *c, const double *d_dev, double alpha, i
     std::vector<ShotRun> shots(1);
     shots[0].c = c;
     shots[0].alpha = alpha;
+    shots[0].maxit = maxit;
+    shots[0].rtol = rtol;
+    shots[0].mode = mode;
     shots[0].d = d_dev;
     shots[0].h_out = h_out;
     shots[0].hist = hist;
-    int rc = solve_batch(shots, maxit, rtol, mode);
+    int rc = solve_batch(shots);
     if (iters) *iters = shots[0].iters;
     if (rc == SSX_OK) rc = shots[0].status;
     return leave(c, rc);
@@ -1534,11 +1626,14 @@ int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, con
     for (int i = 0; i < n; i++) {
         shots[i].c = ctxs[i];
         shots[i].alpha = alphas[i];
+        shots[i].maxit = maxit;
+        shots[i].rtol = rtol;
+        shots[i].mode = mode;
         shots[i].d = d_dev[i];
         shots[i].h_out = h_out_dev[i];
         shots[i].hist = hist ? hist + (size_t)i * (maxit + 1) : nullptr;
     }
-    int rc = solve_batch(shots, maxit, rtol, mode);
+    int rc = solve_batch(shots);
     for (int i = 0; i < n; i++) {
         if (iters) iters[i] = shots[i].iters;
         if (status) status[i] = rc == SSX_OK ? shots[i].status : rc;
@@ -1622,5 +1717,130 @@ int ssx_reset_stats(ssx_ctx *c) {
     c->st = ssx_stats{};
     return SSX_OK;
 }
+
+int ssx_server_create(ssx_server **out, int space_order, size_t hbm_budget_bytes, void *stream) {
+    if (!out || space_order < 2 || space_order > 8 || space_order % 2 || hbm_budget_bytes == 0)
+        return SSX_ERR_ARG;
+    *out = nullptr;
+    ssx_server *sv = new ssx_server();
+    sv->budget = hbm_budget_bytes;
+    sv->order = space_order;
+    ssx_grid_desc g{8, 8, 0.01, 1e-3, 1, space_order, 0};
+    int rc = ssx_create(&sv->lead, &g, stream);
+    if (rc != SSX_OK) {
+        delete sv;
+        return rc;
+    }
+    // requests come and go every round: launch phases directly (no graph
+    // capture per membership) with one fixed tile configuration
+    sv->lead->use_graphs = false;
+    sv->lead->forced_cfg = 1;
+    *out = sv;
+    return SSX_OK;
+}
+
+int ssx_server_submit(ssx_server *sv, const ssx_grid_desc *grid, const ssx_geom_desc *geom,
+                      const float *v_dev, double rho, const double *d_dev, double alpha, int maxit,
+                      double rtol, int mode, double *h_out_dev, int *id_out) {
+    if (!sv || !grid || !geom || !v_dev || !d_dev || !h_out_dev || !id_out || !(alpha >= 0) ||
+        maxit < 0 || !(rtol >= 0) || (mode != SSX_MODE_PCG && mode != SSX_MODE_CG) || !(rho > 0))
+        return SSX_ERR_ARG;
+    if (grid->space_order != sv->order) {
+        sv->err = "request space order differs from the server's";
+        return SSX_ERR_ARG;
+    }
+    auto *q = new ssx_server::Req();
+    q->id = sv->next_id++;
+    q->g = *grid;
+    q->m = *geom;
+    q->v = v_dev;
+    q->rho = rho;
+    q->run.alpha = alpha;
+    q->run.maxit = maxit;
+    q->run.rtol = rtol;
+    q->run.mode = mode;
+    q->run.d = d_dev;
+    q->run.h_out = h_out_dev;
+    q->bytes = estimate_bytes(*grid, *geom);
+    q->t_submit = now_ms();
+    sv->queue.push_back(q);
+    sv->all[q->id] = q;
+    *id_out = q->id;
+    return SSX_OK;
+}
+
+int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued) {
+    if (!sv) return SSX_ERR_ARG;
+    TRY(server_admit(sv));
+    if (!sv->active.empty()) {
+        ssx_ctx *L = sv->lead;
+        ssx_ctx *c = L;
+        CK(cudaEventRecord(L->ev_in, L->user));
+        CK(cudaStreamWaitEvent(L->s, L->ev_in, 0));
+        for (auto *q : sv->active) {   // after each request's own set-up work
+            CK(cudaEventRecord(q->c->ev_in, q->c->s));
+            CK(cudaStreamWaitEvent(L->s, q->c->ev_in, 0));
+        }
+        std::vector<ShotRun *> runs;
+        for (auto *q : sv->active) runs.push_back(&q->run);
+        int rc = engine_round(L, runs);
+        if (rc != SSX_OK) {
+            sv->err = L->err;
+            return rc;
+        }
+        std::vector<ssx_server::Req *> keep;
+        bool changed = false;
+        for (auto *q : sv->active) {
+            if (q->run.active()) {
+                keep.push_back(q);
+                continue;
+            }
+            TRY(engine_retire(L, q->run));
+            CK(cudaStreamSynchronize(L->s));
+            q->done = true;
+            q->t_done = now_ms();
+            ssx_destroy(q->c);
+            q->c = nullptr;
+            q->run.c = nullptr;
+            sv->used -= q->bytes;
+            changed = true;
+        }
+        sv->active.swap(keep);
+        if (changed) drop_phases(L);   // phase tables of departed requests
+        CK(cudaEventRecord(L->ev_out, L->s));
+        CK(cudaStreamWaitEvent(L->user, L->ev_out, 0));
+    }
+    if (n_active) *n_active = (int)sv->active.size();
+    if (n_queued) *n_queued = (int)sv->queue.size();
+    return SSX_OK;
+}
+
+int ssx_server_poll(ssx_server *sv, int id, int *done, int *status, int *iters, double *latency_ms,
+                    double *queue_ms) {
+    if (!sv) return SSX_ERR_ARG;
+    auto it = sv->all.find(id);
+    if (it == sv->all.end()) return SSX_ERR_ARG;
+    ssx_server::Req *q = it->second;
+    if (done) *done = q->done ? 1 : 0;
+    if (status) *status = q->done ? q->run.status : SSX_OK;
+    if (iters) *iters = q->run.iters;
+    if (latency_ms) *latency_ms = q->done ? q->t_done - q->t_submit : 0.0;
+    if (queue_ms) *queue_ms = q->t_admit > 0 ? q->t_admit - q->t_submit : 0.0;
+    return SSX_OK;
+}
+
+int ssx_server_destroy(ssx_server *sv) {
+    if (!sv) return SSX_ERR_ARG;
+    if (sv->lead && sv->lead->s) cudaStreamSynchronize(sv->lead->s);
+    for (auto &kv : sv->all) {
+        if (kv.second->c) ssx_destroy(kv.second->c);
+        delete kv.second;
+    }
+    if (sv->lead) ssx_destroy(sv->lead);
+    delete sv;
+    return SSX_OK;
+}
+
+const char *ssx_server_last_error(const ssx_server *sv) { return sv ? sv->err.c_str() : "null server"; }
 
 }  // extern "C"

@@ -29,7 +29,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_solve_source_subproblem", "ssx_point_source_data", "ssx_set_timing",
            "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode",
            "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
-           "ssx_solve_batch"]
+           "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
+           "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error"]
 
 
 class SSXError(RuntimeError):
@@ -98,6 +99,12 @@ def load_library(path: str = LIB_PATH):
         "ssx_lambda_apply": ([vp, i, vp, vp], i),
         "ssx_time_reversal_inverse": ([vp, vp, vp], i),
         "ssx_solve_batch": ([P(vp), i, P(vp), P(d), i, d, i, P(vp), P(d), P(i), P(i)], i),
+        "ssx_server_create": ([P(vp), i, ctypes.c_size_t, vp], i),
+        "ssx_server_submit": ([vp, P(GridDesc), P(GeomDesc), vp, d, vp, d, i, d, i, vp, P(i)], i),
+        "ssx_server_step": ([vp, P(i), P(i)], i),
+        "ssx_server_poll": ([vp, i, P(i), P(i), P(i), P(d), P(d)], i),
+        "ssx_server_destroy": ([vp], i),
+        "ssx_server_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -282,6 +289,70 @@ def solve_batch(ctxs, ds, alphas, maxit, rtol, mode=MODE_PCG, outs=None):
         raise SSXError(rc, lib.ssx_last_error(ctxs[0]._c).decode())
     hs = [np.array(hist[i * (maxit + 1): i * (maxit + 1) + iters[i] + 1]) for i in range(n)]
     return outs, hs, list(iters), [STATUS[st] for st in status]
+
+
+class Server:
+    """Continuous-batching solve server (ssx_server_*): submit requests, call
+    step() repeatedly, poll results. Tensors given to submit() are kept alive
+    until the request is done."""
+
+    def __init__(self, space_order=8, hbm_budget_bytes=80 * 10 ** 9, stream=None):
+        self._lib = load_library()
+        s = torch.cuda.current_stream() if stream is None else stream
+        self._s = ctypes.c_void_p()
+        rc = self._lib.ssx_server_create(ctypes.byref(self._s), int(space_order),
+                                         int(hbm_budget_bytes), ctypes.c_void_p(s.cuda_stream))
+        if rc != SSX_OK:
+            raise SSXError(rc, "ssx_server_create failed")
+        self._keep = {}
+
+    def submit(self, spec, vel, d, out, alpha=None, maxit=None, rtol=None, mode=MODE_PCG):
+        gd = GridDesc(spec.nx, spec.nz, spec.h, spec.dt, spec.nt, spec.order, spec.n_sponge)
+        gm = GeomDesc(spec.z_s, spec.ix_line0, spec.n_line, spec.z_r, spec.ix_rec0, spec.n_rec,
+                      spec.x_s, spec.dz_datum)
+        v = _dev_ptr(vel, (spec.nz, spec.nx), torch.float32, "vel")
+        dp = _dev_ptr(d, (spec.nt, spec.n_rec), name="d")
+        hp = _dev_ptr(out, (spec.nt, spec.n_line), name="out")
+        rid = ctypes.c_int(0)
+        rc = self._lib.ssx_server_submit(self._s, ctypes.byref(gd), ctypes.byref(gm), v, spec.rho, dp,
+                                         float(spec.alpha if alpha is None else alpha),
+                                         int(spec.maxit if maxit is None else maxit),
+                                         float(spec.rtol if rtol is None else rtol), int(mode), hp,
+                                         ctypes.byref(rid))
+        if rc != SSX_OK:
+            raise SSXError(rc, self._lib.ssx_server_last_error(self._s).decode())
+        self._keep[rid.value] = (vel, d, out)
+        return rid.value
+
+    def step(self):
+        a, q = ctypes.c_int(0), ctypes.c_int(0)
+        rc = self._lib.ssx_server_step(self._s, ctypes.byref(a), ctypes.byref(q))
+        if rc != SSX_OK:
+            raise SSXError(rc, self._lib.ssx_server_last_error(self._s).decode())
+        return a.value, q.value
+
+    def poll(self, rid):
+        done, st, it = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        lat, wait = ctypes.c_double(0), ctypes.c_double(0)
+        rc = self._lib.ssx_server_poll(self._s, int(rid), ctypes.byref(done), ctypes.byref(st),
+                                       ctypes.byref(it), ctypes.byref(lat), ctypes.byref(wait))
+        if rc != SSX_OK:
+            raise SSXError(rc, "unknown request")
+        if done.value:
+            self._keep.pop(rid, None)
+        return {"done": bool(done.value), "status": STATUS[st.value], "iters": it.value,
+                "latency_ms": lat.value, "queue_ms": wait.value}
+
+    def close(self):
+        if self._s:
+            self._lib.ssx_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

@@ -133,6 +133,10 @@ def velocity(spec: Spec) -> np.ndarray:
     x = np.arange(spec.nx) * spec.h
     if spec.model == "homogeneous":
         return np.full((spec.nz, spec.nx), spec.v0, dtype=np.float64)
+    if spec.model == "gradient":
+        zmax = (spec.nz - 1) * spec.h
+        zz = np.repeat(z[:, None], spec.nx, axis=1)
+        return spec.v0 * (1.0 + zz / zmax)
     if spec.model == "gradient_lens":
         # linear gradient v0 -> 2 v0 from top to bottom, times a -20 %
         # Gaussian lens at the centre with sigma = depth / 10 (300 m for 3 km)
