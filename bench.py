@@ -396,6 +396,40 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a seeded Poisson stream of source-subproblem requests of mixed
+    grid sizes through the continuous-batching server, against the plain
+    one-at-a-time GPU solve of the same stream. Reports solves/s and p50/p99
+    latency of both."""
+    import torch
+    from paper_2203_16573_gb300 import build, serve
+    build.build()
+    torch.cuda.set_device(0)
+    specs = serve.request_specs(args.requests, args.rate, seed=1, scale=args.scale,
+                                maxit=args.maxit, rtol=1e-3)
+    inputs = serve.make_inputs(specs)
+    serve.serve(specs[:2], inputs[:2], realtime=False)          # warm-up (kernels, allocator)
+    outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9)
+    outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs)
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
+    pb, ps = serve.percentiles(rec_b), serve.percentiles(rec_s)
+    line = {"metric": "served PCG solves/s (continuous batching) with p50/p99 latency",
+            "value": len(specs) / wall_b, "unit": "solves/s", "n_gpus": 1, "steps": len(specs),
+            "warmup": 1, "ms_per_step": 1000.0 * wall_b / len(specs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, f64 krylov",
+            "data": "synthetic (seeded Poisson request stream)",
+            "config": {"workload": f"{len(specs)} requests, Poisson rate {args.rate}/s, grids "
+                                   f"{{401x201,1001x401,2001x801}} x {args.scale}, nt 1000-5000 x "
+                                   f"{args.scale}, order 8, maxit {args.maxit}, rtol 1e-3, "
+                                   f"HBM budget {args.budget_gb} GB"},
+            "latency_ms": pb, "one_at_a_time": {"value": len(specs) / wall_s, "unit": "solves/s",
+                                                "latency_ms": ps},
+            "results_identical_to_solo": same,
+            "iterations": [r["iters"] for r in rec_b]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _stencil_hash():
     import hashlib
     with open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "stencil.cu"), "rb") as f:
@@ -410,8 +444,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: the single-shot solve (default bench line); c3: the batched survey")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "serve"],
+                    help="c2: the single-shot solve (default bench line); c3: the batched survey; "
+                         "serve: continuous batching of a request stream")
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--scale", type=float, default=0.25)
+    ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--nt", type=int, default=5000)
     ap.add_argument("--maxit", type=int, default=2)
@@ -420,6 +459,10 @@ def main():
         return run_reference(args)
     if args.workload == "c3":
         return run_batch(args)
+    if args.workload == "serve":
+        if args.maxit == 2:
+            args.maxit = 10
+        return run_serve(args)
     return run_ours(args)
 
 
