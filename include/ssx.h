@@ -24,6 +24,9 @@
  * that return host results (ssx_solve_source_subproblem) synchronise.
  * No call throws; each returns an ssx_status. The message of the last failure
  * is available from ssx_last_error. A context is not thread-safe.
+ * Environment: SSX_GRAPHS=0 makes contexts created afterwards launch every
+ * time step directly instead of replaying captured CUDA graphs (same kernels
+ * and results; for profilers, which rebuild a graph on every replay).
  *
  * Discretisation (section "Synthetic models and simulation"): staggered grid,
  * order 2 in time and 2k in space, fields FP32 on the device; sampling by

@@ -24,6 +24,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <chrono>
 #include <deque>
@@ -1336,6 +1337,9 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
     int rc = SSX_OK;
     auto init = [&]() -> int {
         for (auto &row : c->cap) row[0] = row[1] = -1;
+        // SSX_GRAPHS=0: launch every step directly instead of replaying CUDA
+        // graphs (profilers treat each graph replay as a rebuild)
+        if (const char *e = std::getenv("SSX_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
         CK(prepare_kernels());
         CK(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
