@@ -311,6 +311,7 @@ def run_ours(args):
             "iterations": iters_list, "final_rel_residual": res_list,
             "converged": all(r <= spec.rtol for r in res_list),
             "stencil_gpt_updates_per_s": gpts,
+            "stencil_share_of_timed_region": st["sweep_ms"] / t_dev if t_dev else None,
             "point_updates_per_solve": st["point_updates"] / args.steps,
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "solves/s",
