@@ -921,20 +921,6 @@ int op_N(ssx_ctx *c, int mode, double alpha, const double *p, double *q) {
     return SSX_OK;
 }
 
-// r = S^* d: S^T W~_d d (the slab's transposed sweep and S^T in one phase)
-int op_rhs(ssx_ctx *c, int mode, const double *d, double *r) {
-    if (mode != SSX_MODE_PCG) return op_ST(c, d, r);
-    if (!fused(c)) {
-        TRY(op_sym_lambda(c, c->sr, d, c->tr2));
-        return op_ST(c, c->tr2, r);
-    }
-    Slab &s = c->sr;
-    TRY(run_phase(c, "R1", {fwd_sweep(s.g, s.plane, nullptr, d, s.datum, s.tp, s.tv)}));
-    return run_phase(c, "R2", {adj_sweep(s.g, scaled(s.plane, -4.0 * c->sgn), nullptr, c->tr2,
-                                         s.datum, s.tv, s.tp),
-                               adj_sweep(c->full, c->src, r, nullptr, c->rec, c->tr2, nullptr, 2)});
-}
-
 // ------------------------------------------------------------- plumbing --
 int enter(ssx_ctx *c) {
     CK(cudaEventRecord(c->ev_in, c->user));

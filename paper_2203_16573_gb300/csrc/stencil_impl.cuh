@@ -201,47 +201,69 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
             const int kk = wy + kWarps * a_, c = lane + 32 * b;
             if (kk >= VZH || c >= TX) continue;
             const int k = k0 - R + kk, i = i0 + c;
-            const bool own = (kk >= R && kk < R + TZ);
             float val = 0.0f;
             if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
                     d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
-                float cvz = g.cv;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
-                    cvz = B * g.cv;
-                    val = fmaf(-cvz, d, A * rvz[a_][b]);
+                    val = fmaf(-(B * g.cv), d, A * rvz[a_][b]);
                 } else {
-                    val = fmaf(-cvz, d, rvz[a_][b]);
+                    val = fmaf(-g.cv, d, rvz[a_][b]);
                 }
-                if (a.fsrc) {   // vertical load f e_z delta(z - z_s)
-                    const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-                    const int jl = i - a.src.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + jl], val);
-                }
-                if (own) {
-                    io.vz_out[k * pitch + i] = val;
-                    if (a.outv) {
-                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
-                        const int jl = i - a.rec.i0;
-                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                            atomicAdd(&a.outv[(size_t)n * a.rec.n + jl], (double)w * (double)val);
-                    }
-                }
+                if (kk >= R && kk < R + TZ) io.vz_out[k * pitch + i] = val;
             }
             sm.svz[kk][c] = val;
         }
+    // line rows only: vertical load f e_z delta(z - z_s), then the P v_z trace
+    if (a.fsrc || a.outv) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRV; a_++) {
+            const int kk = wy + kWarps * a_;
+            if (kk >= VZH) continue;
+            const int k = k0 - R + kk;
+            const bool own = (kk >= R && kk < R + TZ);
+            const float wi = a.fsrc ? row_weight(k, a.src.kv, a.src.wv0, a.src.wv1) : 0.0f;
+            const float ws = (a.outv && own) ? row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1) : 0.0f;
+            if (wi == 0.0f && ws == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < T::NCT; b++) {
+                const int c = lane + 32 * b;
+                if (c >= TX) continue;
+                const int i = i0 + c;
+                if (SP && !(i < g.NX && k >= 0 && k < g.NZ - 1)) continue;
+                float val = sm.svz[kk][c];
+                const int js = i - a.src.i0;
+                if (wi != 0.0f && js >= 0 && js < a.src.n) {
+                    float cvz = g.cv;
+                    if (SP) {
+                        float A, B;
+                        damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
+                        cvz = B * g.cv;
+                    }
+                    val = fmaf(cvz * (wi * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], val);
+                    sm.svz[kk][c] = val;
+                    if (own) io.vz_out[k * pitch + i] = val;
+                }
+                const int jr = i - a.rec.i0;
+                if (ws != 0.0f && jr >= 0 && jr < a.rec.n)
+                    atomicAdd(&a.outv[(size_t)n * a.rec.n + jr], (double)ws * (double)val);
+            }
+        }
+    }
     __syncthreads();
 
     // p^{n+1} on the tile
+    float pv[T::NRT][T::NCT], cpv[T::NRT][T::NCT];
 #pragma unroll
     for (int a_ = 0; a_ < T::NRT; a_++)
 #pragma unroll
         for (int b = 0; b < T::NCT; b++) {
+            pv[a_][b] = 0.0f;
+            cpv[a_][b] = 0.0f;
             const int r = wy + kWarps * a_, c = lane + 32 * b;
             if (r >= TZ || c >= TX) continue;
             const int k = k0 + r, i = i0 + c;
@@ -258,22 +280,40 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                     damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
                     cp *= B;
                 }
-                float val = fmaf(-cp, d, SP ? A * sm.sp[r + H][c + H] : sm.sp[r + H][c + H]);
-                if (a.hsrc) {   // constitutive defect h delta(z - z_s)
-                    const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
-                    const int jl = i - a.src.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                        val = fmaf(cp * (w * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + jl], val);
-                }
+                const float val = fmaf(-cp, d, SP ? A * sm.sp[r + H][c + H] : sm.sp[r + H][c + H]);
                 io.p_out[k * pitch + i] = val;
-                if (a.outp) {
-                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
-                    const int jl = i - a.rec.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        atomicAdd(&a.outp[(size_t)n * a.rec.n + jl], (double)w * (double)val);
-                }
+                pv[a_][b] = val;
+                cpv[a_][b] = cp;
             }
         }
+    // line rows only: constitutive defect h delta(z - z_s), then the P p trace
+    if (a.hsrc || a.outp) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRT; a_++) {
+            const int r = wy + kWarps * a_;
+            if (r >= TZ) continue;
+            const int k = k0 + r;
+            const float wi = a.hsrc ? row_weight(k, a.src.kp, a.src.wp0, a.src.wp1) : 0.0f;
+            const float ws = a.outp ? row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1) : 0.0f;
+            if (wi == 0.0f && ws == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < T::NCT; b++) {
+                const int c = lane + 32 * b;
+                if (c >= TX) continue;
+                const int i = i0 + c;
+                if (SP && !(k < g.NZ && i < g.NX)) continue;
+                float val = pv[a_][b];
+                const int js = i - a.src.i0;
+                if (wi != 0.0f && js >= 0 && js < a.src.n) {
+                    val = fmaf(cpv[a_][b] * (wi * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + js], val);
+                    io.p_out[k * pitch + i] = val;
+                }
+                const int jr = i - a.rec.i0;
+                if (ws != 0.0f && jr >= 0 && jr < a.rec.n)
+                    atomicAdd(&a.outp[(size_t)n * a.rec.n + jr], (double)ws * (double)val);
+            }
+        }
+    }
 }
 
 // One transposed step on the tile at (i0, k0) (same batching of loads).
@@ -366,15 +406,16 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
             }
             sm.svx[r][jj] = val;
         }
-    // vbar_z' likewise; read out the transposed velocity injection
+    // vbar_z' likewise
+    float ov[T::NRV][T::NCT];
 #pragma unroll
     for (int a_ = 0; a_ < T::NRV; a_++)
 #pragma unroll
         for (int b = 0; b < T::NCT; b++) {
+            ov[a_][b] = 0.0f;
             const int kk = wy + kWarps * a_, c = lane + 32 * b;
             if (kk >= VZH || c >= TX) continue;
             const int k = k0 - R + kk, i = i0 + c;
-            const bool own = (kk >= R && kk < R + TZ);
             float val = 0.0f;
             if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
                 float d = 0.0f;
@@ -385,33 +426,51 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 float A = 1.0f, B = 1.0f;
                 if (SP) damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
                 val = (B * g.cv) * vb;
-                if (own) {
-                    if (a.fbar) {
-                        const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-                        const int jl = i - a.src.i0;
-                        if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                            atomicAdd(&a.fbar[(size_t)n * a.src.n + jl],
-                                      (double)(w * a.src.scale) * (double)val);
-                    }
-                    float out = SP ? A * vb : vb;
-                    if (a.yv && n >= 1) {   // transposed sampling of step n-1
-                        const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
-                        const int jl = i - a.rec.i0;
-                        if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                            out = fmaf(w, (float)a.yv[(size_t)(n - 1) * a.rec.n + jl], out);
-                    }
+                if (kk >= R && kk < R + TZ) {
+                    const float out = SP ? A * vb : vb;
                     io.vz_out[k * pitch + i] = out;
+                    ov[a_][b] = out;
                 }
             }
             sm.svz[kk][c] = val;
         }
+    // line rows only: the transposed velocity injection read out, and the
+    // transposed sampling of step n-1 added to the outgoing state
+    if (a.fbar || (a.yv && n >= 1)) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRV; a_++) {
+            const int kk = wy + kWarps * a_;
+            if (kk >= VZH || kk < R || kk >= R + TZ) continue;
+            const int k = k0 - R + kk;
+            const float wf = a.fbar ? row_weight(k, a.src.kv, a.src.wv0, a.src.wv1) : 0.0f;
+            const float wy_ = (a.yv && n >= 1) ? row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1) : 0.0f;
+            if (wf == 0.0f && wy_ == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < T::NCT; b++) {
+                const int c = lane + 32 * b;
+                if (c >= TX) continue;
+                const int i = i0 + c;
+                if (SP && !(i < g.NX && k >= 0 && k < g.NZ - 1)) continue;
+                const int js = i - a.src.i0;
+                if (wf != 0.0f && js >= 0 && js < a.src.n)
+                    atomicAdd(&a.fbar[(size_t)n * a.src.n + js],
+                              (double)(wf * a.src.scale) * (double)sm.svz[kk][c]);
+                const int jr = i - a.rec.i0;
+                if (wy_ != 0.0f && jr >= 0 && jr < a.rec.n)
+                    io.vz_out[k * pitch + i] =
+                        fmaf(wy_, (float)a.yv[(size_t)(n - 1) * a.rec.n + jr], ov[a_][b]);
+            }
+        }
+    }
     __syncthreads();
 
     // pbar <- A_p pbar + D- (C_v vbar')
+    float po[T::NRT][T::NCT];
 #pragma unroll
     for (int a_ = 0; a_ < T::NRT; a_++)
 #pragma unroll
         for (int b = 0; b < T::NCT; b++) {
+            po[a_][b] = 0.0f;
             const int r = wy + kWarps * a_, c = lane + 32 * b;
             if (r >= TZ || c >= TX) continue;
             const int k = k0 + r, i = i0 + c;
@@ -430,15 +489,32 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 } else {
                     out = rp[a_][b] + d;
                 }
-                if (a.yp && n >= 1) {
-                    const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
-                    const int jl = i - a.rec.i0;
-                    if (w != 0.0f && jl >= 0 && jl < a.rec.n)
-                        out = fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jl], out);
-                }
                 io.p_out[k * pitch + i] = out;
+                po[a_][b] = out;
             }
         }
+    // line rows only: the transposed pressure sampling of step n-1
+    if (a.yp && n >= 1) {
+#pragma unroll
+        for (int a_ = 0; a_ < T::NRT; a_++) {
+            const int r = wy + kWarps * a_;
+            if (r >= TZ) continue;
+            const int k = k0 + r;
+            const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+            if (w == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < T::NCT; b++) {
+                const int c = lane + 32 * b;
+                if (c >= TX) continue;
+                const int i = i0 + c;
+                if (SP && !(k < g.NZ && i < g.NX)) continue;
+                const int jr = i - a.rec.i0;
+                if (jr >= 0 && jr < a.rec.n)
+                    io.p_out[k * pitch + i] =
+                        fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jr], po[a_][b]);
+            }
+        }
+    }
 }
 
 template <int R, int TX, int TZ, int NT>
