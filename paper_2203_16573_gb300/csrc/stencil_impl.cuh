@@ -137,6 +137,12 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int n = io.n;
+    // grid scalars in registers: they are read in every element of every loop
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+    const int NX = g.NX, NZ = g.NZ;
 
     float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rk[T::NRT][T::NCT];
 #pragma unroll
@@ -145,7 +151,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
         for (int b = 0; b < T::NCX; b++) {
             const int r = wy + kWarps * a_, jj = lane + 32 * b;
             const int k = k0 + r, j = i0 - R + jj;
-            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < NZ && j >= 0 && j < NX - 1));
             rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
         }
 #pragma unroll
@@ -154,7 +160,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
         for (int b = 0; b < T::NCT; b++) {
             const int kk = wy + kWarps * a_, c = lane + 32 * b;
             const int k = k0 - R + kk, i = i0 + c;
-            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            const bool ok = kk < VZH && c < TX && (!SP || (i < NX && k >= 0 && k < NZ - 1));
             rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
         }
 #pragma unroll
@@ -162,7 +168,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
 #pragma unroll
         for (int b = 0; b < T::NCT; b++) {
             const int r = wy + kWarps * a_, c = lane + 32 * b;
-            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < NZ && i0 + c < NX));
             rk[a_][b] = ok ? __ldg(g.kap + (k0 + r) * pitch + i0 + c) : 0.0f;
         }
     stage_p<R, TX, TZ, NT, SP, false>(g, io.p_in, i0, k0, sm.sp);
@@ -177,17 +183,17 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
             if (r >= TZ || jj >= VXW) continue;
             const int k = k0 + r, j = i0 - R + jj;
             float val = 0.0f;
-            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
+            if (!SP || (k < NZ && j >= 0 && j < NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
-                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
+                for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
-                    val = fmaf(-(B * g.cv), d, A * rvx[a_][b]);
+                    val = fmaf(-(B * cv), d, A * rvx[a_][b]);
                 } else {
-                    val = fmaf(-g.cv, d, rvx[a_][b]);
+                    val = fmaf(-cv, d, rvx[a_][b]);
                 }
                 if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = val;
             }
@@ -202,17 +208,17 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
             if (kk >= VZH || c >= TX) continue;
             const int k = k0 - R + kk, i = i0 + c;
             float val = 0.0f;
-            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
+            if (!SP || (i < NX && k >= 0 && k < NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
-                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+                    d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
-                    val = fmaf(-(B * g.cv), d, A * rvz[a_][b]);
+                    val = fmaf(-(B * cv), d, A * rvz[a_][b]);
                 } else {
-                    val = fmaf(-g.cv, d, rvz[a_][b]);
+                    val = fmaf(-cv, d, rvz[a_][b]);
                 }
                 if (kk >= R && kk < R + TZ) io.vz_out[k * pitch + i] = val;
             }
@@ -234,15 +240,15 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                 const int c = lane + 32 * b;
                 if (c >= TX) continue;
                 const int i = i0 + c;
-                if (SP && !(i < g.NX && k >= 0 && k < g.NZ - 1)) continue;
+                if (SP && !(i < NX && k >= 0 && k < NZ - 1)) continue;
                 float val = sm.svz[kk][c];
                 const int js = i - a.src.i0;
                 if (wi != 0.0f && js >= 0 && js < a.src.n) {
-                    float cvz = g.cv;
+                    float cvz = cv;
                     if (SP) {
                         float A, B;
                         damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
-                        cvz = B * g.cv;
+                        cvz = B * cv;
                     }
                     val = fmaf(cvz * (wi * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], val);
                     sm.svz[kk][c] = val;
@@ -267,12 +273,12 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
             const int r = wy + kWarps * a_, c = lane + 32 * b;
             if (r >= TZ || c >= TX) continue;
             const int k = k0 + r, i = i0 + c;
-            if (!SP || (k < g.NZ && i < g.NX)) {
+            if (!SP || (k < NZ && i < NX)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) {
-                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
-                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
+                    d = fmaf(cc[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(cc[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
                 float cp = rk[a_][b], A = 1.0f;
                 if (SP) {
@@ -301,7 +307,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
                 const int c = lane + 32 * b;
                 if (c >= TX) continue;
                 const int i = i0 + c;
-                if (SP && !(k < g.NZ && i < g.NX)) continue;
+                if (SP && !(k < NZ && i < NX)) continue;
                 float val = pv[a_][b];
                 const int js = i - a.src.i0;
                 if (wi != 0.0f && js >= 0 && js < a.src.n) {
@@ -328,6 +334,12 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int n = io.n;
+    // grid scalars in registers: they are read in every element of every loop
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+    const int NX = g.NX, NZ = g.NZ;
 
     float rvx[T::NRT][T::NCX], rvz[T::NRV][T::NCT], rp[T::NRT][T::NCT];
 #pragma unroll
@@ -336,7 +348,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
         for (int b = 0; b < T::NCX; b++) {
             const int r = wy + kWarps * a_, jj = lane + 32 * b;
             const int k = k0 + r, j = i0 - R + jj;
-            const bool ok = r < TZ && jj < VXW && (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1));
+            const bool ok = r < TZ && jj < VXW && (!SP || (k < NZ && j >= 0 && j < NX - 1));
             rvx[a_][b] = ok ? ldf(io.vx_in + k * pitch + j) : 0.0f;
         }
 #pragma unroll
@@ -345,7 +357,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
         for (int b = 0; b < T::NCT; b++) {
             const int kk = wy + kWarps * a_, c = lane + 32 * b;
             const int k = k0 - R + kk, i = i0 + c;
-            const bool ok = kk < VZH && c < TX && (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1));
+            const bool ok = kk < VZH && c < TX && (!SP || (i < NX && k >= 0 && k < NZ - 1));
             rvz[a_][b] = ok ? ldf(io.vz_in + k * pitch + i) : 0.0f;
         }
 #pragma unroll
@@ -353,7 +365,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
 #pragma unroll
         for (int b = 0; b < T::NCT; b++) {
             const int r = wy + kWarps * a_, c = lane + 32 * b;
-            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < g.NZ && i0 + c < g.NX));
+            const bool ok = r < TZ && c < TX && (!SP || (k0 + r < NZ && i0 + c < NX));
             rp[a_][b] = ok ? ldf(io.p_in + (k0 + r) * pitch + i0 + c) : 0.0f;
         }
     // q = C_p pbar over tile + 2k halo
@@ -371,7 +383,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 for (int b = 0; b < T::NCT; b++) {
                     const int c = lane + 32 * b;
                     const int i = i0 + c, jl = i - a.src.i0;
-                    if (c < TX && i < g.NX && jl >= 0 && jl < a.src.n)
+                    if (c < TX && i < NX && jl >= 0 && jl < a.src.n)
                         atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
                                   (double)(w * a.src.scale) * (double)sm.sp[r + H][c + H]);
                 }
@@ -388,19 +400,19 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
             if (r >= TZ || jj >= VXW) continue;
             const int k = k0 + r, j = i0 - R + jj;
             float val = 0.0f;
-            if (!SP || (k < g.NZ && j >= 0 && j < g.NX - 1)) {
+            if (!SP || (k < NZ && j >= 0 && j < NX - 1)) {
                 const float *row = &sm.sp[r + H][jj + R];
                 float d = 0.0f;
 #pragma unroll
-                for (int m = 1; m <= R; m++) d = fmaf(g.c[m - 1], row[m] - row[1 - m], d);
+                for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
                 const float vb = rvx[a_][b] + d;
                 if (SP) {
                     float A, B;
                     damp(__ldg(g.sxh + j) + __ldg(g.szi + k), A, B);
-                    val = (B * g.cv) * vb;
+                    val = (B * cv) * vb;
                     if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = A * vb;
                 } else {
-                    val = g.cv * vb;
+                    val = cv * vb;
                     if (jj >= R && jj < R + TX) io.vx_out[k * pitch + j] = vb;
                 }
             }
@@ -417,15 +429,15 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
             if (kk >= VZH || c >= TX) continue;
             const int k = k0 - R + kk, i = i0 + c;
             float val = 0.0f;
-            if (!SP || (i < g.NX && k >= 0 && k < g.NZ - 1)) {
+            if (!SP || (i < NX && k >= 0 && k < NZ - 1)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++)
-                    d = fmaf(g.c[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+                    d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
                 const float vb = rvz[a_][b] + d;
                 float A = 1.0f, B = 1.0f;
                 if (SP) damp(__ldg(g.sxi + i) + __ldg(g.szh + k), A, B);
-                val = (B * g.cv) * vb;
+                val = (B * cv) * vb;
                 if (kk >= R && kk < R + TZ) {
                     const float out = SP ? A * vb : vb;
                     io.vz_out[k * pitch + i] = out;
@@ -450,7 +462,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 const int c = lane + 32 * b;
                 if (c >= TX) continue;
                 const int i = i0 + c;
-                if (SP && !(i < g.NX && k >= 0 && k < g.NZ - 1)) continue;
+                if (SP && !(i < NX && k >= 0 && k < NZ - 1)) continue;
                 const int js = i - a.src.i0;
                 if (wf != 0.0f && js >= 0 && js < a.src.n)
                     atomicAdd(&a.fbar[(size_t)n * a.src.n + js],
@@ -474,12 +486,12 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
             const int r = wy + kWarps * a_, c = lane + 32 * b;
             if (r >= TZ || c >= TX) continue;
             const int k = k0 + r, i = i0 + c;
-            if (!SP || (k < g.NZ && i < g.NX)) {
+            if (!SP || (k < NZ && i < NX)) {
                 float d = 0.0f;
 #pragma unroll
                 for (int m = 1; m <= R; m++) {
-                    d = fmaf(g.c[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
-                    d = fmaf(g.c[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
+                    d = fmaf(cc[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+                    d = fmaf(cc[m - 1], sm.svz[r + R + m - 1][c] - sm.svz[r + R - m][c], d);
                 }
                 float out;
                 if (SP) {
@@ -507,7 +519,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
                 const int c = lane + 32 * b;
                 if (c >= TX) continue;
                 const int i = i0 + c;
-                if (SP && !(k < g.NZ && i < g.NX)) continue;
+                if (SP && !(k < NZ && i < NX)) continue;
                 const int jr = i - a.rec.i0;
                 if (jr >= 0 && jr < a.rec.n)
                     io.p_out[k * pitch + i] =
