@@ -361,6 +361,8 @@ def run_batch(args):
     alphas = [sp.alpha for sp in specs]
     outs = [c._empty(c.n_line) for c in ctxs]
     lead = ctxs[0]
+    if args.tile_config >= 0:
+        lead.set_tile_config(args.tile_config)
     # warm-up: tunes and captures the batched phases
     ssx.solve_batch(ctxs, ds, alphas, args.maxit, 0.0, ssx.MODE_PCG, outs)
     torch.cuda.synchronize()
@@ -392,7 +394,7 @@ def run_batch(args):
                          "unit": "GB/s", "frac": gpts * BYTES_PER_POINT / hbm, "traffic": None,
                          "peak_kind": peak_kind, "kernel": "k_multi_tab (all shots' sweeps per launch)",
                          "avg_launch_us": 1000.0 * st["sweep_ms"] / max(st["timed_steps"], 1)},
-            "gpu_launches": st["kernel_launches"], "tile_cfg_lead": st["tile_cfg"], "clocks": clk}
+            "gpu_launches": st["kernel_launches"], "tile_config": args.tile_config, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -452,6 +454,8 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--tile-config", type=int, default=-1,
+                    help="fix the stencil tile configuration (0-7) instead of autotuning")
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--nt", type=int, default=5000)
     ap.add_argument("--maxit", type=int, default=2)
