@@ -33,9 +33,15 @@ namespace ssx {
 namespace {
 
 // Sponge factors of a point with s = (sigma_x + sigma_z) dt/2:
-// B = 1/(1+s) (correctly rounded) and A = (1-s)/(1+s) = 2B - 1.
+// B = 1/(1+s) and A = (1-s)/(1+s) = 2B - 1. The reciprocal is the hardware's
+// approximate one (rcp.approx, about one unit in the last place: far below the
+// f32 rounding of the fields it scales), except that s = 0 gives exactly
+// B = A = 1, so that an undamped point rounds the same whether its tile takes
+// the sponge path or the interior path.
 __device__ __forceinline__ void damp(float s, float &A, float &B) {
-    B = __frcp_rn(1.0f + s);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + s));
+    B = s == 0.0f ? 1.0f : r;
     A = fmaf(2.0f, B, -1.0f);
 }
 
@@ -78,7 +84,8 @@ __device__ __forceinline__ bool interior_tile(const GridArgs &g, int i0, int k0)
 
 // Loops over the shared-memory regions: warp w takes rows w, w+8, ...; lanes
 // take columns lane, lane+32, ... (trip counts are compile-time constants).
-#define FOR_ROWS(r, n) for (int r = wy; r < (n); r += NT / 32)
+#define FOR_ROWS(r, n) _Pragma("unroll") for (int r##_u = 0; r##_u < ((n) + NT / 32 - 1) / (NT / 32); r##_u++) \
+    if (const int r = wy + (NT / 32) * r##_u; r < (n))
 #define FOR_COLS(c, n) _Pragma("unroll") for (int c##_u = 0; c##_u < ((n) + 31) / 32; c##_u++) \
     if (const int c = lane + 32 * c##_u; c < (n))
 
@@ -529,22 +536,492 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiles by column strips. Thread t owns tile column c = t % TX and the L rows
+// [s L, s L + L) of strip s = t / TX. Its v_z comes from a register window of
+// L + 2k - 1 values down its column (instead of 2k shared-memory reads per
+// point), the z part of its pressure update from a window over the v_z rows,
+// and its own old pressures from the first window; only the x differences read
+// shared memory per point. The damping factors' column parts are loaded once
+// per thread and the row parts once per row. The halo values of v (2k-1
+// columns of v_x, 2k-1 rows of v_z) are shared out over all threads.
+//
+// SP: the tile meets the sponge or the grid edge (damping and masks);
+// LN: a line row (injection or sampling) meets the tile. Every point's
+// arithmetic is the per-point arithmetic of fwd_tile_impl / adj_tile_impl,
+// term for term, so results do not depend on the tile shape.
+// ---------------------------------------------------------------------------
+template <int R, int TX, int TZ, int NT>
+struct StripShape {
+    static constexpr int NS = NT / TX;                 // strips per tile
+    static constexpr int L = NS > 0 ? TZ / NS : 0;     // rows per strip
+    static constexpr bool ok = (NT % TX == 0) && NS >= 1 && (TZ % NS == 0) && L >= 2;
+    static constexpr int NHR = 2 * R - 1;              // halo rows of v_z, halo columns of v_x
+    // v_x halo: TZ rows x NHR columns, the columns padded to a power of two
+    static constexpr int HXP = NHR <= 1 ? 1 : NHR <= 2 ? 2 : NHR <= 4 ? 4 : 8;
+    static constexpr int NQX = (TZ * HXP + NT - 1) / NT;   // v_x halo items per thread
+    // v_z halo: strip s of column c takes halo rows s, s + NS, ...
+    static constexpr int NQZ = NS > 0 ? (NHR + NS - 1) / NS : 0;
+};
+
+// rows kl, kl + 1 of a line against the rows [lo, hi)
+__device__ __forceinline__ bool line_hits(int kl, int lo, int hi) { return kl + 1 >= lo && kl < hi; }
+
+template <int R, int TZ>
+__device__ __forceinline__ bool fwd_lines(const FwdArgs &a, int k0) {
+    return (a.fsrc && line_hits(a.src.kv, k0 - R, k0 + TZ + R - 1)) ||
+           (a.hsrc && line_hits(a.src.kp, k0, k0 + TZ)) ||
+           (a.outv && line_hits(a.rec.kv, k0, k0 + TZ)) ||
+           (a.outp && line_hits(a.rec.kp, k0, k0 + TZ));
+}
+
+template <int TZ>
+__device__ __forceinline__ bool adj_lines(const AdjArgs &a, int k0, int n) {
+    return (a.hbar && line_hits(a.src.kp, k0, k0 + TZ)) ||
+           (a.fbar && line_hits(a.src.kv, k0, k0 + TZ)) ||
+           (a.yv && n >= 1 && line_hits(a.rec.kv, k0, k0 + TZ)) ||
+           (a.yp && n >= 1 && line_hits(a.rec.kp, k0, k0 + TZ));
+}
+
+// Strip geometry of one thread and its halo items. In a sponge tile every
+// load is made (the field storage has an apron of zeros around the padded
+// grid, so all addresses are inside it) and points outside the grid are
+// masked afterwards, which keeps the element loops free of branches.
+template <int R, int TX, int TZ, int NT>
+struct StripThread {
+    using Q = StripShape<R, TX, TZ, NT>;
+    int c, rs, i;
+    int hx_r[Q::NQX], hx_jj[Q::NQX];    // v_x halo: tile row, v_x column (-1: none)
+    int hz_kk[Q::NQZ];                  // v_z halo: v_z row (-1: none)
+    __device__ __forceinline__ StripThread(int i0) {
+        const int t = threadIdx.x;
+        c = t % TX;
+        rs = (t / TX) * Q::L;
+        i = i0 + c;
+#pragma unroll
+        for (int q = 0; q < Q::NQX; q++) {
+            const int e = t + q * NT, hx = e % Q::HXP;   // power of two: mask and shift
+            hx_r[q] = e / Q::HXP;
+            hx_jj[q] = (hx < Q::NHR && e < TZ * Q::HXP) ? (hx < R ? hx : hx + TX) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < Q::NQZ; q++) {
+            const int hz = t / TX + q * Q::NS;
+            hz_kk[q] = hz < Q::NHR ? (hz < R ? hz : hz + TZ) : -1;
+        }
+    }
+};
+
+template <int R, int TX, int TZ, int NT, bool SP, bool LN>
+__device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                          TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    using Q = StripShape<R, TX, TZ, NT>;
+    constexpr int H = S::H, L = Q::L, W = L + 2 * R - 1;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
+    const StripThread<R, TX, TZ, NT> th(i0);
+    const int c = th.c, rs = th.rs, i = th.i;
+    const int n = io.n;
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+    const bool colp = !SP || i < NX;        // p, v_z column inside the grid
+    const bool colx = !SP || i < NX - 1;    // v_x column inside the grid
+
+    // every global operand of the step, in one batch
+    float rvx[L], rvz[L], rk[L], rhx[Q::NQX], rhz[Q::NQZ];
+    float sxi = 0.0f, sxh = 0.0f, szi[L], szh[L];
+    if (SP) {
+        sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
+        sxh = __ldg(g.sxh + min(i, NX - 1));
+    }
+    {
+        const int o0 = (k0 + rs) * pitch + i;
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            const int k = k0 + rs + j;
+            rvx[j] = ldf(io.vx_in + o0 + j * pitch);
+            rvz[j] = ldf(io.vz_in + o0 + j * pitch);
+            rk[j] = __ldg(g.kap + o0 + j * pitch);
+            if (SP) {
+                szi[j] = __ldg(g.szi + min(k, NZ - 1));
+                szh[j] = __ldg(g.szh + min(k, NZ - 1));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q::NQX; q++)
+        rhx[q] = th.hx_jj[q] >= 0 ? ldf(io.vx_in + (k0 + th.hx_r[q]) * pitch + (i0 - R + th.hx_jj[q])) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q::NQZ; q++)
+        rhz[q] = th.hz_kk[q] >= 0 ? ldf(io.vz_in + (k0 - R + th.hz_kk[q]) * pitch + i) : 0.0f;
+    stage_p<R, TX, TZ, NT, SP, false>(g, io.p_in, i0, k0, sm.sp);
+    __syncthreads();
+
+    // own strip: v_z from a window down the column, v_x from the row
+    float pw[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) pw[w] = sm.sp[rs - R + 1 + w + H][c + H];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const int r = rs + j, k = k0 + r;
+        const bool okz = !SP || (colp && k < NZ - 1);
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], pw[j + R - 1 + m] - pw[j + R - m], d);
+        float vz, cvz = cv;
+        if (SP) {
+            float A, B;
+            damp(sxi + szh[j], A, B);
+            cvz = B * cv;
+            vz = fmaf(-cvz, d, A * rvz[j]);
+        } else {
+            vz = fmaf(-cv, d, rvz[j]);
+        }
+        if (LN && a.fsrc && okz) {   // vertical load f e_z delta(z - z_s)
+            const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+            const int js = i - a.src.i0;
+            if (w != 0.0f && js >= 0 && js < a.src.n)
+                vz = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], vz);
+        }
+        if (SP) vz = okz ? vz : 0.0f;
+        if (okz) io.vz_out[k * pitch + i] = vz;
+        if (LN && a.outv && okz) {   // P v_z trace
+            const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+            const int jr = i - a.rec.i0;
+            if (w != 0.0f && jr >= 0 && jr < a.rec.n)
+                atomicAdd(&a.outv[(size_t)n * a.rec.n + jr], (double)w * (double)vz);
+        }
+        sm.svz[r + R][c] = vz;
+
+        const bool okx = !SP || (colx && k < NZ);
+        const float *row = &sm.sp[r + H][c + H];
+        d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
+        float vx;
+        if (SP) {
+            float A, B;
+            damp(sxh + szi[j], A, B);
+            vx = fmaf(-(B * cv), d, A * rvx[j]);
+            vx = okx ? vx : 0.0f;
+        } else {
+            vx = fmaf(-cv, d, rvx[j]);
+        }
+        if (okx) io.vx_out[k * pitch + i] = vx;
+        sm.svx[r][c + R] = vx;
+    }
+    // halo v (not written out)
+#pragma unroll
+    for (int q = 0; q < Q::NQX; q++) {
+        const int jj = th.hx_jj[q], r = th.hx_r[q];
+        if (jj < 0) continue;
+        const int k = k0 + r, j = i0 - R + jj;
+        const float *row = &sm.sp[r + H][jj + R];
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
+        float val;
+        if (SP) {
+            const bool ok = k < NZ && j >= 0 && j < NX - 1;
+            float A, B;
+            damp(__ldg(g.sxh + (ok ? j : 0)) + __ldg(g.szi + (ok ? k : 0)), A, B);
+            val = ok ? fmaf(-(B * cv), d, A * rhx[q]) : 0.0f;
+        } else {
+            val = fmaf(-cv, d, rhx[q]);
+        }
+        sm.svx[r][jj] = val;
+    }
+#pragma unroll
+    for (int q = 0; q < Q::NQZ; q++) {
+        const int kk = th.hz_kk[q];
+        if (kk < 0) continue;
+        const int k = k0 - R + kk;
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++)
+            d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+        const bool ok = !SP || (colp && k >= 0 && k < NZ - 1);
+        float val, cvz = cv;
+        if (SP) {
+            float A, B;
+            damp(sxi + __ldg(g.szh + (ok ? k : 0)), A, B);
+            cvz = B * cv;
+            val = fmaf(-cvz, d, A * rhz[q]);
+        } else {
+            val = fmaf(-cv, d, rhz[q]);
+        }
+        if (LN && a.fsrc && ok) {
+            const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+            const int js = i - a.src.i0;
+            if (w != 0.0f && js >= 0 && js < a.src.n)
+                val = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], val);
+        }
+        sm.svz[kk][c] = ok ? val : 0.0f;
+    }
+    __syncthreads();
+
+    // own strip: p^{n+1}; z differences from a window over the v_z rows
+    float zw[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) zw[w] = sm.svz[rs + w][c];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const int r = rs + j, k = k0 + r;
+        const bool okp = !SP || (colp && k < NZ);
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) {
+            d = fmaf(cc[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+            d = fmaf(cc[m - 1], zw[j + R + m - 1] - zw[j + R - m], d);
+        }
+        float cp = rk[j], val;
+        if (SP) {
+            float A, B;
+            damp(sxi + szi[j], A, B);
+            cp *= B;
+            val = fmaf(-cp, d, A * pw[j + R - 1]);
+        } else {
+            val = fmaf(-cp, d, pw[j + R - 1]);
+        }
+        if (LN && a.hsrc && okp) {   // constitutive defect h delta(z - z_s)
+            const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+            const int js = i - a.src.i0;
+            if (w != 0.0f && js >= 0 && js < a.src.n)
+                val = fmaf(cp * (w * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + js], val);
+        }
+        if (okp) io.p_out[k * pitch + i] = val;
+        if (LN && a.outp && okp) {   // P p trace
+            const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+            const int jr = i - a.rec.i0;
+            if (w != 0.0f && jr >= 0 && jr < a.rec.n)
+                atomicAdd(&a.outp[(size_t)n * a.rec.n + jr], (double)w * (double)val);
+        }
+    }
+}
+
+// The transposed step by column strips (same split of the work as fwd_strip;
+// per point the arithmetic of adj_tile_impl).
+template <int R, int TX, int TZ, int NT, bool SP, bool LN>
+__device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                          TileSmem<R, TX, TZ> &sm) {
+    using S = TileSmem<R, TX, TZ>;
+    using Q = StripShape<R, TX, TZ, NT>;
+    constexpr int H = S::H, L = Q::L, W = L + 2 * R - 1;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
+    const StripThread<R, TX, TZ, NT> th(i0);
+    const int c = th.c, rs = th.rs, i = th.i;
+    const int n = io.n;
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+    const bool colp = !SP || i < NX;
+    const bool colx = !SP || i < NX - 1;
+
+    float rvx[L], rvz[L], rp[L], rhx[Q::NQX], rhz[Q::NQZ];
+    float sxi = 0.0f, sxh = 0.0f, szi[L], szh[L];
+    if (SP) {
+        sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
+        sxh = __ldg(g.sxh + min(i, NX - 1));
+    }
+    {
+        const int o0 = (k0 + rs) * pitch + i;
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            const int k = k0 + rs + j;
+            rvx[j] = ldf(io.vx_in + o0 + j * pitch);
+            rvz[j] = ldf(io.vz_in + o0 + j * pitch);
+            rp[j] = ldf(io.p_in + o0 + j * pitch);
+            if (SP) {
+                szi[j] = __ldg(g.szi + min(k, NZ - 1));
+                szh[j] = __ldg(g.szh + min(k, NZ - 1));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q::NQX; q++)
+        rhx[q] = th.hx_jj[q] >= 0 ? ldf(io.vx_in + (k0 + th.hx_r[q]) * pitch + (i0 - R + th.hx_jj[q])) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q::NQZ; q++)
+        rhz[q] = th.hz_kk[q] >= 0 ? ldf(io.vz_in + (k0 - R + th.hz_kk[q]) * pitch + i) : 0.0f;
+    // q = C_p pbar over tile + 2k halo
+    stage_p<R, TX, TZ, NT, SP, true>(g, io.p_in, i0, k0, sm.sp);
+    __syncthreads();
+
+    float qw[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) qw[w] = sm.sp[rs - R + 1 + w + H][c + H];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const int r = rs + j, k = k0 + r;
+        if (LN && a.hbar && colp) {   // transposed pressure injection: hbar[n] = scale sum_k w_k q
+            const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
+            const int jl = i - a.src.i0;
+            if (w != 0.0f && jl >= 0 && jl < a.src.n)
+                atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
+                          (double)(w * a.src.scale) * (double)qw[j + R - 1]);
+        }
+        // vbar_x' = vbar_x + D+ q; C_vx vbar_x' kept for the p update
+        const bool okx = !SP || (colx && k < NZ);
+        const float *row = &sm.sp[r + H][c + H];
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
+        const float vbx = rvx[j] + d;
+        float vx, ox;
+        if (SP) {
+            float A, B;
+            damp(sxh + szi[j], A, B);
+            vx = okx ? (B * cv) * vbx : 0.0f;
+            ox = A * vbx;
+        } else {
+            vx = cv * vbx;
+            ox = vbx;
+        }
+        if (okx) io.vx_out[k * pitch + i] = ox;
+        sm.svx[r][c + R] = vx;
+        // vbar_z' likewise, from the window down the column
+        const bool okz = !SP || (colp && k < NZ - 1);
+        d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], qw[j + R - 1 + m] - qw[j + R - m], d);
+        const float vb = rvz[j] + d;
+        float A = 1.0f, B = 1.0f;
+        if (SP) damp(sxi + szh[j], A, B);
+        float vz = (B * cv) * vb;
+        float out = SP ? A * vb : vb;
+        if (LN && a.fbar && okz) {   // transposed velocity injection read out
+            const float wf = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
+            const int js = i - a.src.i0;
+            if (wf != 0.0f && js >= 0 && js < a.src.n)
+                atomicAdd(&a.fbar[(size_t)n * a.src.n + js], (double)(wf * a.src.scale) * (double)vz);
+        }
+        if (LN && a.yv && n >= 1 && okz) {   // transposed v_z sampling of step n-1
+            const float wy_ = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
+            const int jr = i - a.rec.i0;
+            if (wy_ != 0.0f && jr >= 0 && jr < a.rec.n)
+                out = fmaf(wy_, (float)a.yv[(size_t)(n - 1) * a.rec.n + jr], out);
+        }
+        if (okz) io.vz_out[k * pitch + i] = out;
+        sm.svz[r + R][c] = okz ? vz : 0.0f;
+    }
+    // halo vbar' (not written out)
+#pragma unroll
+    for (int q = 0; q < Q::NQX; q++) {
+        const int jj = th.hx_jj[q], r = th.hx_r[q];
+        if (jj < 0) continue;
+        const int k = k0 + r, j = i0 - R + jj;
+        const float *row = &sm.sp[r + H][jj + R];
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
+        const float vb = rhx[q] + d;
+        float val;
+        if (SP) {
+            const bool ok = k < NZ && j >= 0 && j < NX - 1;
+            float A, B;
+            damp(__ldg(g.sxh + (ok ? j : 0)) + __ldg(g.szi + (ok ? k : 0)), A, B);
+            val = ok ? (B * cv) * vb : 0.0f;
+        } else {
+            val = cv * vb;
+        }
+        sm.svx[r][jj] = val;
+    }
+#pragma unroll
+    for (int q = 0; q < Q::NQZ; q++) {
+        const int kk = th.hz_kk[q];
+        if (kk < 0) continue;
+        const int k = k0 - R + kk;
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++)
+            d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+        const float vb = rhz[q] + d;
+        float val;
+        if (SP) {
+            const bool ok = colp && k >= 0 && k < NZ - 1;
+            float A, B;
+            damp(sxi + __ldg(g.szh + (ok ? k : 0)), A, B);
+            val = ok ? (B * cv) * vb : 0.0f;
+        } else {
+            val = (1.0f * cv) * vb;
+        }
+        sm.svz[kk][c] = val;
+    }
+    __syncthreads();
+
+    // pbar <- A_p pbar + D- (C_v vbar')
+    float zw[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) zw[w] = sm.svz[rs + w][c];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const int r = rs + j, k = k0 + r;
+        const bool okp = !SP || (colp && k < NZ);
+        float d = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) {
+            d = fmaf(cc[m - 1], sm.svx[r][c + R + m - 1] - sm.svx[r][c + R - m], d);
+            d = fmaf(cc[m - 1], zw[j + R + m - 1] - zw[j + R - m], d);
+        }
+        float out;
+        if (SP) {
+            float A, B;
+            damp(sxi + szi[j], A, B);
+            out = fmaf(A, rp[j], d);
+        } else {
+            out = rp[j] + d;
+        }
+        if (LN && a.yp && n >= 1 && okp) {   // transposed pressure sampling of step n-1
+            const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
+            const int jr = i - a.rec.i0;
+            if (w != 0.0f && jr >= 0 && jr < a.rec.n)
+                out = fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jr], out);
+        }
+        if (okp) io.p_out[k * pitch + i] = out;
+    }
+}
+
 template <int R, int TX, int TZ, int NT>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int i0, int k0,
                                          TileSmem<R, TX, TZ> &sm) {
-    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
-        fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
-    else
-        fwd_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+    const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
+    if constexpr (StripShape<R, TX, TZ, NT>::ok) {
+        const bool ln = fwd_lines<R, TZ>(a, k0);
+        if (in) {
+            if (ln) fwd_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, sm);
+            else fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, sm);
+        } else {
+            if (ln) fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, sm);
+            else fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, sm);
+        }
+    } else {
+        if (in) fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
+        else fwd_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+    }
 }
 
 template <int R, int TX, int TZ, int NT>
 __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int i0, int k0,
                                          TileSmem<R, TX, TZ> &sm) {
-    if (interior_tile<R, TX, TZ>(a.g, i0, k0))
-        adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
-    else
-        adj_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+    const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
+    if constexpr (StripShape<R, TX, TZ, NT>::ok) {
+        const bool ln = adj_lines<TZ>(a, k0, io.n);
+        if (in) {
+            if (ln) adj_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, sm);
+            else adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, sm);
+        } else {
+            if (ln) adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, sm);
+            else adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, sm);
+        }
+    } else {
+        if (in) adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
+        else adj_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
+    }
 }
 
 // Programmatic dependent launch: let the next step's grid become resident
