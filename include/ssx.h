@@ -244,8 +244,12 @@ int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
 /* Tile configuration of the step kernels: -1 (default) lets the library time
  * every configuration on each grid's first sweep in each direction and keep
  * the fastest; 0..7 fixes one (tile 64x16/256 threads, 64x16/512, 64x16/1024,
- * 64x32/512, 64x32/1024, 128x16/512, 128x32/1024, 32x16/256). All
- * configurations compute identical results. */
+ * 64x32/512, 64x32/1024, 128x16/512, 128x32/1024, 32x16/256); 8 + k fixes
+ * shape k with the multi-sweep steps run by the TMA-staged kernel (operand
+ * tiles copied by the tensor memory accelerator into a two-stage shared-memory
+ * pipeline, persistent CTAs), available for space order 8 and the shapes
+ * whose column strips hold at least two rows (all but 2); elsewhere 8 + k
+ * runs shape k. All configurations compute identical results. */
 int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
 
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the

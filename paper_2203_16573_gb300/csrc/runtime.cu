@@ -20,6 +20,8 @@
 // Each sweep (memsets + nt step kernels) is captured once into a CUDA graph
 // per (grid, buffers) and replayed; all operators run on the context's own
 // non-blocking stream, ordered against the caller's stream by events.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,6 +31,7 @@
 #include <chrono>
 #include <deque>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -109,7 +112,8 @@ struct ssx_ctx {
         int cfg = -1;
         JobSet jobs{};          // small phases: by-value kernel parameter
         Job *dtab = nullptr;    // large phases (batches): device table
-        int njobs = 0, total = 0, T = 0;
+        TmaJob *ttab = nullptr; // TMA-staged kernel: sweeps with their tensor maps
+        int njobs = 0, total = 0, T = 0, cap = 0;
     };
     std::unordered_map<std::string, PhaseInfo> phases;
 
@@ -126,6 +130,7 @@ struct ssx_ctx {
     int *d_err = nullptr;      // persistent-sweep wait timeout flag (device)
     int sweep_mode = SSX_SWEEP_AUTO;
     int cap[kNumTileCfgs][2];         // co-resident CTAs of the persistent kernels (-1: unknown)
+    int tma_cap[kNumTileCfgs];        // co-resident CTAs of the TMA-staged phase kernel (-1: unknown)
     int forced_cfg = -1;              // tile configuration fixed by the caller (-1: autotune)
     bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
     bool use_graphs = true;
@@ -294,8 +299,10 @@ int check_sweeps_quiet(ssx_ctx *c) {
     CK(cudaMemcpyAsync(eh, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     if (*eh != 0) {
+        const int code = *eh;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
-        return fail(c, SSX_ERR_CUDA, "a persistent sweep's neighbour wait timed out");
+        return fail(c, SSX_ERR_CUDA, code == 2 ? "a phase kernel's tensor-copy wait timed out"
+                                               : "a persistent sweep's neighbour wait timed out");
     }
     return SSX_OK;
 }
@@ -410,7 +417,7 @@ int select_config(ssx_ctx *c, DGrid &G, bool adj) {
     };
     std::vector<Cand> cands;
     for (int k = 0; k < kNumTileCfgs; k++) {
-        if (c->forced_cfg >= 0 && k != c->forced_cfg) continue;
+        if (c->forced_cfg >= 0 && k != c->forced_cfg % kNumTileCfgs) continue;
         if (c->sweep_mode != SSX_SWEEP_PERSISTENT) cands.push_back({k, false});
         if (c->sweep_mode != SSX_SWEEP_STEP && tiles_of(G, k) <= capacity(c, k, adj))
             cands.push_back({k, true});
@@ -574,6 +581,7 @@ Sweep adj_sweep(DGrid &G, const Line &src, double *hb, double *fb, const Line &r
 }
 
 std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, int *total) {
+    cfg %= kNumTileCfgs;   // the TMA-staged kernel tiles like the shape it is built on
     std::vector<Job> jobs(sw.size());
     int base = 0;
     for (size_t j = 0; j < sw.size(); j++) {
@@ -613,17 +621,81 @@ std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, in
     return jobs;
 }
 
-// Kernel arguments of a phase: small phases by value, large ones in a device table.
+// Kernel arguments of a phase: small phases by value, large ones in a device
+// table; for the TMA-staged kernel, a table of sweeps with their tensor maps.
 struct PhaseArgs {
     JobSet set{};
     Job *dtab = nullptr;
-    int njobs = 0, total = 0;
+    TmaJob *ttab = nullptr;
+    int njobs = 0, total = 0, cap = 0;
 };
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// map of one field's whole storage (apron included), box bx x by floats;
+// `f` points at the field's (k = 0, i = 0)
+bool field_map(CUtensorMap *m, const float *f, const FieldLayout &L, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)L.pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(f - L.origin()), dim, stride, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the TMA-staged kernel runs shape `base` for this context (order 8 only)
+bool tma_usable(ssx_ctx *c, int base) {
+    if (c->R != kMaxR || base < 0 || base >= kNumTileCfgs || !tma_shape_supported(base)) return false;
+    if (c->tma_cap[base] < 0) c->tma_cap[base] = tma_capacity(base);
+    return c->tma_cap[base] > 0 && tensor_map_encoder() != nullptr;
+}
+
 int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
-               Job **dtab) {
+               Job **dtab, TmaJob **ttab) {
     std::vector<Job> jobs = make_jobs(sw, cfg, quiet, &pa->total);
     pa->njobs = (int)jobs.size();
+    pa->dtab = nullptr;
+    pa->ttab = nullptr;
+    if (cfg >= kNumTileCfgs) {
+        const int base = cfg - kNumTileCfgs;
+        const int TX = kTileCfgs[base].tx, TZ = kTileCfgs[base].tz, R = kMaxR;
+        std::vector<TmaJob> tj(jobs.size());
+        for (size_t j = 0; j < jobs.size(); j++) {
+            memset(&tj[j], 0, sizeof(TmaJob));
+            tj[j].job = jobs[j];
+            const DGrid &G = *sw[j].G;
+            bool ok = true;
+            for (int b = 0; b < 2; b++) {
+                ok = ok && field_map(&tj[j].map[b], G.f[b][0], G.L, TX + 4 * R, TZ + 4 * R);
+                ok = ok && field_map(&tj[j].map[2 + b], G.f[b][1], G.L, TX + 2 * R, TZ);
+                ok = ok && field_map(&tj[j].map[4 + b], G.f[b][2], G.L, TX, TZ + 2 * R - 1);
+            }
+            ok = ok && (jobs[j].adj ? field_map(&tj[j].map[6], G.args.kap, G.L, TX + 4 * R, TZ + 4 * R)
+                                    : field_map(&tj[j].map[6], G.args.kap, G.L, TX, TZ));
+            if (!ok) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
+        }
+        if (!*ttab) CK(cudaMalloc(ttab, tj.size() * sizeof(TmaJob)));
+        CK(cudaMemcpyAsync(*ttab, tj.data(), tj.size() * sizeof(TmaJob), cudaMemcpyHostToDevice, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        pa->ttab = *ttab;
+        pa->cap = c->tma_cap[base];
+        return SSX_OK;
+    }
     if (jobs.size() <= (size_t)kMaxJobs) {
         memset(&pa->set, 0, sizeof pa->set);
         pa->set.njobs = pa->njobs;
@@ -662,7 +734,10 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
                     a.vz_in = w.G->f[0][2];
                     CK(launch_adj_init(a, w.nt, s));
                 }
-        if (pa.dtab)
+        if (pa.ttab)
+            CK(launch_multi_tma(pa.ttab, pa.njobs, pa.total, t, cfg - kNumTileCfgs, pa.cap, c->d_err,
+                                2000000000ull, s, true));
+        else if (pa.dtab)
             CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, true));
         else
             CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, true));
@@ -673,7 +748,8 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
 // time each admissible tile configuration on a short source-free run of the phase
 int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
     if (c->forced_cfg >= 0) {
-        *best_cfg = c->forced_cfg;
+        const int f = c->forced_cfg;
+        *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
         return SSX_OK;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -683,9 +759,11 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
     float best = 1e30f;
     int rc = SSX_OK;
     Job *tmp = nullptr;
-    for (int k = 0; k < kNumTileCfgs && rc == SSX_OK; k++) {
+    TmaJob *ttmp = nullptr;
+    for (int k = 0; k < 2 * kNumTileCfgs && rc == SSX_OK; k++) {
+        if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) continue;
         PhaseArgs pa;
-        rc = phase_args(c, sw, k, true, &pa, &tmp);
+        rc = phase_args(c, sw, k, true, &pa, &tmp, &ttmp);
         if (rc != SSX_OK) break;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -714,6 +792,7 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
         }
     }
     if (tmp) cudaFree(tmp);
+    if (ttmp) cudaFree(ttmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
@@ -737,8 +816,10 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     if (it == c->phases.end()) {
         ssx_ctx::PhaseInfo info;
         TRY(tune_phase(c, sw, &info.cfg));
+        TRY(check_sweeps_quiet(c));
         PhaseArgs pa;
-        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab));
+        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab, &info.ttab));
+        info.cap = pa.cap;
         info.jobs = pa.set;
         info.njobs = pa.njobs;
         info.total = pa.total;
@@ -749,6 +830,8 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     PhaseArgs pa;
     pa.set = info.jobs;
     pa.dtab = info.dtab;
+    pa.ttab = info.ttab;
+    pa.cap = info.cap;
     pa.njobs = info.njobs;
     pa.total = info.total;
     auto enqueue = [&](cudaStream_t s) -> int {
@@ -965,8 +1048,10 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
 }
 
 void drop_phases(ssx_ctx *c) {
-    for (auto &kv : c->phases)
+    for (auto &kv : c->phases) {
         if (kv.second.dtab) cudaFree(kv.second.dtab);
+        if (kv.second.ttab) cudaFree(kv.second.ttab);
+    }
     c->phases.clear();
 }
 
@@ -1323,6 +1408,7 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
     int rc = SSX_OK;
     auto init = [&]() -> int {
         for (auto &row : c->cap) row[0] = row[1] = -1;
+        for (int &v : c->tma_cap) v = -1;
         // SSX_GRAPHS=0: launch every step directly instead of replaying CUDA
         // graphs (profilers treat each graph replay as a rebuild)
         if (const char *e = std::getenv("SSX_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
@@ -1667,7 +1753,7 @@ int ssx_set_sweep_mode(ssx_ctx *c, int mode) {
 
 int ssx_set_tile_config(ssx_ctx *c, int cfg) {
     if (!c) return SSX_ERR_ARG;
-    if (cfg < -1 || cfg >= kNumTileCfgs) return fail(c, SSX_ERR_ARG, "unknown tile configuration");
+    if (cfg < -1 || cfg >= 2 * kNumTileCfgs) return fail(c, SSX_ERR_ARG, "unknown tile configuration");
     c->forced_cfg = cfg;
     reset_choices(c);
     return SSX_OK;

@@ -1,6 +1,7 @@
 // ssx_internal.cuh -- device-side data layout and kernel interfaces shared by
 // the CUDA translation units of libssx (not part of the public ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +106,14 @@ struct Job {
     float *f[2][3];          // ping-pong field triples (origin-offset pointers)
 };
 constexpr int kMaxJobs = 4;
+// A sweep of a phase run by the TMA-staged kernel (order 8): its arguments and
+// the tensor maps of its storage -- p, v_x, v_z of ping-pong buffers 0 and 1
+// (maps 0-1, 2-3, 4-5; boxes of the tile with halos 2k x 2k, k x 0, 0 x k)
+// and kappa (map 6: the tile, or the p box for a transposed sweep).
+struct alignas(128) TmaJob {
+    CUtensorMap map[7];
+    Job job;
+};
 // The sweeps of a phase, passed by value as the kernel parameter (constant
 // bank): a CTA reads its sweep's arguments without a global-memory round trip.
 struct JobSet {
@@ -147,6 +156,14 @@ cudaError_t launch_multi(const JobSet &jobs, int total_tiles, int t, int R, int 
 cudaError_t launch_multi_tab(const Job *jobs, int njobs, int total_tiles, int t, int R, int cfg,
                              cudaStream_t s, bool pdl);
 cudaError_t prepare_kernels();                     // dynamic shared-memory limits (once per device)
+// The TMA-staged phase kernel (stencil_tma.cu), order 8 only. Configuration
+// ids above kNumTileCfgs - 1 name it: id kNumTileCfgs + k runs tile shape k.
+bool tma_shape_supported(int cfg);                 // shape cfg has a TMA-staged kernel
+int tma_capacity(int cfg);                         // its co-resident CTAs (the launch's grid cap)
+cudaError_t prepare_tma_kernels();
+cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,
+                             int cap, int *err, unsigned long long timeout_ns, cudaStream_t s,
+                             bool pdl);
 
 // per-R instantiations (stencil_r<R>.cu)
 #define SSX_DECLARE_R(RR)                                                                       \

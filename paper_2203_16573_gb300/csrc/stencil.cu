@@ -123,7 +123,8 @@ cudaError_t prepare_kernels() {
     if ((e = stencil_prepare_r1()) != cudaSuccess) return e;
     if ((e = stencil_prepare_r2()) != cudaSuccess) return e;
     if ((e = stencil_prepare_r3()) != cudaSuccess) return e;
-    return stencil_prepare_r4();
+    if ((e = stencil_prepare_r4()) != cudaSuccess) return e;
+    return prepare_tma_kernels();
 }
 
 cudaError_t launch_adj_init(const AdjArgs &a, int nt, cudaStream_t s) {

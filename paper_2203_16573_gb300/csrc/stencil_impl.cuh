@@ -612,9 +612,45 @@ struct StripThread {
     }
 };
 
-template <int R, int TX, int TZ, int NT, bool SP, bool LN>
+// Operands of a strip step read straight from the field storage (the tile's
+// p, or q = C_p pbar, is staged into shared memory by stage_p). `own_*(j)`:
+// the thread's column at strip row j; `hvx(r, jj)`: v_x at tile row r and
+// v_x column jj (x = i0 - k + jj); `hvz(kk)`: v_z at row k0 - k + kk of the
+// thread's column.
+template <int R, int TX, int TZ, int NT, bool SP>
+struct GlobalIn {
+    const GridArgs &g;
+    const StepIO &io;
+    const int i0, k0, pitch;
+    const float *vxp, *vzp, *kp, *pp;
+    float (&spa)[TZ + 4 * R][TX + 4 * R];
+    __device__ __forceinline__ GlobalIn(const GridArgs &g_, const StepIO &io_, int i0_, int k0_,
+                                        int rs, int c, TileSmem<R, TX, TZ> &sm)
+        : g(g_), io(io_), i0(i0_), k0(k0_), pitch(g_.pitch), spa(sm.sp) {
+        const int o0 = (k0 + rs) * pitch + i0 + c;
+        vxp = io.vx_in + o0;
+        vzp = io.vz_in + o0;
+        kp = g.kap + o0;
+        pp = io.p_in + o0;
+    }
+    __device__ __forceinline__ float own_vx(int j) const { return ldf(vxp + j * pitch); }
+    __device__ __forceinline__ float own_vz(int j) const { return ldf(vzp + j * pitch); }
+    __device__ __forceinline__ float own_kap(int j) const { return __ldg(kp + j * pitch); }
+    __device__ __forceinline__ float own_p(int j) const { return ldf(pp + j * pitch); }
+    __device__ __forceinline__ float hvx(int r, int jj) const {
+        return ldf(io.vx_in + (k0 + r) * pitch + (i0 - R + jj));
+    }
+    __device__ __forceinline__ float hvz(int kk, int i) const {
+        return ldf(io.vz_in + (k0 - R + kk) * pitch + i);
+    }
+    template <bool PRE>
+    __device__ __forceinline__ void stage() { stage_p<R, TX, TZ, NT, SP, PRE>(g, io.p_in, i0, k0, spa); }
+    __device__ __forceinline__ float (&sp())[TZ + 4 * R][TX + 4 * R] { return spa; }
+};
+
+template <int R, int TX, int TZ, int NT, bool SP, bool LN, class In, class Work>
 __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, int i0, int k0,
-                                          TileSmem<R, TX, TZ> &sm) {
+                                          In &in, Work &sm) {
     using S = TileSmem<R, TX, TZ>;
     using Q = StripShape<R, TX, TZ, NT>;
     constexpr int H = S::H, L = Q::L, W = L + 2 * R - 1;
@@ -637,33 +673,29 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
         sxh = __ldg(g.sxh + min(i, NX - 1));
     }
-    {
-        const int o0 = (k0 + rs) * pitch + i;
 #pragma unroll
-        for (int j = 0; j < L; j++) {
-            const int k = k0 + rs + j;
-            rvx[j] = ldf(io.vx_in + o0 + j * pitch);
-            rvz[j] = ldf(io.vz_in + o0 + j * pitch);
-            rk[j] = __ldg(g.kap + o0 + j * pitch);
-            if (SP) {
-                szi[j] = __ldg(g.szi + min(k, NZ - 1));
-                szh[j] = __ldg(g.szh + min(k, NZ - 1));
-            }
+    for (int j = 0; j < L; j++) {
+        const int k = k0 + rs + j;
+        rvx[j] = in.own_vx(j);
+        rvz[j] = in.own_vz(j);
+        rk[j] = in.own_kap(j);
+        if (SP) {
+            szi[j] = __ldg(g.szi + min(k, NZ - 1));
+            szh[j] = __ldg(g.szh + min(k, NZ - 1));
         }
     }
 #pragma unroll
-    for (int q = 0; q < Q::NQX; q++)
-        rhx[q] = th.hx_jj[q] >= 0 ? ldf(io.vx_in + (k0 + th.hx_r[q]) * pitch + (i0 - R + th.hx_jj[q])) : 0.0f;
+    for (int q = 0; q < Q::NQX; q++) rhx[q] = th.hx_jj[q] >= 0 ? in.hvx(th.hx_r[q], th.hx_jj[q]) : 0.0f;
 #pragma unroll
-    for (int q = 0; q < Q::NQZ; q++)
-        rhz[q] = th.hz_kk[q] >= 0 ? ldf(io.vz_in + (k0 - R + th.hz_kk[q]) * pitch + i) : 0.0f;
-    stage_p<R, TX, TZ, NT, SP, false>(g, io.p_in, i0, k0, sm.sp);
+    for (int q = 0; q < Q::NQZ; q++) rhz[q] = th.hz_kk[q] >= 0 ? in.hvz(th.hz_kk[q], i) : 0.0f;
+    in.template stage<false>();
     __syncthreads();
+    float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
 
     // own strip: v_z from a window down the column, v_x from the row
     float pw[W];
 #pragma unroll
-    for (int w = 0; w < W; w++) pw[w] = sm.sp[rs - R + 1 + w + H][c + H];
+    for (int w = 0; w < W; w++) pw[w] = spa[rs - R + 1 + w + H][c + H];
 #pragma unroll
     for (int j = 0; j < L; j++) {
         const int r = rs + j, k = k0 + r;
@@ -697,7 +729,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         sm.svz[r + R][c] = vz;
 
         const bool okx = !SP || (colx && k < NZ);
-        const float *row = &sm.sp[r + H][c + H];
+        const float *row = &spa[r + H][c + H];
         d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
@@ -719,7 +751,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         const int jj = th.hx_jj[q], r = th.hx_r[q];
         if (jj < 0) continue;
         const int k = k0 + r, j = i0 - R + jj;
-        const float *row = &sm.sp[r + H][jj + R];
+        const float *row = &spa[r + H][jj + R];
         float d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
@@ -742,7 +774,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         float d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++)
-            d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+            d = fmaf(cc[m - 1], spa[kk + R + m][c + H] - spa[kk + R + 1 - m][c + H], d);
         const bool ok = !SP || (colp && k >= 0 && k < NZ - 1);
         float val, cvz = cv;
         if (SP) {
@@ -804,9 +836,9 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
 
 // The transposed step by column strips (same split of the work as fwd_strip;
 // per point the arithmetic of adj_tile_impl).
-template <int R, int TX, int TZ, int NT, bool SP, bool LN>
+template <int R, int TX, int TZ, int NT, bool SP, bool LN, class In, class Work>
 __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, int i0, int k0,
-                                          TileSmem<R, TX, TZ> &sm) {
+                                          In &in, Work &sm) {
     using S = TileSmem<R, TX, TZ>;
     using Q = StripShape<R, TX, TZ, NT>;
     constexpr int H = S::H, L = Q::L, W = L + 2 * R - 1;
@@ -828,33 +860,29 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
         sxh = __ldg(g.sxh + min(i, NX - 1));
     }
-    {
-        const int o0 = (k0 + rs) * pitch + i;
 #pragma unroll
-        for (int j = 0; j < L; j++) {
-            const int k = k0 + rs + j;
-            rvx[j] = ldf(io.vx_in + o0 + j * pitch);
-            rvz[j] = ldf(io.vz_in + o0 + j * pitch);
-            rp[j] = ldf(io.p_in + o0 + j * pitch);
-            if (SP) {
-                szi[j] = __ldg(g.szi + min(k, NZ - 1));
-                szh[j] = __ldg(g.szh + min(k, NZ - 1));
-            }
+    for (int j = 0; j < L; j++) {
+        const int k = k0 + rs + j;
+        rvx[j] = in.own_vx(j);
+        rvz[j] = in.own_vz(j);
+        rp[j] = in.own_p(j);
+        if (SP) {
+            szi[j] = __ldg(g.szi + min(k, NZ - 1));
+            szh[j] = __ldg(g.szh + min(k, NZ - 1));
         }
     }
 #pragma unroll
-    for (int q = 0; q < Q::NQX; q++)
-        rhx[q] = th.hx_jj[q] >= 0 ? ldf(io.vx_in + (k0 + th.hx_r[q]) * pitch + (i0 - R + th.hx_jj[q])) : 0.0f;
+    for (int q = 0; q < Q::NQX; q++) rhx[q] = th.hx_jj[q] >= 0 ? in.hvx(th.hx_r[q], th.hx_jj[q]) : 0.0f;
 #pragma unroll
-    for (int q = 0; q < Q::NQZ; q++)
-        rhz[q] = th.hz_kk[q] >= 0 ? ldf(io.vz_in + (k0 - R + th.hz_kk[q]) * pitch + i) : 0.0f;
+    for (int q = 0; q < Q::NQZ; q++) rhz[q] = th.hz_kk[q] >= 0 ? in.hvz(th.hz_kk[q], i) : 0.0f;
     // q = C_p pbar over tile + 2k halo
-    stage_p<R, TX, TZ, NT, SP, true>(g, io.p_in, i0, k0, sm.sp);
+    in.template stage<true>();
     __syncthreads();
+    float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
 
     float qw[W];
 #pragma unroll
-    for (int w = 0; w < W; w++) qw[w] = sm.sp[rs - R + 1 + w + H][c + H];
+    for (int w = 0; w < W; w++) qw[w] = spa[rs - R + 1 + w + H][c + H];
 #pragma unroll
     for (int j = 0; j < L; j++) {
         const int r = rs + j, k = k0 + r;
@@ -867,7 +895,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         }
         // vbar_x' = vbar_x + D+ q; C_vx vbar_x' kept for the p update
         const bool okx = !SP || (colx && k < NZ);
-        const float *row = &sm.sp[r + H][c + H];
+        const float *row = &spa[r + H][c + H];
         float d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
@@ -915,7 +943,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         const int jj = th.hx_jj[q], r = th.hx_r[q];
         if (jj < 0) continue;
         const int k = k0 + r, j = i0 - R + jj;
-        const float *row = &sm.sp[r + H][jj + R];
+        const float *row = &spa[r + H][jj + R];
         float d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
@@ -939,7 +967,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         float d = 0.0f;
 #pragma unroll
         for (int m = 1; m <= R; m++)
-            d = fmaf(cc[m - 1], sm.sp[kk + R + m][c + H] - sm.sp[kk + R + 1 - m][c + H], d);
+            d = fmaf(cc[m - 1], spa[kk + R + m][c + H] - spa[kk + R + 1 - m][c + H], d);
         const float vb = rhz[q] + d;
         float val;
         if (SP) {
@@ -991,13 +1019,17 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
                                          TileSmem<R, TX, TZ> &sm) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
+        using Q = StripShape<R, TX, TZ, NT>;
+        const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
         const bool ln = fwd_lines<R, TZ>(a, k0);
         if (in) {
-            if (ln) fwd_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, sm);
-            else fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, sm);
+            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
+            if (ln) fwd_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, gi, sm);
+            else fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
-            if (ln) fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, sm);
-            else fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            if (ln) fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
+            else fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
@@ -1010,19 +1042,28 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int
                                          TileSmem<R, TX, TZ> &sm) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
+        using Q = StripShape<R, TX, TZ, NT>;
+        const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
         const bool ln = adj_lines<TZ>(a, k0, io.n);
         if (in) {
-            if (ln) adj_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, sm);
-            else adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, sm);
+            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
+            if (ln) adj_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, gi, sm);
+            else adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
-            if (ln) adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, sm);
-            else adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            if (ln) adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
+            else adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
         else adj_tile_impl<R, TX, TZ, NT, true>(a, io, i0, k0, sm);
     }
 }
+
+// Resident CTAs per SM that the register budget is sized for: a step's tiles
+// should fit in one wave (152 SMs x 3 CTAs of 256 threads covers the 418
+// tiles of a 681 x 381 grid and its two slabs).
+constexpr int min_ctas(int nt) { return nt <= 256 ? 3 : nt <= 512 ? 2 : 1; }
 
 // Programmatic dependent launch: let the next step's grid become resident
 // while this one runs, and wait here until the previous step's grid has
@@ -1039,7 +1080,7 @@ __device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
 }
 
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_fwd(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, min_ctas(NT)) k_fwd(const FwdArgs a) {
     griddep_launch();
     griddep_wait();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
@@ -1047,7 +1088,7 @@ __global__ void __launch_bounds__(NT) k_fwd(const FwdArgs a) {
 }
 
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_adj(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, min_ctas(NT)) k_adj(const AdjArgs a) {
     griddep_launch();
     griddep_wait();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
@@ -1167,7 +1208,7 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
 // the kernel parameter; the CTA finds its sweep and steps its tile if that
 // sweep is active in this launch.
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_multi(const JobSet P, int t) {
+__global__ void __launch_bounds__(NT, min_ctas(NT)) k_multi(const JobSet P, int t) {
     griddep_launch();
     int j = 0;
 #pragma unroll
@@ -1198,7 +1239,7 @@ __global__ void __launch_bounds__(NT) k_multi(const JobSet P, int t) {
 // shots, each launch streams far more data than the look-up costs): binary
 // search of the CTA's sweep, its arguments copied to shared memory.
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
+__global__ void __launch_bounds__(NT, min_ctas(NT)) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
     griddep_launch();
     __shared__ Job sj;
     __shared__ int s_j;

@@ -1,0 +1,373 @@
+// stencil_tma.cu -- the phase kernel of spatial order 8 with its operands
+// moved by the tensor memory accelerator.
+//
+// The plain phase kernel (k_multi_tab) gives every tile its own CTA, and each
+// CTA loads its operands, waits for them, computes, and stores: on a grid far
+// larger than L2 the SMs then spend most of their time waiting for DRAM. This
+// kernel keeps a fixed set of CTAs resident (as many as fit on the GPU), each
+// walking the tiles of the launch with a stride of the grid size, and gives
+// each CTA two stages of shared memory: while it computes tile n from one
+// stage, four 2-D TMA copies (cp.async.bulk.tensor) are already filling the
+// other with the operands of tile n+1 -- the p (or pbar) box with its 2k halo,
+// the v_x box with its k-wide column halo, the v_z box with its row halo and
+// the kappa box -- and signal an mbarrier with their byte count. One thread
+// issues the copies; the address arithmetic of the loads disappears from the
+// other threads. The per-point arithmetic is that of the column-strip tiles
+// (fwd_strip / adj_strip, the same functions, fed from the stage), so results
+// are identical to every other tile configuration's.
+//
+// Every mbarrier wait is bounded (%globaltimer): past the limit the CTA
+// records error 2 in the context's error flag, waits (bounded again) for the
+// copies it still has in flight, and returns.
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "stencil_impl.cuh"
+
+namespace ssx {
+namespace {
+
+constexpr int kR = 4;   // spatial order 8: the TMA boxes' x offsets are 16-byte aligned
+
+// One pipeline stage: the operand boxes of one tile, laid out as TMA writes
+// them (row-major, no swizzle). x offsets: p and the transposed kappa box
+// start at i0 - 2k, v_x at i0 - k, v_z and the forward kappa box at i0.
+template <int TX, int TZ>
+struct TmaStage {
+    static constexpr int PH = TZ + 4 * kR, PW = TX + 4 * kR;
+    static constexpr int VXB = TX + 2 * kR, VZH = TZ + 2 * kR - 1;
+    alignas(128) float p[PH][PW];      // p (forward) or pbar (transposed); q = C_p pbar after staging
+    alignas(128) float vx[TZ][VXB];    // v_x, x = i0-k .. i0+TX+k-1
+    alignas(128) float vz[VZH][TX];    // v_z, rows k0-k .. k0+TZ+k-2
+    alignas(128) float k[PH][PW];      // kappa: [TZ][TX] at i0 (forward) or the p box (transposed)
+    static constexpr unsigned bytes(bool adj) {
+        return (unsigned)(sizeof(float) * (PH * PW + TZ * VXB + VZH * TX + (adj ? PH * PW : TZ * TX)));
+    }
+};
+
+template <int TX, int TZ>
+struct TmaSmem {
+    TmaStage<TX, TZ> st[2];
+    float svx[TZ][TX + 2 * kR - 1];    // C_v v_x of the step (as in TileSmem)
+    float svz[TZ + 2 * kR - 1][TX];
+    Job job;                           // the current tile's sweep
+    alignas(8) unsigned long long bar[2];
+};
+
+template <int TX, int TZ>
+constexpr size_t tma_smem_bytes() { return sizeof(TmaSmem<TX, TZ>) + 128; }   // + base alignment
+
+template <int TX, int TZ, int NT>
+constexpr bool tma_shape_ok() {
+    return StripShape<kR, TX, TZ, NT>::ok && tma_smem_bytes<TX, TZ>() <= 232448;
+}
+
+// ------------------------------------------------------------ PTX pieces --
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of the barrier to complete, at most timeout_ns
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          unsigned long long timeout_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try(bar, parity))
+        if (globaltimer() - t0 > timeout_ns) return false;
+    return true;
+}
+// 2-D tile copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// ------------------------------------------------------------- operands --
+// Strip operands read from a stage (same interface as GlobalIn).
+template <int TX, int TZ, int NT, bool SP>
+struct TmaIn {
+    using St = TmaStage<TX, TZ>;
+    St &st;
+    const GridArgs &g;
+    const int i0, k0, rs, c;
+    __device__ __forceinline__ TmaIn(St &st_, const GridArgs &g_, int i0_, int k0_, int rs_, int c_)
+        : st(st_), g(g_), i0(i0_), k0(k0_), rs(rs_), c(c_) {}
+    __device__ __forceinline__ float own_vx(int j) const { return st.vx[rs + j][c + kR]; }
+    __device__ __forceinline__ float own_vz(int j) const { return st.vz[rs + j + kR][c]; }
+    __device__ __forceinline__ float own_kap(int j) const {
+        return reinterpret_cast<const float(*)[TX]>(&st.k[0][0])[rs + j][c];
+    }
+    __device__ __forceinline__ float own_p(int j) const { return st.p[rs + j + 2 * kR][c + 2 * kR]; }
+    __device__ __forceinline__ float hvx(int r, int jj) const { return st.vx[r][jj]; }
+    __device__ __forceinline__ float hvz(int kk, int i) const { return st.vz[kk][i - i0]; }
+    // transposed step: q = C_p pbar in place over the box (0 outside the grid),
+    // the per-point arithmetic of stage_p; every thread has its own pbar first
+    template <bool PRE>
+    __device__ __forceinline__ void stage() {
+        if (!PRE) return;
+        __syncthreads();
+        constexpr int N = St::PH * St::PW;
+#pragma unroll
+        for (int q = 0; q < (N + NT - 1) / NT; q++) {
+            const int e = threadIdx.x + q * NT;
+            if (e < N) {
+                const int r = e / St::PW, x = e % St::PW;
+                const float pv = st.p[r][x], kv = st.k[r][x];
+                float v;
+                if (!SP) {
+                    v = __fmul_rn(kv, pv);
+                } else {
+                    const int k = k0 - 2 * kR + r, i = i0 - 2 * kR + x;
+                    const bool ok = k >= 0 && k < g.NZ && i >= 0 && i < g.NX;
+                    float A, B;
+                    damp(__ldg(g.sxi + (ok ? i : 0)) + __ldg(g.szi + (ok ? k : 0)), A, B);
+                    v = ok ? __fmul_rn(__fmul_rn(B, kv), pv) : 0.0f;
+                }
+                st.p[r][x] = v;
+            }
+        }
+    }
+    __device__ __forceinline__ float (&sp())[TZ + 4 * kR][TX + 4 * kR] { return st.p; }
+};
+
+template <int TX, int TZ, int NT>
+__device__ __forceinline__ void tma_tile(const Job &J, const StepIO &io, int i0, int k0,
+                                         TmaStage<TX, TZ> &st, TmaSmem<TX, TZ> &sm) {
+    using Q = StripShape<kR, TX, TZ, NT>;
+    const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
+    if (J.adj) {
+        const AdjArgs &a = J.aa;
+        const bool ln = adj_lines<TZ>(a, k0, io.n);
+        if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
+            TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
+            if (ln) adj_strip<kR, TX, TZ, NT, false, true>(a, io, i0, k0, ti, sm);
+            else adj_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+        } else {
+            TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
+            if (ln) adj_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
+            else adj_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+        }
+    } else {
+        const FwdArgs &a = J.fa;
+        const bool ln = fwd_lines<kR, TZ>(a, k0);
+        if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
+            TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
+            if (ln) fwd_strip<kR, TX, TZ, NT, false, true>(a, io, i0, k0, ti, sm);
+            else fwd_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+        } else {
+            TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
+            if (ln) fwd_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
+            else fwd_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+        }
+    }
+}
+
+// The next tile >= tile on this CTA's stride whose sweep steps in launch t
+// (total if none); *jo = its sweep. Every thread computes it (uniform).
+__device__ __forceinline__ int next_active(const TmaJob *__restrict__ jobs, int njobs, int total,
+                                           int t, int tile, int G, int *jo) {
+    while (tile < total) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {   // last sweep whose tile_base <= tile
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&jobs[mid].job.tile_base) <= tile) lo = mid; else hi = mid - 1;
+        }
+        const int st = t - __ldg(&jobs[lo].job.offset);
+        if (st >= 0 && st < __ldg(&jobs[lo].job.nt)) {
+            *jo = lo;
+            return tile;
+        }
+        const int end = __ldg(&jobs[lo].job.tile_base) + __ldg(&jobs[lo].job.tiles);
+        tile += (end - tile + G - 1) / G * G;   // skip the rest of an idle sweep
+    }
+    *jo = 0;
+    return total;
+}
+
+// thread 0: start the four copies of `tile` (sweep j) into stage `st`
+template <int TX, int TZ>
+__device__ __forceinline__ void issue(const TmaJob *__restrict__ jobs, int j, int tile, int t,
+                                      TmaStage<TX, TZ> &st, unsigned bar) {
+    const TmaJob &J = jobs[j];
+    const int tl = tile - __ldg(&J.job.tile_base), tx = __ldg(&J.job.tiles_x);
+    const int i0 = (tl % tx) * TX, k0 = (tl / tx) * TZ;
+    const int odd = (t - __ldg(&J.job.offset)) & 1;   // input buffer of this step
+    const bool adj = __ldg(&J.job.adj) != 0;
+    mbar_expect_tx(bar, TmaStage<TX, TZ>::bytes(adj));
+    const int x0 = GX + i0, y0 = GZ + k0;   // storage coordinates of the tile corner
+    tma_load_2d(&st.p[0][0], &J.map[odd], x0 - 2 * kR, y0 - 2 * kR, bar);
+    tma_load_2d(&st.vx[0][0], &J.map[2 + odd], x0 - kR, y0, bar);
+    tma_load_2d(&st.vz[0][0], &J.map[4 + odd], x0, y0 - kR, bar);
+    if (adj) tma_load_2d(&st.k[0][0], &J.map[6], x0 - 2 * kR, y0 - 2 * kR, bar);
+    else tma_load_2d(&st.k[0][0], &J.map[6], x0, y0, bar);
+}
+
+template <int TX, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
+    k_multi_tma(const TmaJob *__restrict__ jobs, int njobs, int total, int t, int *err,
+                unsigned long long timeout_ns) {
+    extern __shared__ __align__(16) unsigned char ssx_smem[];
+    TmaSmem<TX, TZ> &sm = *reinterpret_cast<TmaSmem<TX, TZ> *>(
+        (reinterpret_cast<uintptr_t>(ssx_smem) + 127) & ~uintptr_t(127));
+    griddep_launch();
+    const unsigned bar[2] = {smem_u32(&sm.bar[0]), smem_u32(&sm.bar[1])};
+    if (threadIdx.x == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    griddep_wait();   // the previous step's fields are complete
+
+    const int G = gridDim.x;
+    int j = 0, jn = 0;
+    int tile = next_active(jobs, njobs, total, t, blockIdx.x, G, &j);
+    if (threadIdx.x == 0 && tile < total) issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar[0]);
+    unsigned parity[2] = {0u, 0u};
+    int s = 0, cur_job = -1;
+    while (tile < total) {
+        const int nxt = next_active(jobs, njobs, total, t, tile + G, G, &jn);
+        // the other stage was last read before the previous tile's closing barrier
+        if (threadIdx.x == 0 && nxt < total) issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar[s ^ 1]);
+        if (j != cur_job) {   // the sweep's arguments into shared memory
+            const int *src = reinterpret_cast<const int *>(&jobs[j].job);
+            int *dst = reinterpret_cast<int *>(&sm.job);
+            for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+            cur_job = j;
+        }
+        const bool ok = mbar_wait(bar[s], parity[s], timeout_ns);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 2);
+            mbar_wait(bar[s], parity[s], timeout_ns);   // copies still in flight
+            if (nxt < total) mbar_wait(bar[s ^ 1], parity[s ^ 1], timeout_ns);
+            return;
+        }
+        parity[s] ^= 1u;
+        const Job &J = sm.job;
+        const int st = t - J.offset, tl = tile - J.tile_base;
+        const int odd = st & 1;
+        StepIO io;
+        io.p_in = io.vx_in = io.vz_in = nullptr;   // operands come from the stage
+        io.p_out = J.f[odd ^ 1][0];
+        io.vx_out = J.f[odd ^ 1][1];
+        io.vz_out = J.f[odd ^ 1][2];
+        io.n = J.adj ? J.nt - 1 - st : st;
+        tma_tile<TX, TZ, NT>(J, io, (tl % J.tiles_x) * TX, (tl / J.tiles_x) * TZ, sm.st[s], sm);
+        // the transposed step rewrote stage s (q = C_p pbar) with ordinary
+        // stores; order them before the copies that will refill it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();   // stage s, svx, svz and the job are free again
+        tile = nxt;
+        j = jn;
+        s ^= 1;
+    }
+}
+
+template <int TX, int TZ, int NT>
+struct TmaKernel {
+    static cudaError_t prepare() {
+        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return cudaSuccess;
+        else
+            return cudaFuncSetAttribute(k_multi_tma<TX, TZ, NT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tma_smem_bytes<TX, TZ>());
+    }
+    static int capacity() {
+        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return 0;
+        else {
+            int dev = 0, sms = 0, per_sm = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_tma<TX, TZ, NT>, NT,
+                                                              tma_smem_bytes<TX, TZ>()) != cudaSuccess)
+                return 0;
+            return per_sm * sms;
+        }
+    }
+    static cudaError_t launch(const TmaJob *jobs, int njobs, int total, int t, int *err,
+                              unsigned long long timeout_ns, int cap, cudaStream_t s, bool pdl) {
+        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return cudaErrorInvalidValue;
+        else {
+            if (cap <= 0) return cudaErrorInvalidValue;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(total < cap ? total : cap);
+            cfg.blockDim = dim3(NT);
+            cfg.dynamicSmemBytes = tma_smem_bytes<TX, TZ>();
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = pdl ? at : nullptr;
+            cfg.numAttrs = pdl ? 1 : 0;
+            return cudaLaunchKernelEx(&cfg, k_multi_tma<TX, TZ, NT>, jobs, njobs, total, t, err,
+                                      timeout_ns);
+        }
+    }
+};
+
+}  // namespace
+
+bool tma_shape_supported(int cfg) {
+    switch (cfg) {
+#define SSX_CASE_TMA_OK(id, TX, TZ, NT) case id: return tma_shape_ok<TX, TZ, NT>();
+        SSX_TILE_CONFIGS(SSX_CASE_TMA_OK)
+#undef SSX_CASE_TMA_OK
+    }
+    return false;
+}
+
+int tma_capacity(int cfg) {
+    switch (cfg) {
+#define SSX_CASE_TMA_CAP(id, TX, TZ, NT) case id: return TmaKernel<TX, TZ, NT>::capacity();
+        SSX_TILE_CONFIGS(SSX_CASE_TMA_CAP)
+#undef SSX_CASE_TMA_CAP
+    }
+    return 0;
+}
+
+cudaError_t prepare_tma_kernels() {
+    cudaError_t e = cudaSuccess;
+#define SSX_CASE_TMA_PREP(id, TX, TZ, NT) if (e == cudaSuccess) e = TmaKernel<TX, TZ, NT>::prepare();
+    SSX_TILE_CONFIGS(SSX_CASE_TMA_PREP)
+#undef SSX_CASE_TMA_PREP
+    return e;
+}
+
+cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,
+                             int cap, int *err, unsigned long long timeout_ns, cudaStream_t s,
+                             bool pdl) {
+    switch (cfg) {
+#define SSX_CASE_TMA_LAUNCH(id, TX, TZ, NT) \
+    case id: return TmaKernel<TX, TZ, NT>::launch(jobs, njobs, total_tiles, t, err, timeout_ns, cap, s, pdl);
+        SSX_TILE_CONFIGS(SSX_CASE_TMA_LAUNCH)
+#undef SSX_CASE_TMA_LAUNCH
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ssx

@@ -282,8 +282,9 @@ def test_persistent_wait_timeout_is_reported_and_context_survives(ssx, oracle):
 
 @pytest.mark.parametrize("order", [4, 8])
 def test_every_tile_configuration_gives_identical_results(ssx, order):
-    """All tile shapes / CTA sizes and both launch forms run the same per-point
-    arithmetic: bitwise-identical sweeps (ragged tiles on both grid edges)."""
+    """All tile shapes / CTA sizes, both launch forms and the TMA-staged phase
+    kernel (ids 8-15; order 8) run the same per-point arithmetic:
+    bitwise-identical sweeps (ragged tiles on both grid edges)."""
     spec = frac_spec(order, nt=120)
     ctx = ssx.Context.for_problem(spec, W.velocity(spec))
     x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 19))
@@ -291,7 +292,7 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     ref = None
     for mode in (ssx.SWEEP_STEP, ssx.SWEEP_PERSISTENT):
         ctx.set_sweep_mode(mode)
-        for cfg in range(8):
+        for cfg in range(16 if mode == ssx.SWEEP_STEP else 8):
             ctx.set_tile_config(cfg)
             got = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
                    ctx.weight_apply(ssx.W_D, y).clone())
