@@ -27,6 +27,8 @@
  * Environment: SSX_GRAPHS=0 makes contexts created afterwards launch every
  * time step directly instead of replaying captured CUDA graphs (same kernels
  * and results; for profilers, which rebuild a graph on every replay).
+ * SSX_LOG_TUNING=1 makes them print, to stderr, the time per step of every
+ * tile configuration the phase autotuner tries (a diagnostic).
  *
  * Discretisation (section "Synthetic models and simulation"): staggered grid,
  * order 2 in time and 2k in space, fields FP32 on the device; sampling by

@@ -134,6 +134,7 @@ struct ssx_ctx {
     int forced_cfg = -1;              // tile configuration fixed by the caller (-1: autotune)
     bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
     bool use_graphs = true;
+    bool log_tuning = false;          // SSX_LOG_TUNING=1: print the phase tuner's timings
     std::unordered_map<std::string, cudaGraphExec_t> graphs;
     std::unordered_map<std::string, long long> graph_nodes;
 
@@ -301,8 +302,10 @@ int check_sweeps_quiet(ssx_ctx *c) {
     if (*eh != 0) {
         const int code = *eh;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->s));
-        return fail(c, SSX_ERR_CUDA, code == 2 ? "a phase kernel's tensor-copy wait timed out"
-                                               : "a persistent sweep's neighbour wait timed out");
+        return fail(c, SSX_ERR_CUDA,
+                    code == 2   ? "a phase kernel's tensor-copy wait timed out"
+                    : code == 3 ? "the TMA phase kernel's shared memory is misaligned"
+                                : "a persistent sweep's neighbour wait timed out");
     }
     return SSX_OK;
 }
@@ -746,7 +749,7 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
 }
 
 // time each admissible tile configuration on a short source-free run of the phase
-int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
+int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *best_cfg) {
     if (c->forced_cfg >= 0) {
         const int f = c->forced_cfg;
         *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
@@ -786,6 +789,9 @@ int tune_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int *best_cfg) {
             if (rep > 0) ms = std::min(ms, t);
         }
         cudaGraphExecDestroy(exec);
+        if (c->log_tuning)
+            std::fprintf(stderr, "ssx tune: phase %s (%zu sweeps, %d tiles) config %d: %.3f us/step\n",
+                         name, sw.size(), pa.total, k, 1000.0 * ms / T);
         if (ms < best) {
             best = ms;
             *best_cfg = k;
@@ -815,7 +821,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     auto it = c->phases.find(key);
     if (it == c->phases.end()) {
         ssx_ctx::PhaseInfo info;
-        TRY(tune_phase(c, sw, &info.cfg));
+        TRY(tune_phase(c, name, sw, &info.cfg));
         TRY(check_sweeps_quiet(c));
         PhaseArgs pa;
         TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab, &info.ttab));
@@ -1412,6 +1418,7 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
         // SSX_GRAPHS=0: launch every step directly instead of replaying CUDA
         // graphs (profilers treat each graph replay as a rebuild)
         if (const char *e = std::getenv("SSX_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
+        if (const char *e = std::getenv("SSX_LOG_TUNING")) c->log_tuning = std::strcmp(e, "1") == 0;
         CK(prepare_kernels());
         CK(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));

@@ -1021,15 +1021,18 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
         const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
-        const bool ln = fwd_lines<R, TZ>(a, k0);
-        if (in) {
+        // three variants: interior tiles, sponge / edge tiles, and tiles a line
+        // meets (the general one, which reduces to the same arithmetic where a
+        // point is undamped and inside the grid)
+        if (fwd_lines<R, TZ>(a, k0)) {
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
+        } else if (in) {
             GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
-            if (ln) fwd_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, gi, sm);
-            else fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
+            fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
             GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
-            if (ln) fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
-            else fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
+            fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
@@ -1044,15 +1047,18 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
         const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
-        const bool ln = adj_lines<TZ>(a, k0, io.n);
-        if (in) {
+        // three variants: interior tiles, sponge / edge tiles, and tiles a line
+        // meets (the general one, which reduces to the same arithmetic where a
+        // point is undamped and inside the grid)
+        if (adj_lines<TZ>(a, k0, io.n)) {
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
+        } else if (in) {
             GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
-            if (ln) adj_strip<R, TX, TZ, NT, false, true>(a, io, i0, k0, gi, sm);
-            else adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
+            adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
             GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
-            if (ln) adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
-            else adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
+            adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);

@@ -18,7 +18,8 @@
 //
 // Every mbarrier wait is bounded (%globaltimer): past the limit the CTA
 // records error 2 in the context's error flag, waits (bounded again) for the
-// copies it still has in flight, and returns.
+// copies it still has in flight, and returns. A shared-memory window that is
+// not 128-byte aligned (never seen) records error 3 before any copy.
 #include <cuda.h>
 
 #include <cstdint>
@@ -56,7 +57,7 @@ struct TmaSmem {
 };
 
 template <int TX, int TZ>
-constexpr size_t tma_smem_bytes() { return sizeof(TmaSmem<TX, TZ>) + 128; }   // + base alignment
+constexpr size_t tma_smem_bytes() { return sizeof(TmaSmem<TX, TZ>); }
 
 template <int TX, int TZ, int NT>
 constexpr bool tma_shape_ok() {
@@ -162,27 +163,27 @@ __device__ __forceinline__ void tma_tile(const Job &J, const StepIO &io, int i0,
     const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
     if (J.adj) {
         const AdjArgs &a = J.aa;
-        const bool ln = adj_lines<TZ>(a, k0, io.n);
-        if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
+        if (adj_lines<TZ>(a, k0, io.n)) {
+            TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
+            adj_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
+        } else if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
             TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
-            if (ln) adj_strip<kR, TX, TZ, NT, false, true>(a, io, i0, k0, ti, sm);
-            else adj_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+            adj_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
         } else {
             TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
-            if (ln) adj_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
-            else adj_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+            adj_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
         }
     } else {
         const FwdArgs &a = J.fa;
-        const bool ln = fwd_lines<kR, TZ>(a, k0);
-        if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
+        if (fwd_lines<kR, TZ>(a, k0)) {
+            TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
+            fwd_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
+        } else if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
             TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
-            if (ln) fwd_strip<kR, TX, TZ, NT, false, true>(a, io, i0, k0, ti, sm);
-            else fwd_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+            fwd_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
         } else {
             TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
-            if (ln) fwd_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
-            else fwd_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+            fwd_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
         }
     }
 }
@@ -231,10 +232,16 @@ template <int TX, int TZ, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     k_multi_tma(const TmaJob *__restrict__ jobs, int njobs, int total, int t, int *err,
                 unsigned long long timeout_ns) {
-    extern __shared__ __align__(16) unsigned char ssx_smem[];
-    TmaSmem<TX, TZ> &sm = *reinterpret_cast<TmaSmem<TX, TZ> *>(
-        (reinterpret_cast<uintptr_t>(ssx_smem) + 127) & ~uintptr_t(127));
+    // a direct cast keeps the shared address space visible to the compiler
+    // (shared-memory instructions, not generic ones); the dynamic window of a
+    // kernel without static shared memory starts 128-byte aligned
+    extern __shared__ __align__(128) unsigned char ssx_tma_smem[];
+    TmaSmem<TX, TZ> &sm = *reinterpret_cast<TmaSmem<TX, TZ> *>(ssx_tma_smem);
     griddep_launch();
+    if (smem_u32(ssx_tma_smem) & 127u) {   // TMA destinations must be 128-byte aligned
+        if (threadIdx.x == 0) atomicExch(err, 3);
+        return;
+    }
     const unsigned bar[2] = {smem_u32(&sm.bar[0]), smem_u32(&sm.bar[1])};
     if (threadIdx.x == 0) {
         mbar_init(bar[0], 1);
