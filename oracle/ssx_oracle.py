@@ -251,12 +251,14 @@ class Slab:
 class Problem:
     """One source subproblem (eqn:esis) on a full grid with its two slabs."""
 
-    def __init__(self, spec, vel):
+    def __init__(self, spec, vel, v_max=None):
         self.spec = spec
         self.vel = np.asarray(vel, dtype=np.float64)
         s = spec
         self.nt = s.nt
-        self.g = Grid(self.vel, s.h, s.dt, s.order, s.n_sponge, s.rho)
+        # v_max sets the sponge strength; fixing it keeps the sponge constant
+        # when the model is perturbed (finite-difference checks)
+        self.g = Grid(self.vel, s.h, s.dt, s.order, s.n_sponge, s.rho, v_max=v_max)
         self.src = self.g.line(s.z_s, s.ix_line0, s.n_line)
         self.rec = self.g.line(s.z_r, s.ix_rec0, s.n_rec)
         # propagation direction from the source line towards the receivers;
@@ -414,3 +416,73 @@ def step(g: Grid, p, vx, vz):
         assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == (g.NZ, g.NX)
     lib().og_step_fwd(ctypes.byref(g._c), _ptr(p), _ptr(vx), _ptr(vz), None, None, None,
                       None, None, None)
+
+
+# --------------------------------------------------------------------------
+# Reduced objective of variable projection and its gradient in the velocity.
+# --------------------------------------------------------------------------
+def objective(prob: Problem, h, d, alpha):
+    """Phi(c, h) = ||S[c] h - d||^2 + alpha ||A h||^2, the objective of the
+    source subproblem eqn:esis (A of eqn:penop). Minimised over h it is the
+    reduced objective J(c) that variable projection optimises over c
+    (eqn:esi and the paragraph after eqn:esis)."""
+    r = prob.S(h) - d
+    return float(np.sum(r * r) + alpha * np.sum(prob.A(h) ** 2))
+
+
+def velocity_gradient(prob: Problem, h, d):
+    """d Phi / d v at fixed h: the gradient of ||S[v] h - d||^2 with respect
+    to the physical velocity model v[nz][nx] (the penalty does not depend on
+    v). At h = the minimiser of eqn:esis this is the gradient of the reduced
+    objective, because Phi is stationary in h there (variable projection).
+
+    Discrete adjoint state method (the paper's route to exact adjoints,
+    section "Synthetic models and simulation" and Appendix A), in the
+    discretisation's own steps:
+      1. forward sweep of S h, keeping p^n for n = 0 .. nt;
+      2. residual r = P p - d; the objective's derivative in the traces is 2 r;
+      3. reverse sweep of the transposed step on 2 r. After the transposed
+         sampling of sample n is added, the adjoint pressure pbar equals
+         dPhi/dp^{n+1};
+      4. p^{n+1} = A_p p^n + kappa (dt/h) B_p q^n with q^n independent of kappa
+         (q^n = -D- v^{n+1/2} + injected h), so dp^{n+1}/dkappa at a point is
+         (p^{n+1} - A_p p^n) / kappa there, and
+         dPhi/dkappa = sum_n pbar^{n+1} (p^{n+1} - A_p p^n) / kappa;
+      5. kappa = rho v_pad^2 on the padded grid, v_pad the model extended into
+         the sponge by edge replication: dPhi/dv sums 2 rho v_pad dPhi/dkappa
+         over the padded points that copy each model point.
+    The sponge profile (it depends on max v) is held fixed."""
+    g, src, rec, nt = prob.g, prob.src, prob.rec, prob.nt
+    L = lib()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    shape = (g.NZ, g.NX)
+    p, vx, vz = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    ps = [p.copy()]
+    y = np.zeros((nt, rec.n))
+    for n in range(nt):
+        row = np.ascontiguousarray(h[n])
+        yrow = np.zeros(rec.n)
+        L.og_step_fwd(ctypes.byref(g._c), _ptr(p), _ptr(vx), _ptr(vz), ctypes.byref(src),
+                      _ptr(row), None, ctypes.byref(rec), _ptr(yrow), None)
+        y[n] = yrow
+        ps.append(p.copy())
+    ybar = 2.0 * (y - d)
+    s_p = 0.5 * g.dt * (g.sz_i[:, None] + g.sx_i[None, :])
+    a_p = (1.0 - s_p) / (1.0 + s_p)
+    pb, vxb, vzb = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    q, wx, wz = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    gk = np.zeros(shape)
+    cols = rec.i0 + np.arange(rec.n)
+    for n in range(nt - 1, -1, -1):
+        pb[rec.kp, cols] += rec.wp0 * ybar[n]
+        if rec.wp1 != 0.0:
+            pb[rec.kp + 1, cols] += rec.wp1 * ybar[n]
+        gk += pb * (ps[n + 1] - a_p * ps[n]) / g.kappa
+        L.og_step_adj(ctypes.byref(g._c), _ptr(pb), _ptr(vxb), _ptr(vzb), ctypes.byref(src),
+                      None, None, _ptr(q), _ptr(wx), _ptr(wz))
+    gv_pad = gk * 2.0 * np.sqrt(g.rho * g.kappa)          # 2 rho v dPhi/dkappa
+    kk = np.clip(np.arange(g.NZ) - g.nsp, 0, g.nz - 1)
+    ii = np.clip(np.arange(g.NX) - g.nsp, 0, g.nx - 1)
+    out = np.zeros((g.nz, g.nx))
+    np.add.at(out, (kk[:, None], ii[None, :]), gv_pad)
+    return out
