@@ -195,6 +195,28 @@ int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, con
                     int maxit, double rtol, int mode, double *const *h_out_dev, double *hist,
                     int *iters, int *status);
 
+/* Gradient in the velocity model of Phi(c, h) = ||S[c] h - d||^2 +
+ * alpha ||A h||^2 at fixed h (eqn:esis). At h = the subproblem's minimiser
+ * (ssx_solve_source_subproblem with SSX_MODE_CG solves that Euclidean
+ * problem) Phi is stationary in h, so this is the gradient of the reduced
+ * objective that variable projection minimises over c (eqn:esi and the
+ * paragraph after eqn:esis). Computed by the discrete adjoint state method
+ * (the route the paper takes to exact adjoints): a forward sweep of S h
+ * keeping the wavefield before every checkpoint_every-th step, then the
+ * transposed sweep driven by 2 (S h - d), segment by segment backwards, each
+ * segment's forward pressures recomputed from its checkpoint, accumulating
+ * sum_n pbar^{n+1} (p^{n+1} - A_p p^n) / kappa in FP64 (kappa = rho c^2 enters
+ * only the pressure update), folded onto the physical model through
+ * kappa = rho c^2 and the sponge's edge replication. The sponge strength
+ * (set from max c) is held fixed. Results do not depend on checkpoint_every.
+ * h_dev [nt][n_line], d_dev [nt][n_rec] in (device); grad_dev [nz][nx]
+ * float64 out (device, dPhi/dc in the units of the model); objective_host
+ * (may be NULL) receives Phi. Device memory: (nt / checkpoint_every) x 3 +
+ * checkpoint_every + 11 padded fields, kept by the context for reuse.
+ * Errors: SSX_ERR_ARG for null pointers, checkpoint_every < 1 or alpha < 0. */
+int ssx_velocity_gradient(ssx_ctx *ctx, const double *h_dev, const double *d_dev, double alpha,
+                          int checkpoint_every, double *grad_dev, double *objective_host);
+
 /* A solve server with continuous batching. Requests (each a full source
  * subproblem: grid, geometry, model, data, alpha, stopping rule, output
  * buffer) queue in submission order and are admitted while their estimated
@@ -239,7 +261,10 @@ int ssx_point_source_data(ssx_ctx *ctx, double x_d, double z_d,
  * hanging; the context stays usable.
  * SSX_SWEEP_TEST_STALL (test hook, not a mode): in the next persistent sweep
  *   one tile never signals its neighbours, whose waits then run out after
- *   0.2 s, so the timeout path can be exercised without a fault. */
+ *   0.2 s; or, if the next multi-sweep phase runs on the TMA-staged kernel,
+ *   the copies of its first tile in its first step are never issued, so that
+ *   CTA's mbarrier wait runs out after 0.2 s. Either way the timeout path is
+ *   exercised without a fault, and the call returns SSX_ERR_CUDA. */
 enum { SSX_SWEEP_AUTO = 0, SSX_SWEEP_STEP = 1, SSX_SWEEP_PERSISTENT = 2, SSX_SWEEP_TEST_STALL = 3 };
 int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
 

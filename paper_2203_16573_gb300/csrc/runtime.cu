@@ -128,6 +128,12 @@ struct ssx_ctx {
     std::vector<double> hostD;
 
     int *d_err = nullptr;      // persistent-sweep wait timeout flag (device)
+    // velocity gradient: wavefield checkpoints and recompute slots (floats),
+    // accumulator and trace buffers (doubles); grown on demand, kept
+    float *gw = nullptr;
+    size_t gw_floats = 0;
+    double *gwd = nullptr;
+    size_t gw_doubles = 0;
     int sweep_mode = SSX_SWEEP_AUTO;
     int cap[kNumTileCfgs][2];         // co-resident CTAs of the persistent kernels (-1: unknown)
     int tma_cap[kNumTileCfgs];        // co-resident CTAs of the TMA-staged phase kernel (-1: unknown)
@@ -722,7 +728,7 @@ int phase_len(const std::vector<Sweep> &sw) {
 // the launches of a phase: transposed sweeps get their initial state (the
 // transposed sampling of their last data sample) just before their first step
 int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int T, int cfg,
-                  cudaStream_t s, bool with_init) {
+                  cudaStream_t s, bool with_init, bool stall = false) {
     for (int t = 0; t < T; t++) {
         if (with_init)
             for (const Sweep &w : sw)
@@ -739,7 +745,8 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
                 }
         if (pa.ttab)
             CK(launch_multi_tma(pa.ttab, pa.njobs, pa.total, t, cfg - kNumTileCfgs, pa.cap, c->d_err,
-                                2000000000ull, s, true));
+                                stall && t == 0 ? 200000000ull : 2000000000ull,
+                                stall && t == 0 ? 0 : -1, s, true));
         else if (pa.dtab)
             CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, true));
         else
@@ -840,6 +847,10 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     pa.cap = info.cap;
     pa.njobs = info.njobs;
     pa.total = info.total;
+    // test hook: the next TMA-staged phase withholds the copies of its first
+    // tile in its first launch (run uncached, so no graph keeps the stall)
+    const bool stall = c->stall_next && info.cfg >= kNumTileCfgs;
+    if (stall) c->stall_next = false;
     auto enqueue = [&](cudaStream_t s) -> int {
         for (const Sweep &w : sw) {
             const size_t E = w.G->L.elems();
@@ -851,7 +862,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
             if (w.fb) CK(cudaMemsetAsync(w.fb, 0, ns, s));
             CK(cudaMemsetAsync(w.G->mem + E, 0, 3 * E * sizeof(float), s));
         }
-        return enqueue_phase(c, sw, pa, info.T, info.cfg, s, true);
+        return enqueue_phase(c, sw, pa, info.T, info.cfg, s, true, stall);
     };
     double pts = 0;
     long long inits = 0;
@@ -860,6 +871,13 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         inits += w.adj ? 1 : 0;
     }
     c->st.sweeps += (long long)sw.size() - 1;   // run_cached counts one
+    if (stall) {
+        const bool g0 = c->use_graphs;
+        c->use_graphs = false;
+        const int rc = run_cached(c, "", info.T + inits, info.T, pts, enqueue);
+        c->use_graphs = g0;
+        return rc;
+    }
     return run_cached(c, "phase" + std::to_string(info.cfg) + key, info.T + inits, info.T, pts,
                       enqueue);
 }
@@ -1465,6 +1483,8 @@ int ssx_destroy(ssx_ctx *c) {
     if (c->partials) cudaFree(c->partials);
     if (c->sc_host) cudaFreeHost(c->sc_host);
     if (c->d_err) cudaFree(c->d_err);
+    if (c->gw) cudaFree(c->gw);
+    if (c->gwd) cudaFree(c->gwd);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->s) cudaStreamDestroy(c->s);
@@ -1573,6 +1593,164 @@ int ssx_forward(ssx_ctx *c, const double *h_dev, double *d_dev) {
         return check_sweeps(c);
     };
     return leave(c, body());
+}
+
+// ------------------------------------------------------- velocity gradient --
+// dPhi/dv of Phi = ||S[v] h - d||^2 + alpha ||A h||^2 at fixed h (the reduced
+// objective's gradient when h solves eqn:esis), by the discrete adjoint state
+// method with uniform checkpoints:
+//   1. forward sweep of S h from rest, saving the state (p, v_x, v_z) before
+//      every K-th step, and the traces y;
+//   2. ybar = 2 (y - d), Phi from the two norms;
+//   3. the transposed sweep driven by ybar, run backwards segment by segment:
+//      each segment's forward pressures p^{n0} .. p^{n1} are recomputed from
+//      its checkpoint (same kernels, so bit for bit the first sweep's), then
+//      its reverse steps run, each preceded by the accumulation of
+//      pbar^{n+1} (p^{n+1} - A_p p^n) / kappa~ into the FP64 gradient;
+//   4. the padded-grid sum is folded onto the physical model.
+static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, double alpha, int K,
+                             double *grad, double *objective) {
+    DGrid &G = c->full;
+    const int nt = c->gd.nt, R = c->R;
+    const int nrec = c->geom.n_rec, nl = c->geom.n_line;
+    TRY(select_config(c, G, false));
+    TRY(select_config(c, G, true));
+    const int cf = G.cfg[0], ca = G.cfg[1];   // step launches (never the persistent form)
+    const size_t E = G.L.elems(), org = G.L.origin();
+    const int ncp = (nt + K - 1) / K, seg = std::min(K, nt);
+    // floats: checkpoints [ncp][3][E] | p slots [seg+1][E] | v_x, v_z [2][2][E] | adjoint [2][3][E]
+    const size_t nf = ((size_t)ncp * 3 + (size_t)seg + 1 + 4 + 6) * E;
+    // doubles: accumulator [NZ][NX] | y, ybar [nt][nrec] | A h [nt][nl] | 2 scalars
+    const size_t NP = (size_t)G.L.NX * G.L.NZ;
+    const size_t nd = NP + 2 * (size_t)nt * nrec + (size_t)nt * nl + 2;
+    cudaStream_t s = c->s;
+    if (c->gw_floats < nf) {
+        if (c->gw) CK(cudaFree(c->gw));
+        c->gw = nullptr;
+        c->gw_floats = 0;
+        CK(cudaMalloc(&c->gw, nf * sizeof(float)));
+        c->gw_floats = nf;
+    }
+    if (c->gw_doubles < nd) {
+        if (c->gwd) CK(cudaFree(c->gwd));
+        c->gwd = nullptr;
+        c->gw_doubles = 0;
+        CK(cudaMalloc(&c->gwd, nd * sizeof(double)));
+        c->gw_doubles = nd;
+    }
+    float *cp = c->gw;                                    // checkpoints
+    float *slot = cp + (size_t)ncp * 3 * E;               // recomputed p^n
+    float *vbuf = slot + (size_t)(seg + 1) * E;           // [vx0 vz0 vx1 vz1]
+    float *abuf = vbuf + 4 * E;                           // adjoint [p vx vz] x 2
+    double *gacc = c->gwd, *y = gacc + NP, *ybar = y + (size_t)nt * nrec;
+    double *ah = ybar + (size_t)nt * nrec, *sc = ah + (size_t)nt * nl;
+    // every field array starts from zeros: the aprons are never written
+    CK(cudaMemsetAsync(slot, 0, (size_t)(seg + 1 + 4 + 6) * E * sizeof(float), s));
+    CK(cudaMemsetAsync(gacc, 0, NP * sizeof(double), s));
+    CK(cudaMemsetAsync(y, 0, (size_t)nt * nrec * sizeof(double), s));
+    CK(cudaMemsetAsync(G.mem + E, 0, 3 * E * sizeof(float), s));
+    auto F = [&](float *base) { return base + org; };   // origin-offset field pointer
+
+    // 1. forward sweep with checkpoints and traces
+    FwdArgs a{};
+    a.g = G.args;
+    a.src = c->src;
+    a.hsrc = h;
+    a.rec = c->rec;
+    a.outp = y;
+    for (int n = 0; n < nt; n++) {
+        const int bi = n & 1, bo = bi ^ 1;
+        if (n % K == 0)
+            for (int f = 0; f < 3; f++)
+                CK(cudaMemcpyAsync(cp + ((size_t)(n / K) * 3 + f) * E, G.f[bi][f] - org,
+                                   E * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        a.p_in = G.f[bi][0];
+        a.vx_in = G.f[bi][1];
+        a.vz_in = G.f[bi][2];
+        a.p_out = G.f[bo][0];
+        a.vx_out = G.f[bo][1];
+        a.vz_out = G.f[bo][2];
+        a.n = n;
+        CK(launch_fwd_step(a, R, cf, s, true));
+    }
+    // 2. residual and objective
+    CK(launch_residual2(ybar, y, d, (size_t)nt * nrec, s));
+    CK(launch_dot(ybar, ybar, (size_t)nt * nrec, c->partials, sc, s));
+    CK(launch_colscale(ah, h, c->dist, nt, nl, s));
+    CK(launch_dot(ah, ah, (size_t)nt * nl, c->partials, sc + 1, s));
+
+    // 3. transposed sweep of ybar, segments in reverse, with recompute
+    AdjArgs b{};
+    b.g = G.args;
+    b.src = c->src;
+    b.rec = c->rec;
+    b.yp = ybar;
+    float *A[2][3];
+    for (int q = 0; q < 2; q++)
+        for (int f = 0; f < 3; f++) A[q][f] = F(abuf + (size_t)(3 * q + f) * E);
+    b.p_in = A[0][0];
+    b.vx_in = A[0][1];
+    b.vz_in = A[0][2];
+    CK(launch_adj_init(b, nt, s));
+    FwdArgs r{};
+    r.g = G.args;
+    r.src = c->src;
+    r.hsrc = h;
+    r.rec = c->rec;
+    r.rec.n = 0;   // recompute: no sampling
+    for (int k = ncp - 1; k >= 0; k--) {
+        const int n0 = k * K, n1 = std::min(nt, n0 + K);
+        CK(cudaMemcpyAsync(slot, cp + (size_t)k * 3 * E, E * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(vbuf, cp + ((size_t)k * 3 + 1) * E, 2 * E * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s));
+        for (int n = n0; n < n1; n++) {
+            const int vi = (n - n0) & 1, vo = vi ^ 1;
+            r.p_in = F(slot + (size_t)(n - n0) * E);
+            r.p_out = F(slot + (size_t)(n - n0 + 1) * E);
+            r.vx_in = F(vbuf + (size_t)(2 * vi) * E);
+            r.vz_in = F(vbuf + (size_t)(2 * vi + 1) * E);
+            r.vx_out = F(vbuf + (size_t)(2 * vo) * E);
+            r.vz_out = F(vbuf + (size_t)(2 * vo + 1) * E);
+            r.n = n;
+            CK(launch_fwd_step(r, R, cf, s, true));
+        }
+        for (int n = n1 - 1; n >= n0; n--) {
+            const int t = nt - 1 - n, bi = t & 1, bo = bi ^ 1;
+            CK(launch_grad_accum(gacc, A[bi][0], F(slot + (size_t)(n + 1 - n0) * E),
+                                 F(slot + (size_t)(n - n0) * E), G.args, s));
+            b.p_in = A[bi][0];
+            b.vx_in = A[bi][1];
+            b.vz_in = A[bi][2];
+            b.p_out = A[bo][0];
+            b.vx_out = A[bo][1];
+            b.vz_out = A[bo][2];
+            b.n = n;
+            CK(launch_adj_step(b, R, ca, s, true));
+        }
+    }
+    // 4. onto the physical model: dPhi/dv = 2 rho v (dt/h) sum dPhi/dkappa~
+    CK(launch_grad_fold(grad, gacc, c->vel, c->gd.nx, c->gd.nz, c->gd.n_sponge, G.L.NX,
+                        2.0 * c->rho * c->gd.dt / c->gd.h, s));
+    c->st.kernel_launches += 4LL * nt + 6;
+    c->st.point_updates += 3LL * (long long)G.L.NX * G.L.NZ * nt;
+    if (objective) {
+        CK(cudaMemcpyAsync(c->sc_host, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *objective = 0.25 * c->sc_host[0] + alpha * c->sc_host[1];
+    }
+    return SSX_OK;
+}
+
+int ssx_velocity_gradient(ssx_ctx *c, const double *h_dev, const double *d_dev, double alpha,
+                          int checkpoint_every, double *grad_dev, double *objective) {
+    TRY(ready(c));
+    if (!h_dev || !d_dev || !grad_dev) return fail(c, SSX_ERR_ARG, "null argument");
+    if (checkpoint_every < 1) return fail(c, SSX_ERR_ARG, "checkpoint_every must be >= 1");
+    if (!(alpha >= 0.0)) return fail(c, SSX_ERR_ARG, "alpha must be >= 0");
+    TRY(enter(c));
+    int rc = velocity_gradient(c, h_dev, d_dev, alpha, checkpoint_every, grad_dev, objective);
+    if (rc == SSX_OK) rc = check_sweeps(c);
+    return leave(c, rc);
 }
 
 int ssx_adjoint(ssx_ctx *c, const double *d_dev, double *h_dev) {

@@ -161,9 +161,11 @@ cudaError_t prepare_kernels();                     // dynamic shared-memory limi
 bool tma_shape_supported(int cfg);                 // shape cfg has a TMA-staged kernel
 int tma_capacity(int cfg);                         // its co-resident CTAs (the launch's grid cap)
 cudaError_t prepare_tma_kernels();
+// stall_tile >= 0 (test hook): that tile's copies are never issued, so the
+// CTA's bounded wait runs out and reports error 2
 cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,
-                             int cap, int *err, unsigned long long timeout_ns, cudaStream_t s,
-                             bool pdl);
+                             int cap, int *err, unsigned long long timeout_ns, int stall_tile,
+                             cudaStream_t s, bool pdl);
 
 // per-R instantiations (stencil_r<R>.cu)
 #define SSX_DECLARE_R(RR)                                                                       \
@@ -200,6 +202,14 @@ cudaError_t launch_colscale(double *out, const double *in, const double *w, int 
                             cudaStream_t s);
 cudaError_t launch_colscale_add(double *q, const double *in, const double *w, double alpha,
                                 int nt, int nc, cudaStream_t s);
+
+// Velocity-gradient kernels (gradient.cu).
+cudaError_t launch_grad_accum(double *g, const float *mu, const float *pn1, const float *pn,
+                              const GridArgs &a, cudaStream_t s);
+cudaError_t launch_grad_fold(double *out, const double *g, const float *vel, int nx, int nz,
+                             int nsp, int NX, double scale, cudaStream_t s);
+cudaError_t launch_residual2(double *ybar, const double *y, const double *d, size_t n,
+                             cudaStream_t s);
 
 // Device scalar slots used by the PCG kernels.
 enum { SC_GR = 0, SC_PQ, SC_ALPHA, SC_RR, SC_GRNEW, SC_BETA, SC_FLAG, SC_COUNT };

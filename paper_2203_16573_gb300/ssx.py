@@ -30,7 +30,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_get_stats", "ssx_reset_stats", "ssx_forward_noalloc", "ssx_set_sweep_mode",
            "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
-           "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error"]
+           "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
+           "ssx_velocity_gradient"]
 
 
 class SSXError(RuntimeError):
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_server_poll": ([vp, i, P(i), P(i), P(i), P(d), P(d)], i),
         "ssx_server_destroy": ([vp], i),
         "ssx_server_last_error": ([vp], ctypes.c_char_p),
+        "ssx_velocity_gradient": ([vp, vp, vp, d, i, vp, P(d)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -229,6 +231,20 @@ class Context:
         self._check(self._lib.ssx_normal_apply(self._c, mode, float(alpha), self._line(p, "p"),
                                                self._line(out, "q")))
         return out
+
+    def velocity_gradient(self, h, d, alpha=0.0, checkpoint_every=50, out=None):
+        """dPhi/dc of Phi = ||S[c] h - d||^2 + alpha ||A h||^2 at fixed h
+        (ssx_velocity_gradient): returns (gradient [nz][nx] float64, Phi)."""
+        out = (torch.empty((self.nz, self.nx), dtype=torch.float64, device=self.device)
+               if out is None else out)
+        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != (self.nz, self.nx):
+            raise TypeError("gradient buffer must be contiguous float64 [nz][nx]")
+        obj = ctypes.c_double(0.0)
+        self._check(self._lib.ssx_velocity_gradient(self._c, self._line(h, "h"), self._rec(d, "d"),
+                                                    float(alpha), int(checkpoint_every),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    ctypes.byref(obj)))
+        return out, obj.value
 
     def solve(self, d, alpha, maxit, rtol, mode=MODE_PCG, out=None, allow_not_converged=True):
         """Algorithm 1. Returns (h, residual history (numpy), iterations, status)."""

@@ -59,7 +59,7 @@ class Spec:
     maxit: int         # PCG iteration cap
     rtol: float        # relative residual target
     dz_datum: float = 0.1   # thin-slab datum distance, km (the paper's 100 m)
-    model: str = "homogeneous"  # or "gradient_lens"
+    model: str = "homogeneous"  # "gradient", "gradient_lens", "gradient_perturbed"
     v0: float = 1.5
 
     @property
@@ -106,6 +106,49 @@ def c3_shots(n_shots: int = 64, nt: int = 5000) -> list[Spec]:
     return out
 
 
+def c4_shots(n_shots: int = 32, nt: int = 4000) -> list[Spec]:
+    """Gradient workload: 1001 x 401 grid (8 km x 3.2 km, h = 8 m), order 8,
+    40-point sponge, dt = 0.6 ms, 4000 steps. Shot i: a 15 Hz Ricker point
+    source at x_i = (i + 1/2) 8 km / n at 40 m depth, its extended source on
+    the line z = 40 m within 1 km of x_i (clipped to the model), 1001
+    receivers on the line z = 3.0 km; alpha = 1e-2. The data come from the
+    "true" model (model "gradient_perturbed": the linear gradient 1.5 -> 3.0
+    km/s times 1 + a smooth random perturbation of at most 10 %, correlation
+    length 200 m); the gradient is taken at the unperturbed linear gradient
+    (model "gradient", see ``background``)."""
+    out = []
+    for i in range(n_shots):
+        xs = (i + 0.5) * 8.0 / n_shots
+        ixs = int(round(xs / 0.008))
+        xs = ixs * 0.008
+        i0, i1 = max(0, ixs - 125), min(1000, ixs + 125)
+        out.append(Spec(name=f"c4_shot{i:02d}_1001x401_o8_nt{nt}", nx=1001, nz=401, h=0.008,
+                        dt=0.6e-3, nt=nt, order=8, n_sponge=40, rho=1.0, z_s=0.04,
+                        ix_line0=i0, n_line=i1 - i0 + 1, z_r=3.0, ix_rec0=0, n_rec=1001,
+                        x_s=xs, x_d=xs, z_d=0.04, f_peak=15.0, alpha=1e-2, maxit=10,
+                        rtol=1e-3, model="gradient_perturbed"))
+    return out
+
+
+def background(spec: Spec) -> Spec:
+    """The same workload on the unperturbed linear-gradient model."""
+    return dataclasses.replace(spec, model="gradient")
+
+
+def smooth_perturbation(nz: int, nx: int, h: float, corr: float, amp: float,
+                        seed: int) -> np.ndarray:
+    """Seeded smooth random field [nz][nx]: white noise blurred by a Gaussian
+    of standard deviation corr (km), scaled so that max |field| = amp."""
+    g = np.random.default_rng(SEED + seed).standard_normal((nz, nx))
+    w = max(1, int(round(corr / h)))
+    k = np.arange(-3 * w, 3 * w + 1)
+    ker = np.exp(-0.5 * (k / w) ** 2)
+    ker /= ker.sum()
+    g = np.apply_along_axis(lambda s: np.convolve(np.pad(s, 3 * w, mode="wrap"), ker, "valid"), 0, g)
+    g = np.apply_along_axis(lambda s: np.convolve(np.pad(s, 3 * w, mode="wrap"), ker, "valid"), 1, g)
+    return amp * g / np.max(np.abs(g))
+
+
 def small(order: int = 4, nt: int = 400, model: str = "gradient_lens",
           n_sponge: int = 12) -> Spec:
     """A reduced c2-like case (same structure, ~1/5 linear size) that the
@@ -137,6 +180,11 @@ def velocity(spec: Spec) -> np.ndarray:
         zmax = (spec.nz - 1) * spec.h
         zz = np.repeat(z[:, None], spec.nx, axis=1)
         return spec.v0 * (1.0 + zz / zmax)
+    if spec.model == "gradient_perturbed":
+        zmax = (spec.nz - 1) * spec.h
+        zz = np.repeat(z[:, None], spec.nx, axis=1)
+        pert = smooth_perturbation(spec.nz, spec.nx, spec.h, 0.2, 0.1, seed=404)
+        return spec.v0 * (1.0 + zz / zmax) * (1.0 + pert)
     if spec.model == "gradient_lens":
         # linear gradient v0 -> 2 v0 from top to bottom, times a -20 %
         # Gaussian lens at the centre with sigma = depth / 10 (300 m for 3 km)

@@ -1,0 +1,143 @@
+"""GPU parity of the velocity gradient (ssx_velocity_gradient) with the FP64
+oracle, its independence of the checkpoint interval, and, at the full size
+of the gradient workload (1001 x 401, 4000 steps), agreement with central
+differences of the GPU's own objective."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_16573_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 2e-3    # relative L2, FP32 wavefields against the FP64 oracle
+
+
+@pytest.fixture(scope="module")
+def ssx():
+    from paper_2203_16573_gb300 import build, ssx as mod
+    build.build()
+    return mod
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def frac_spec(order, nt):
+    return dataclasses.replace(W.small(order=order, nt=nt), z_s=0.5537, z_r=0.0471)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_gradient_matches_oracle(ssx, oracle, order):
+    spec = frac_spec(order, 240)
+    vel = W.velocity(spec)
+    ctx = ssx.Context.for_problem(spec, vel)
+    P = oracle.Problem(spec, vel)
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 31)
+    d = 0.5 * P.S(h) + 0.1 * W.smooth_random_gather(spec.nt, spec.n_rec, 32)
+    alpha = 0.05
+    g, phi = ctx.velocity_gradient(dev(h), dev(d), alpha, checkpoint_every=50)
+    g_ref = oracle.velocity_gradient(P, h, d)
+    phi_ref = oracle.objective(P, h, d, alpha)
+    assert g.shape == (spec.nz, spec.nx)
+    assert rel(g, g_ref) <= GTOL
+    assert abs(phi - phi_ref) / phi_ref <= 1e-4
+
+
+def test_checkpoint_interval_does_not_change_the_result(ssx):
+    """Recomputed segments are the first sweep's bits, and every point's sum
+    runs over the same steps in the same order, whatever the interval."""
+    spec = frac_spec(8, 130)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    h = dev(W.smooth_random_gather(spec.nt, spec.n_line, 33))
+    d = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 34))
+    ref, phi_ref = ctx.velocity_gradient(h, d, 0.0, checkpoint_every=1)
+    ref = ref.clone()
+    for K in (7, 50, 129, 130, 1000):
+        g, phi = ctx.velocity_gradient(h, d, 0.0, checkpoint_every=K)
+        assert torch.equal(g, ref), K
+        assert phi == phi_ref
+
+
+def test_gradient_argument_errors(ssx):
+    spec = frac_spec(4, 20)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    h = dev(np.zeros((spec.nt, spec.n_line)))
+    d = dev(np.zeros((spec.nt, spec.n_rec)))
+    for K, alpha in ((0, 0.0), (10, -1.0)):
+        with pytest.raises(ssx.SSXError) as e:
+            ctx.velocity_gradient(h, d, alpha, checkpoint_every=K)
+        assert e.value.code == 1
+    g, phi = ctx.velocity_gradient(h, d, 0.0, checkpoint_every=5)   # zero data: zero gradient
+    assert phi == 0.0 and float(g.abs().max()) == 0.0
+
+
+def test_full_size_gradient_matches_central_differences(ssx):
+    """1001 x 401, order 8, 4000 steps, checkpoints every 50 steps (the
+    gradient workload's shot 16, on its background model): the directional
+    derivative along a smooth perturbation that leaves max v (and so the
+    sponge) unchanged equals central differences of the GPU objective."""
+    spec = W.background(W.c4_shots(32)[16])
+    vel = W.velocity(spec).astype(np.float32)
+    ctx = ssx.Context.for_problem(spec, vel)
+    true_spec = W.c4_shots(32)[16]
+    tctx = ssx.Context.for_problem(true_spec, W.velocity(true_spec))
+    wav = torch.as_tensor(W.ricker(spec), device="cuda")
+    d = tctx.point_source_data(spec.x_d, spec.z_d, wav)
+    tctx.close()
+    h = ctx.time_reversal_inverse(d)     # any fixed source will do
+    g, phi = ctx.velocity_gradient(h, d, 0.0, checkpoint_every=50)
+    dv = W.smooth_perturbation(spec.nz, spec.nx, spec.h, 0.2, 1.0, seed=77)
+    dv[vel > 0.97 * vel.max()] = 0.0
+    an = float((g.cpu().numpy() * dv).sum())
+    eps = 5e-3
+    vals = []
+    for sgn in (1.0, -1.0):
+        ctx.set_velocity_model(torch.as_tensor((vel + sgn * eps * dv).astype(np.float32), device="cuda"),
+                               spec.rho)
+        y = ctx.forward(h)
+        vals.append(float(((y - d) ** 2).sum()))
+    fd = (vals[0] - vals[1]) / (2 * eps)
+    assert abs(fd - an) / abs(an) < 2e-2, (fd, an)
+
+
+def test_autograd_reduced_objective_matches_central_differences(ssx):
+    """torch.autograd through the reduced objective J(c) = min_h Phi(c, h):
+    backward gives dPhi/dc at the inner CG solution, which equals central
+    differences of J itself (inner problem re-solved at each perturbed
+    model) because Phi is stationary in h at the minimiser."""
+    from paper_2203_16573_gb300.autograd import reduced_objective
+    # receivers 200 m above a one-point source line: 300 unknowns, so CG
+    # reaches the inner minimiser, where the identity holds
+    base = W.small(order=4, nt=300, model="gradient")
+    ixs = int(round(base.x_s / base.h))
+    spec = dataclasses.replace(base, alpha=0.05, z_r=0.35, ix_line0=ixs, n_line=1,
+                               x_s=ixs * base.h, x_d=ixs * base.h)
+    v0 = W.velocity(spec)
+    ctx = ssx.Context.for_problem(spec, W.velocity(dataclasses.replace(spec, model="gradient_lens")))
+    wav = torch.as_tensor(W.ricker(spec), device="cuda")
+    d = ctx.point_source_data(spec.x_d, spec.z_d, wav)       # data from the lens model
+    kw = dict(rho=spec.rho, alpha=spec.alpha, maxit=900, rtol=1e-10, checkpoint_every=40)
+    vel = torch.as_tensor(v0, dtype=torch.float64, device="cuda").requires_grad_(True)
+    J = reduced_objective(vel, d, ctx, **kw)
+    J.backward()
+    g = vel.grad.detach().cpu().numpy()
+    dv = W.smooth_perturbation(spec.nz, spec.nx, spec.h, 0.1, 1.0, seed=78)
+    dv[v0 > 0.97 * v0.max()] = 0.0                            # sponge strength unchanged
+    an = float((g * dv).sum())
+    eps = 2e-3
+    Jp = float(reduced_objective(torch.as_tensor(v0 + eps * dv, device="cuda"), d, ctx, **kw))
+    Jm = float(reduced_objective(torch.as_tensor(v0 - eps * dv, device="cuda"), d, ctx, **kw))
+    fd = (Jp - Jm) / (2 * eps)
+    assert float(J.detach()) > 0.0 and an != 0.0
+    ctx.set_velocity_model(torch.as_tensor(v0, dtype=torch.float32, device="cuda"), spec.rho)
+    _, hist, iters, _ = ctx.solve(d, spec.alpha, 900, 1e-10, ssx.MODE_CG)
+    assert abs(fd - an) / abs(an) < 2e-2, (fd, an, iters, hist[-1] / hist[0])
