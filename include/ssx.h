@@ -270,7 +270,7 @@ int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
 
 /* Tile configuration of the step kernels: -1 (default) lets the library time
  * every configuration on each grid's first sweep in each direction and keep
- * the fastest; 0..7 fixes one (tile 64x16/256 threads, 64x16/512, 64x16/1024,
+ * the fastest; 0..7 fixes one (tile 64x16/256 threads, 64x16/512, 32x32/256,
  * 64x32/512, 64x32/1024, 128x16/512, 128x32/1024, 32x16/256); 8 + k fixes
  * shape k with the multi-sweep steps run by the TMA-staged kernel (operand
  * tiles copied by the tensor memory accelerator into a two-stage shared-memory

@@ -128,7 +128,7 @@ struct JobSet {
 #define SSX_TILE_CONFIGS(X) \
     X(0, 64, 16, 256)       \
     X(1, 64, 16, 512)       \
-    X(2, 64, 16, 1024)      \
+    X(2, 32, 32, 256)       \
     X(3, 64, 32, 512)       \
     X(4, 64, 32, 1024)      \
     X(5, 128, 16, 512)      \

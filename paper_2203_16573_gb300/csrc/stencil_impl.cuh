@@ -54,6 +54,10 @@ __device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
 // neighbour CTA rewrote these lines during the previous step, and L1 is not
 // coherent across SMs.
 __device__ __forceinline__ float ldf(const float *p) { return __ldcg(p); }
+// Field stores, explicitly global: where a kernel reads the field pointers
+// from shared memory the compiler cannot tell their space and would emit
+// generic stores.
+__device__ __forceinline__ void st_out(float *p, float v) { __stcg(p, v); }
 
 template <int R, int TX, int TZ>
 struct TileSmem {
@@ -719,7 +723,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
                 vz = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], vz);
         }
         if (SP) vz = okz ? vz : 0.0f;
-        if (okz) io.vz_out[k * pitch + i] = vz;
+        if (okz) st_out(io.vz_out + k * pitch + i, vz);
         if (LN && a.outv && okz) {   // P v_z trace
             const float w = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
             const int jr = i - a.rec.i0;
@@ -742,7 +746,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         } else {
             vx = fmaf(-cv, d, rvx[j]);
         }
-        if (okx) io.vx_out[k * pitch + i] = vx;
+        if (okx) st_out(io.vx_out + k * pitch + i, vx);
         sm.svx[r][c + R] = vx;
     }
     // halo v (not written out)
@@ -824,7 +828,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
             if (w != 0.0f && js >= 0 && js < a.src.n)
                 val = fmaf(cp * (w * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + js], val);
         }
-        if (okp) io.p_out[k * pitch + i] = val;
+        if (okp) st_out(io.p_out + k * pitch + i, val);
         if (LN && a.outp && okp) {   // P p trace
             const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
             const int jr = i - a.rec.i0;
@@ -910,7 +914,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
             vx = cv * vbx;
             ox = vbx;
         }
-        if (okx) io.vx_out[k * pitch + i] = ox;
+        if (okx) st_out(io.vx_out + k * pitch + i, ox);
         sm.svx[r][c + R] = vx;
         // vbar_z' likewise, from the window down the column
         const bool okz = !SP || (colp && k < NZ - 1);
@@ -934,7 +938,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
             if (wy_ != 0.0f && jr >= 0 && jr < a.rec.n)
                 out = fmaf(wy_, (float)a.yv[(size_t)(n - 1) * a.rec.n + jr], out);
         }
-        if (okz) io.vz_out[k * pitch + i] = out;
+        if (okz) st_out(io.vz_out + k * pitch + i, out);
         sm.svz[r + R][c] = okz ? vz : 0.0f;
     }
     // halo vbar' (not written out)
@@ -1010,7 +1014,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
             if (w != 0.0f && jr >= 0 && jr < a.rec.n)
                 out = fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jr], out);
         }
-        if (okp) io.p_out[k * pitch + i] = out;
+        if (okp) st_out(io.p_out + k * pitch + i, out);
     }
 }
 
@@ -1069,7 +1073,12 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int
 // Resident CTAs per SM that the register budget is sized for: a step's tiles
 // should fit in one wave (152 SMs x 3 CTAs of 256 threads covers the 418
 // tiles of a 681 x 381 grid and its two slabs).
-constexpr int min_ctas(int nt) { return nt <= 256 ? 3 : nt <= 512 ? 2 : 1; }
+// Strips of 8 or more rows need more registers: two CTAs of 256 threads.
+constexpr int min_ctas(int nt, int rows_per_thread = 4) {
+    return nt <= 256 ? (rows_per_thread >= 8 ? 2 : 3) : nt <= 512 ? 2 : 1;
+}
+template <int TX, int TZ, int NT>
+constexpr int tile_min_ctas() { return min_ctas(NT, NT >= TX ? TZ / (NT / TX) : 1); }
 
 // Programmatic dependent launch: let the next step's grid become resident
 // while this one runs, and wait here until the previous step's grid has
@@ -1086,7 +1095,7 @@ __device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
 }
 
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(NT)) k_fwd(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_fwd(const FwdArgs a) {
     griddep_launch();
     griddep_wait();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
@@ -1094,7 +1103,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) k_fwd(const FwdArgs a) {
 }
 
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(NT)) k_adj(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_adj(const AdjArgs a) {
     griddep_launch();
     griddep_wait();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
@@ -1214,7 +1223,7 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
 // the kernel parameter; the CTA finds its sweep and steps its tile if that
 // sweep is active in this launch.
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(NT)) k_multi(const JobSet P, int t) {
+__global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(const JobSet P, int t) {
     griddep_launch();
     int j = 0;
 #pragma unroll
@@ -1245,7 +1254,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) k_multi(const JobSet P, int 
 // shots, each launch streams far more data than the look-up costs): binary
 // search of the CTA's sweep, its arguments copied to shared memory.
 template <int R, int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(NT)) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
+__global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
     griddep_launch();
     __shared__ Job sj;
     __shared__ int s_j;

@@ -229,9 +229,9 @@ __device__ __forceinline__ void issue(const TmaJob *__restrict__ jobs, int j, in
 }
 
 template <int TX, int TZ, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
+__global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() : 1))
     k_multi_tma(const TmaJob *__restrict__ jobs, int njobs, int total, int t, int *err,
-                unsigned long long timeout_ns) {
+                unsigned long long timeout_ns, int stall_tile) {
     // a direct cast keeps the shared address space visible to the compiler
     // (shared-memory instructions, not generic ones); the dynamic window of a
     // kernel without static shared memory starts 128-byte aligned
@@ -254,13 +254,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
     const int G = gridDim.x;
     int j = 0, jn = 0;
     int tile = next_active(jobs, njobs, total, t, blockIdx.x, G, &j);
-    if (threadIdx.x == 0 && tile < total) issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar[0]);
+    // stall_tile (test hook, normally -1): that tile's copies are never issued,
+    // so its wait must run out
+    if (threadIdx.x == 0 && tile < total && tile != stall_tile)
+        issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar[0]);
     unsigned parity[2] = {0u, 0u};
     int s = 0, cur_job = -1;
     while (tile < total) {
         const int nxt = next_active(jobs, njobs, total, t, tile + G, G, &jn);
         // the other stage was last read before the previous tile's closing barrier
-        if (threadIdx.x == 0 && nxt < total) issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar[s ^ 1]);
+        if (threadIdx.x == 0 && nxt < total && nxt != stall_tile)
+            issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar[s ^ 1]);
         if (j != cur_job) {   // the sweep's arguments into shared memory
             const int *src = reinterpret_cast<const int *>(&jobs[j].job);
             int *dst = reinterpret_cast<int *>(&sm.job);
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1)
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, 2);
             mbar_wait(bar[s], parity[s], timeout_ns);   // copies still in flight
-            if (nxt < total) mbar_wait(bar[s ^ 1], parity[s ^ 1], timeout_ns);
+            if (nxt < total && nxt != stall_tile) mbar_wait(bar[s ^ 1], parity[s ^ 1], timeout_ns);
             return;
         }
         parity[s] ^= 1u;
@@ -317,7 +321,8 @@ struct TmaKernel {
         }
     }
     static cudaError_t launch(const TmaJob *jobs, int njobs, int total, int t, int *err,
-                              unsigned long long timeout_ns, int cap, cudaStream_t s, bool pdl) {
+                              unsigned long long timeout_ns, int stall_tile, int cap,
+                              cudaStream_t s, bool pdl) {
         if constexpr (!tma_shape_ok<TX, TZ, NT>()) return cudaErrorInvalidValue;
         else {
             if (cap <= 0) return cudaErrorInvalidValue;
@@ -332,7 +337,7 @@ struct TmaKernel {
             cfg.attrs = pdl ? at : nullptr;
             cfg.numAttrs = pdl ? 1 : 0;
             return cudaLaunchKernelEx(&cfg, k_multi_tma<TX, TZ, NT>, jobs, njobs, total, t, err,
-                                      timeout_ns);
+                                      timeout_ns, stall_tile);
         }
     }
 };
@@ -366,11 +371,11 @@ cudaError_t prepare_tma_kernels() {
 }
 
 cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,
-                             int cap, int *err, unsigned long long timeout_ns, cudaStream_t s,
-                             bool pdl) {
+                             int cap, int *err, unsigned long long timeout_ns, int stall_tile,
+                             cudaStream_t s, bool pdl) {
     switch (cfg) {
 #define SSX_CASE_TMA_LAUNCH(id, TX, TZ, NT) \
-    case id: return TmaKernel<TX, TZ, NT>::launch(jobs, njobs, total_tiles, t, err, timeout_ns, cap, s, pdl);
+    case id: return TmaKernel<TX, TZ, NT>::launch(jobs, njobs, total_tiles, t, err, timeout_ns, stall_tile, cap, s, pdl);
         SSX_TILE_CONFIGS(SSX_CASE_TMA_LAUNCH)
 #undef SSX_CASE_TMA_LAUNCH
     }
