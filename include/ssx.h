@@ -274,9 +274,9 @@ int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
  * 64x32/512, 64x32/1024, 128x16/512, 128x32/1024, 32x16/256); 8 + k fixes
  * shape k with the multi-sweep steps run by the TMA-staged kernel (operand
  * tiles copied by the tensor memory accelerator into a two-stage shared-memory
- * pipeline, persistent CTAs), available for space order 8 and the shapes
- * whose column strips hold at least two rows (all but 2); elsewhere 8 + k
- * runs shape k. All configurations compute identical results. */
+ * pipeline, persistent CTAs), available for space order 8; for other orders
+ * 8 + k runs shape k. All configurations compute identical results. */
+#define SSX_NUM_TILE_CONFIGS 8
 int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
 
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the

@@ -23,6 +23,8 @@ SWEEP_AUTO, SWEEP_STEP, SWEEP_PERSISTENT, SWEEP_TEST_STALL = 0, 1, 2, 3
 W_D, W_M, W_M_INV = 0, 1, 2
 
 # every symbol the header declares, in declaration order
+N_TILE_CONFIGS = 8    # SSX_NUM_TILE_CONFIGS of include/ssx.h
+
 EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_velocity_model", "ssx_set_geometry", "ssx_forward", "ssx_adjoint",
            "ssx_weight_apply", "ssx_precond_apply", "ssx_normal_apply",

@@ -32,6 +32,15 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, s), s
 
 
+def test_binding_constants_match_the_header():
+    from paper_2203_16573_gb300 import ssx
+    text = open(os.path.join(ROOT, "include", "ssx.h")).read()
+    n = int(re.search(r"#define SSX_NUM_TILE_CONFIGS (\d+)", text).group(1))
+    assert ssx.N_TILE_CONFIGS == n
+    src = open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "ssx_internal.cuh")).read()
+    assert re.search(r"constexpr int kNumTileCfgs = (\d+);", src).group(1) == str(n)
+
+
 def test_version_string(lib):
     assert b"sm_103a" in lib.ssx_version()
 

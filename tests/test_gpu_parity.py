@@ -280,10 +280,28 @@ def test_persistent_wait_timeout_is_reported_and_context_survives(ssx, oracle):
     assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
 
 
+def test_tma_copy_wait_timeout_is_reported_and_context_survives(ssx):
+    """The TMA-staged phase kernel: a tile whose copies are withheld (test
+    hook) makes its CTA's bounded mbarrier wait run out (0.2 s); the call
+    returns SSX_ERR_CUDA, no copy is left in flight, and the next call on the
+    same context gives the same bits as before."""
+    spec = frac_spec(8, nt=80)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    ctx.set_tile_config(ssx.N_TILE_CONFIGS)   # TMA-staged kernel, shape 0
+    x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 21))
+    ref = ctx.forward(x).clone()
+    ctx.set_sweep_mode(ssx.SWEEP_TEST_STALL)
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.forward(x)
+    assert e.value.code == 2 and "timed out" in e.value.msg
+    assert torch.equal(ctx.forward(x), ref)
+    ctx.set_tile_config(-1)
+
+
 @pytest.mark.parametrize("order", [4, 8])
 def test_every_tile_configuration_gives_identical_results(ssx, order):
     """All tile shapes / CTA sizes, both launch forms and the TMA-staged phase
-    kernel (ids 8-15; order 8) run the same per-point arithmetic:
+    kernel (ids N..2N-1; order 8) run the same per-point arithmetic:
     bitwise-identical sweeps (ragged tiles on both grid edges)."""
     spec = frac_spec(order, nt=120)
     ctx = ssx.Context.for_problem(spec, W.velocity(spec))
@@ -292,7 +310,8 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     ref = None
     for mode in (ssx.SWEEP_STEP, ssx.SWEEP_PERSISTENT):
         ctx.set_sweep_mode(mode)
-        for cfg in range(16 if mode == ssx.SWEEP_STEP else 8):
+        N = ssx.N_TILE_CONFIGS
+        for cfg in range(2 * N if mode == ssx.SWEEP_STEP else N):
             ctx.set_tile_config(cfg)
             got = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
                    ctx.weight_apply(ssx.W_D, y).clone())
