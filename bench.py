@@ -429,9 +429,14 @@ def run_grad(args):
     wav = torch.as_tensor(W.ricker(specs[0]), device=dev)
     ds = [truth.point_source_data(sp.x_d, sp.z_d, wav) for sp in specs]
     truth.close()
+    # one stream per shot: each context's calls are ordered after its own
+    # stream, so the shots' gradients can run side by side
+    streams = [torch.cuda.Stream() for _ in specs]
+    main = torch.cuda.current_stream()
     ctxs = []
-    for sp in specs:
-        c = ssx.Context.from_spec(sp)
+    for sp, st in zip(specs, streams):
+        c = ssx.Context.from_spec(sp, st)
+        st.wait_stream(main)
         c.set_velocity_model(vb, sp.rho)
         c.set_geometry(sp.z_s, sp.ix_line0, sp.n_line, sp.z_r, sp.ix_rec0, sp.n_rec, sp.x_s,
                        sp.dz_datum)
@@ -439,30 +444,36 @@ def run_grad(args):
     alphas = [sp.alpha for sp in specs]
     hs = [c._empty(c.n_line) for c in ctxs]
     grad = torch.zeros((bspec.nz, bspec.nx), dtype=torch.float64, device=dev)
+    gbufs = [torch.empty_like(grad) for _ in ctxs]
     K = 50
 
-    def evaluate():
-        ssx.solve_batch(ctxs, ds, alphas, args.maxit, 0.0, ssx.MODE_CG, hs)
+    def evaluate(maxit):
+        for st in streams:
+            st.wait_stream(main)
+        ssx.solve_batch(ctxs, ds, alphas, maxit, 0.0, ssx.MODE_CG, hs)
+        for st in streams:
+            main.wait_stream(st)
         e1.record()
         grad.zero_()
-        phi = 0.0
-        for c, h, d in zip(ctxs, hs, ds):
-            g, ph = c.velocity_gradient(h, d, c_alpha, K)
-            grad.add_(g)
-            phi += ph
-        return phi
+        for c, h, d, gb, st in zip(ctxs, hs, ds, gbufs, streams):
+            st.wait_stream(main)
+            with torch.cuda.stream(st):
+                c.velocity_gradient(h, d, c_alpha, K, out=gb, wait=False)   # queued, not waited
+        for gb, st in zip(gbufs, streams):
+            main.wait_stream(st)
+            grad.add_(gb)
+        e2.record()
+        return sum(c.last_objective() for c in ctxs)
 
     c_alpha = alphas[0]
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    # warm-up: tuning, graph capture, gradient scratch
-    ssx.solve_batch(ctxs, ds, alphas, 1, 0.0, ssx.MODE_CG, hs)
-    ctxs[0].velocity_gradient(hs[0], ds[0], c_alpha, K)
+    # warm-up: tuning, graph capture, every context's gradient scratch
+    evaluate(1)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     e0.record()
-    phi = evaluate()
-    e2.record()
+    phi = evaluate(args.maxit)
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_solve = e0.elapsed_time(e1) / 1000.0

@@ -211,11 +211,19 @@ int ssx_solve_batch(ssx_ctx *const *ctxs, int n, const double *const *d_dev, con
  * (set from max c) is held fixed. Results do not depend on checkpoint_every.
  * h_dev [nt][n_line], d_dev [nt][n_rec] in (device); grad_dev [nz][nx]
  * float64 out (device, dPhi/dc in the units of the model); objective_host
- * (may be NULL) receives Phi. Device memory: (nt / checkpoint_every) x 3 +
- * checkpoint_every + 11 padded fields, kept by the context for reuse.
- * Errors: SSX_ERR_ARG for null pointers, checkpoint_every < 1 or alpha < 0. */
+ * (may be NULL) receives Phi and makes the call synchronise; with NULL the
+ * call returns once its work is queued on the context's stream (ordered
+ * before later work on the caller's stream), so the gradients of several
+ * contexts (a survey's shots) run concurrently. Device memory:
+ * (nt / checkpoint_every) x 3 + checkpoint_every + 11 padded fields, kept by
+ * the context for reuse. Errors: SSX_ERR_ARG for null pointers,
+ * checkpoint_every < 1 or alpha < 0. */
 int ssx_velocity_gradient(ssx_ctx *ctx, const double *h_dev, const double *d_dev, double alpha,
                           int checkpoint_every, double *grad_dev, double *objective_host);
+
+/* Phi of the context's last ssx_velocity_gradient (synchronises the context's
+ * stream). SSX_ERR_ARG if no gradient was computed yet. */
+int ssx_last_objective(ssx_ctx *ctx, double *objective_host);
 
 /* A solve server with continuous batching. Requests (each a full source
  * subproblem: grid, geometry, model, data, alpha, stopping rule, output

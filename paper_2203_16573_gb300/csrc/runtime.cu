@@ -31,6 +31,8 @@
 #include <chrono>
 #include <deque>
 #include <functional>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -132,6 +134,8 @@ struct ssx_ctx {
     // accumulator and trace buffers (doubles); grown on demand, kept
     float *gw = nullptr;
     size_t gw_floats = 0;
+    double grad_alpha = 0.0;          // alpha of the last gradient (its Phi: 2 scalars in gwd)
+    bool have_grad = false;
     double *gwd = nullptr;
     size_t gw_doubles = 0;
     int sweep_mode = SSX_SWEEP_AUTO;
@@ -417,9 +421,34 @@ int capacity(ssx_ctx *c, int cfg, bool adj) {
 // Pick the tile configuration and launch form of a grid's sweeps in one
 // direction by timing each admissible candidate on a short source-free sweep
 // (all configurations give identical results, so only speed matters).
+// Tuned choices are shared by every context of the process with a grid of the
+// same shape (padded size, sponge width, order), direction and sweep mode, so
+// the shots of a survey tune once.
+struct TuneKey {
+    int dev, NX, NZ, nsp, R, adj, mode;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, NX, NZ, nsp, R, adj, mode) <
+               std::tie(o.dev, o.NX, o.NZ, o.nsp, o.R, o.adj, o.mode);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, bool>> g_tuned;
+
 int select_config(ssx_ctx *c, DGrid &G, bool adj) {
     const int d = adj ? 1 : 0;
     if (G.cfg[d] >= 0) return SSX_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const TuneKey key{dev, G.L.NX, G.L.NZ, c->gd.n_sponge, c->R, d, c->sweep_mode};
+    if (c->forced_cfg < 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            G.cfg[d] = it->second.first;
+            G.pers[d] = it->second.second;
+            return SSX_OK;
+        }
+    }
     struct Cand {
         int cfg;
         bool pers;
@@ -482,6 +511,10 @@ int select_config(ssx_ctx *c, DGrid &G, bool adj) {
     } else {
         G.cfg[d] = cands[0].cfg;
         G.pers[d] = cands[0].pers;
+    }
+    if (c->forced_cfg < 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[key] = {G.cfg[d], G.pers[d]};
     }
     return SSX_OK;
 }
@@ -1608,6 +1641,19 @@ int ssx_forward(ssx_ctx *c, const double *h_dev, double *d_dev) {
 //      its reverse steps run, each preceded by the accumulation of
 //      pbar^{n+1} (p^{n+1} - A_p p^n) / kappa~ into the FP64 gradient;
 //   4. the padded-grid sum is folded onto the physical model.
+// Phi of the last gradient: ||y - d||^2 = |ybar|^2 / 4 and ||A h||^2, the two
+// scalars after the gradient's trace and penalty buffers (synchronises)
+static int last_objective(ssx_ctx *c, double *objective) {
+    if (!c->have_grad) return fail(c, SSX_ERR_ARG, "no velocity gradient computed yet");
+    const int nt = c->gd.nt;
+    const size_t NP = (size_t)c->full.L.NX * c->full.L.NZ;
+    const double *sc = c->gwd + NP + 2 * (size_t)nt * c->geom.n_rec + (size_t)nt * c->geom.n_line;
+    CK(cudaMemcpyAsync(c->sc_host, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    *objective = 0.25 * c->sc_host[0] + c->grad_alpha * c->sc_host[1];
+    return SSX_OK;
+}
+
 static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, double alpha, int K,
                              double *grad, double *objective) {
     DGrid &G = c->full;
@@ -1623,7 +1669,6 @@ static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, doubl
     // doubles: accumulator [NZ][NX] | y, ybar [nt][nrec] | A h [nt][nl] | 2 scalars
     const size_t NP = (size_t)G.L.NX * G.L.NZ;
     const size_t nd = NP + 2 * (size_t)nt * nrec + (size_t)nt * nl + 2;
-    cudaStream_t s = c->s;
     if (c->gw_floats < nf) {
         if (c->gw) CK(cudaFree(c->gw));
         c->gw = nullptr;
@@ -1644,6 +1689,9 @@ static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, doubl
     float *abuf = vbuf + 4 * E;                           // adjoint [p vx vz] x 2
     double *gacc = c->gwd, *y = gacc + NP, *ybar = y + (size_t)nt * nrec;
     double *ah = ybar + (size_t)nt * nrec, *sc = ah + (size_t)nt * nl;
+    // the launches, captured once per set of buffers into a CUDA graph (an
+    // outer loop recomputes gradients on the same buffers) and replayed
+    auto enqueue = [&](cudaStream_t s) -> int {
     // every field array starts from zeros: the aprons are never written
     CK(cudaMemsetAsync(slot, 0, (size_t)(seg + 1 + 4 + 6) * E * sizeof(float), s));
     CK(cudaMemsetAsync(gacc, 0, NP * sizeof(double), s));
@@ -1731,13 +1779,15 @@ static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, doubl
     // 4. onto the physical model: dPhi/dv = 2 rho v (dt/h) sum dPhi/dkappa~
     CK(launch_grad_fold(grad, gacc, c->vel, c->gd.nx, c->gd.nz, c->gd.n_sponge, G.L.NX,
                         2.0 * c->rho * c->gd.dt / c->gd.h, s));
-    c->st.kernel_launches += 4LL * nt + 6;
-    c->st.point_updates += 3LL * (long long)G.L.NX * G.L.NZ * nt;
-    if (objective) {
-        CK(cudaMemcpyAsync(c->sc_host, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        *objective = 0.25 * c->sc_host[0] + alpha * c->sc_host[1];
-    }
+    return SSX_OK;
+    };
+    char key[256];
+    snprintf(key, sizeof key, "grad:%p:%p:%p:%p:%p:%d:%d:%d:%d", (const void *)h, (const void *)d,
+             (void *)grad, (void *)c->gw, (void *)c->gwd, K, nt, cf, ca);
+    TRY(run_cached(c, key, 4LL * nt + 6, 3LL * nt, 3.0 * G.L.NX * G.L.NZ * nt, enqueue));
+    c->grad_alpha = alpha;
+    c->have_grad = true;
+    if (objective) TRY(last_objective(c, objective));
     return SSX_OK;
 }
 
@@ -1748,9 +1798,16 @@ int ssx_velocity_gradient(ssx_ctx *c, const double *h_dev, const double *d_dev, 
     if (checkpoint_every < 1) return fail(c, SSX_ERR_ARG, "checkpoint_every must be >= 1");
     if (!(alpha >= 0.0)) return fail(c, SSX_ERR_ARG, "alpha must be >= 0");
     TRY(enter(c));
-    int rc = velocity_gradient(c, h_dev, d_dev, alpha, checkpoint_every, grad_dev, objective);
-    if (rc == SSX_OK) rc = check_sweeps(c);
+    // step kernels only (no bounded waits, so no timeout flag to read): without
+    // objective_host the call returns as soon as its work is queued
+    const int rc = velocity_gradient(c, h_dev, d_dev, alpha, checkpoint_every, grad_dev, objective);
     return leave(c, rc);
+}
+
+int ssx_last_objective(ssx_ctx *c, double *objective_host) {
+    if (!c) return SSX_ERR_ARG;
+    if (!objective_host) return fail(c, SSX_ERR_ARG, "null argument");
+    return last_objective(c, objective_host);
 }
 
 int ssx_adjoint(ssx_ctx *c, const double *d_dev, double *h_dev) {

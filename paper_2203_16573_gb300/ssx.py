@@ -33,7 +33,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
            "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
-           "ssx_velocity_gradient"]
+           "ssx_velocity_gradient", "ssx_last_objective"]
 
 
 class SSXError(RuntimeError):
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_server_destroy": ([vp], i),
         "ssx_server_last_error": ([vp], ctypes.c_char_p),
         "ssx_velocity_gradient": ([vp, vp, vp, d, i, vp, P(d)], i),
+        "ssx_last_objective": ([vp, P(d)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -234,9 +235,11 @@ class Context:
                                                self._line(out, "q")))
         return out
 
-    def velocity_gradient(self, h, d, alpha=0.0, checkpoint_every=50, out=None):
+    def velocity_gradient(self, h, d, alpha=0.0, checkpoint_every=50, out=None, wait=True):
         """dPhi/dc of Phi = ||S[c] h - d||^2 + alpha ||A h||^2 at fixed h
-        (ssx_velocity_gradient): returns (gradient [nz][nx] float64, Phi)."""
+        (ssx_velocity_gradient): returns (gradient [nz][nx] float64, Phi).
+        wait=False returns (gradient, None) as soon as the work is queued
+        (Phi later from last_objective())."""
         out = (torch.empty((self.nz, self.nx), dtype=torch.float64, device=self.device)
                if out is None else out)
         if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != (self.nz, self.nx):
@@ -245,8 +248,14 @@ class Context:
         self._check(self._lib.ssx_velocity_gradient(self._c, self._line(h, "h"), self._rec(d, "d"),
                                                     float(alpha), int(checkpoint_every),
                                                     ctypes.c_void_p(out.data_ptr()),
-                                                    ctypes.byref(obj)))
-        return out, obj.value
+                                                    ctypes.byref(obj) if wait else None))
+        return out, (obj.value if wait else None)
+
+    def last_objective(self):
+        """Phi of the last velocity_gradient (synchronises)."""
+        obj = ctypes.c_double(0.0)
+        self._check(self._lib.ssx_last_objective(self._c, ctypes.byref(obj)))
+        return obj.value
 
     def solve(self, d, alpha, maxit, rtol, mode=MODE_PCG, out=None, allow_not_converged=True):
         """Algorithm 1. Returns (h, residual history (numpy), iterations, status)."""

@@ -141,3 +141,31 @@ def test_autograd_reduced_objective_matches_central_differences(ssx):
     ctx.set_velocity_model(torch.as_tensor(v0, dtype=torch.float32, device="cuda"), spec.rho)
     _, hist, iters, _ = ctx.solve(d, spec.alpha, 900, 1e-10, ssx.MODE_CG)
     assert abs(fd - an) / abs(an) < 2e-2, (fd, an, iters, hist[-1] / hist[0])
+
+
+def test_queued_gradients_on_several_streams_match_waited_ones(ssx):
+    """Without the objective the call only queues its work: gradients of two
+    contexts on their own streams, read after the fact, equal the waited
+    results, and last_objective gives the same Phi."""
+    spec = frac_spec(8, 90)
+    vel = W.velocity(spec)
+    h = dev(W.smooth_random_gather(spec.nt, spec.n_line, 35))
+    d = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 36))
+    ref_ctx = ssx.Context.for_problem(spec, vel)
+    with pytest.raises(ssx.SSXError):
+        ref_ctx.last_objective()
+    ref, phi_ref = ref_ctx.velocity_gradient(h, d, 0.1, checkpoint_every=20)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    ctxs = [ssx.Context.for_problem(spec, vel, stream=s) for s in streams]
+    outs = []
+    for c, s in zip(ctxs, streams):
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            g, phi = c.velocity_gradient(h, d, 0.1, checkpoint_every=20, wait=False)
+        assert phi is None
+        outs.append(g)
+    for s in streams:
+        torch.cuda.current_stream().wait_stream(s)
+    for c, g in zip(ctxs, outs):
+        assert torch.equal(g, ref)
+        assert c.last_objective() == phi_ref
