@@ -194,9 +194,10 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     if (G.tab) cudaFree(G.tab);
     G.mem = nullptr;
     G.tab = nullptr;
-    CK(cudaMalloc(&G.mem, 7 * E * sizeof(float)));
+    // kap | buffer 0 (p vx vz) | buffer 1 (p vx vz) | C_p
+    CK(cudaMalloc(&G.mem, 8 * E * sizeof(float)));
     CK(cudaMalloc(&G.tab, 2 * (size_t)(L.NX + L.NZ) * sizeof(float)));
-    CK(cudaMemsetAsync(G.mem, 0, 7 * E * sizeof(float), c->s));
+    CK(cudaMemsetAsync(G.mem, 0, 8 * E * sizeof(float), c->s));
     int max_tiles = 0;
     for (int k = 0; k < kNumTileCfgs; k++) {
         const int t = ((L.NX + kTileCfgs[k].tx - 1) / kTileCfgs[k].tx) *
@@ -215,6 +216,7 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     a.NZ = L.NZ;
     a.pitch = L.pitch;
     a.kap = G.kap;
+    a.cpk = G.mem + 7 * E + L.origin();
     a.sxi = G.tab;
     a.sxh = G.tab + L.NX;
     a.szi = G.tab + 2 * L.NX;
@@ -273,6 +275,7 @@ int grid_fill(ssx_ctx *c, DGrid &G) {
     CK(launch_sponge_table(G.tab + 2 * G.L.NX, G.tab + 2 * G.L.NX + G.L.NZ, G.L.NZ, G.nz, nsp,
                            smax * d.dt * 0.5, c->s));
     G.args.cv = (float)(d.dt / (c->rho * d.h));
+    CK(launch_fill_cpk(G.args, G.L, G.mem + 7 * G.L.elems(), c->s));
     G.ready = true;
     return SSX_OK;
 }
@@ -727,7 +730,7 @@ int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, Ph
                 ok = ok && field_map(&tj[j].map[2 + b], G.f[b][1], G.L, TX + 2 * R, TZ);
                 ok = ok && field_map(&tj[j].map[4 + b], G.f[b][2], G.L, TX, TZ + 2 * R - 1);
             }
-            ok = ok && (jobs[j].adj ? field_map(&tj[j].map[6], G.args.kap, G.L, TX + 4 * R, TZ + 4 * R)
+            ok = ok && (jobs[j].adj ? field_map(&tj[j].map[6], G.args.cpk, G.L, TX + 4 * R, TZ + 4 * R)
                                     : field_map(&tj[j].map[6], G.args.kap, G.L, TX, TZ));
             if (!ok) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
         }
@@ -1377,7 +1380,7 @@ static size_t estimate_bytes(const ssx_grid_desc &g, const ssx_geom_desc &m) {
         const int NX = nx + 2 * nsp, NZ = nz + 2 * nsp;
         const size_t pitch = ((((NX + TILE_X_MAX - 1) / TILE_X_MAX) * TILE_X_MAX + 2 * GX + 31) / 32) * 32;
         const size_t rows = ((NZ + TILE_Z_MAX - 1) / TILE_Z_MAX) * TILE_Z_MAX + 2 * GZ;
-        return 7 * pitch * rows * 4 + (size_t)4096 * 4;
+        return 8 * pitch * rows * 4 + (size_t)4096 * 4;
     };
     const int slab_rows = (int)std::ceil(m.dz_datum / g.h) + 3 + g.space_order;
     const size_t nl = (size_t)g.nt * m.n_line, nr = (size_t)g.nt * m.n_rec;

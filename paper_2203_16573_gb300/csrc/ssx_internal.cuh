@@ -45,6 +45,7 @@ struct Line {
 struct GridArgs {
     int NX, NZ, pitch;
     const float *kap;       // kappa dt / h at p points (origin-offset pointer)
+    const float *cpk;       // C_p = B_p kappa dt / h inside the grid, 0 outside (same layout)
     const float *sxi, *sxh; // sigma dt/2 at x = i h and (i+1/2) h, [NX]
     const float *szi, *szh; // sigma dt/2 at z = k h and (k+1/2) h, [NZ]
     float cv;               // dt / (rho h)
@@ -109,7 +110,7 @@ constexpr int kMaxJobs = 4;
 // A sweep of a phase run by the TMA-staged kernel (order 8): its arguments and
 // the tensor maps of its storage -- p, v_x, v_z of ping-pong buffers 0 and 1
 // (maps 0-1, 2-3, 4-5; boxes of the tile with halos 2k x 2k, k x 0, 0 x k)
-// and kappa (map 6: the tile, or the p box for a transposed sweep).
+// and kappa over the tile (map 6) or, for a transposed sweep, C_p over the p box.
 struct alignas(128) TmaJob {
     CUtensorMap map[7];
     Job job;
@@ -188,6 +189,8 @@ cudaError_t launch_fill_kappa(float *kap, const FieldLayout &L, const float *vel
 cudaError_t launch_sponge_table(float *ti, float *th, int N, int n_phys, int nsp,
                                 double smax_dt_half, cudaStream_t s);
 cudaError_t launch_vmax(const float *v, int n, float *out, cudaStream_t s);
+// C_p = B_p kappa dt/h over a grid's whole storage (0 outside the padded grid)
+cudaError_t launch_fill_cpk(const GridArgs &a, const FieldLayout &L, float *cpk, cudaStream_t s);
 
 // FP64 Krylov kernels (krylov.cu).
 constexpr int kDotBlocks = 512;

@@ -2,11 +2,27 @@
 // maximum), the adjoint sweep's initial injection, and the dispatch of the
 // step kernels (stencil_impl.cuh, instantiated per half order R in
 // stencil_r<R>.cu) over R and the tile configurations.
-#include "ssx_internal.cuh"
+#include "stencil_impl.cuh"
 
 namespace ssx {
 
 namespace {
+
+// C_p = B_p kappa~ at every storage point, with B_p the pressure points'
+// sponge factor (the same damp() as the steps) and 0 outside the padded grid,
+// so the transposed step stages q = C_p pbar with one product and no tests.
+__global__ void k_fill_cpk(float *cpk, const GridArgs a, int rows, int gz, int gx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= a.pitch || y >= rows) return;
+    const int k = y - gz, i = x - gx;
+    float v = 0.0f;
+    if (k >= 0 && k < a.NZ && i >= 0 && i < a.NX) {
+        float A, B;
+        damp(a.sxi[i] + a.szi[k], A, B);
+        v = __fmul_rn(B, a.kap[k * a.pitch + i]);
+    }
+    cpk[(size_t)y * a.pitch + x] = v;
+}
 
 // Adjoint state entering reverse step nt-1: the transposed sampling of the
 // last trace sample, on zeroed fields (one thread per receiver column, so the
@@ -125,6 +141,12 @@ cudaError_t prepare_kernels() {
     if ((e = stencil_prepare_r3()) != cudaSuccess) return e;
     if ((e = stencil_prepare_r4()) != cudaSuccess) return e;
     return prepare_tma_kernels();
+}
+
+cudaError_t launch_fill_cpk(const GridArgs &a, const FieldLayout &L, float *cpk, cudaStream_t s) {
+    dim3 grid((L.pitch + 127) / 128, L.rows);
+    k_fill_cpk<<<grid, 128, 0, s>>>(cpk, a, L.rows, GZ, GX);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adj_init(const AdjArgs &a, int nt, cudaStream_t s) {

@@ -94,7 +94,9 @@ __device__ __forceinline__ bool interior_tile(const GridArgs &g, int i0, int k0)
     if (const int c = lane + 32 * c##_u; c < (n))
 
 // Stage a field over tile + 2k halo (corners are never used and not loaded);
-// with PRE the staged value is C_p * field (transpose step).
+// with PRE the staged value is C_p * field (transpose step), C_p from the
+// grid's precomputed field (B_p kappa~ inside the grid, 0 outside: the
+// storage's apron makes every address valid).
 template <int R, int TX, int TZ, int NT, bool SP, bool PRE>
 __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i0, int k0,
                                         float (&sp)[TZ + 4 * R][TX + 4 * R]) {
@@ -104,11 +106,7 @@ __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i
     auto val = [&](int k, int i) -> float {
         const int o = k * pitch + i;
         if (!PRE) return ldf(f + o);
-        if (!SP) return __fmul_rn(__ldg(g.kap + o), ldf(f + o));
-        if (k < 0 || k >= g.NZ || i < 0 || i >= g.NX) return 0.0f;
-        float A, B;
-        damp(__ldg(g.sxi + i) + __ldg(g.szi + k), A, B);
-        return __fmul_rn(__fmul_rn(B, __ldg(g.kap + o)), ldf(f + o));
+        return __fmul_rn(__ldg(g.cpk + o), ldf(f + o));
     };
     // tile rows with the x halo
     FOR_ROWS(r, TZ) {

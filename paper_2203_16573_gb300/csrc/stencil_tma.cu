@@ -41,7 +41,7 @@ struct TmaStage {
     alignas(128) float p[PH][PW];      // p (forward) or pbar (transposed); q = C_p pbar after staging
     alignas(128) float vx[TZ][VXB];    // v_x, x = i0-k .. i0+TX+k-1
     alignas(128) float vz[VZH][TX];    // v_z, rows k0-k .. k0+TZ+k-2
-    alignas(128) float k[PH][PW];      // kappa: [TZ][TX] at i0 (forward) or the p box (transposed)
+    alignas(128) float k[PH][PW];      // kappa: [TZ][TX] at i0 (forward); C_p over the p box (transposed)
     static constexpr unsigned bytes(bool adj) {
         return (unsigned)(sizeof(float) * (PH * PW + TZ * VXB + VZH * TX + (adj ? PH * PW : TZ * TX)));
     }
@@ -126,8 +126,9 @@ struct TmaIn {
     __device__ __forceinline__ float own_p(int j) const { return st.p[rs + j + 2 * kR][c + 2 * kR]; }
     __device__ __forceinline__ float hvx(int r, int jj) const { return st.vx[r][jj]; }
     __device__ __forceinline__ float hvz(int kk, int i) const { return st.vz[kk][i - i0]; }
-    // transposed step: q = C_p pbar in place over the box (0 outside the grid),
-    // the per-point arithmetic of stage_p; every thread has its own pbar first
+    // transposed step: q = C_p pbar in place over the box (C_p is 0 outside
+    // the grid), the per-point arithmetic of stage_p; every thread has its own
+    // pbar first
     template <bool PRE>
     __device__ __forceinline__ void stage() {
         if (!PRE) return;
@@ -138,18 +139,7 @@ struct TmaIn {
             const int e = threadIdx.x + q * NT;
             if (e < N) {
                 const int r = e / St::PW, x = e % St::PW;
-                const float pv = st.p[r][x], kv = st.k[r][x];
-                float v;
-                if (!SP) {
-                    v = __fmul_rn(kv, pv);
-                } else {
-                    const int k = k0 - 2 * kR + r, i = i0 - 2 * kR + x;
-                    const bool ok = k >= 0 && k < g.NZ && i >= 0 && i < g.NX;
-                    float A, B;
-                    damp(__ldg(g.sxi + (ok ? i : 0)) + __ldg(g.szi + (ok ? k : 0)), A, B);
-                    v = ok ? __fmul_rn(__fmul_rn(B, kv), pv) : 0.0f;
-                }
-                st.p[r][x] = v;
+                st.p[r][x] = __fmul_rn(st.k[r][x], st.p[r][x]);
             }
         }
     }
