@@ -316,7 +316,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 fields, f64 krylov", "data": "synthetic (seeded lens model, Ricker point source)",
+            "dtype": "f32", "dtype_note": "fields and stencils f32; Krylov vectors, scalars and reductions f64", "data": "synthetic (seeded lens model, Ricker point source)",
             "config": config_of(spec, world),
             "iterations": iters_list, "final_rel_residual": res_list,
             "converged": all(r <= spec.rtol for r in res_list),
@@ -394,7 +394,7 @@ def run_batch(args):
     line = {"metric": "batched survey: stencil Gpt-updates/s & HBM % of peak", "value": gpts,
             "unit": "Gpt-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 fields, f64 krylov", "data": "synthetic (seeded lens model, Ricker point sources)",
+            "dtype": "f32", "dtype_note": "fields and stencils f32; Krylov vectors, scalars and reductions f64", "data": "synthetic (seeded lens model, Ricker point sources)",
             "config": {"workload": f"c3 survey: {args.shots} shots, 2001x801 lens model, h 5 m, "
                                    f"order 8, nt {args.nt}, set-up + {args.maxit} PCG iterations",
                        "l2": "inputs larger than L2 (per-step state of all shots ~4 GB)"},
@@ -488,7 +488,7 @@ def run_grad(args):
                       "adjoint-state velocity gradient, all shots)",
             "value": 1.0 / (t_solve + t_grad), "unit": "gradients/s", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": 1000.0 * (t_solve + t_grad), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, f64 gradient and krylov",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "dtype_note": "fields and stencils f32; gradient sum, Krylov vectors and reductions f64",
             "data": "synthetic (seeded perturbed gradient model, Ricker point sources)",
             "config": {"workload": f"gradient: {len(specs)} shots, 1001x401 background model "
                                    f"(h 8 m), order 8, nt {bspec.nt}, checkpoints every {K} "
@@ -528,7 +528,7 @@ def run_serve(args):
     line = {"metric": "served PCG solves/s (continuous batching) with p50/p99 latency",
             "value": len(specs) / wall_b, "unit": "solves/s", "n_gpus": 1, "steps": len(specs),
             "warmup": 1, "ms_per_step": 1000.0 * wall_b / len(specs), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, f64 krylov",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "dtype_note": "fields and stencils f32; Krylov vectors, scalars and reductions f64",
             "data": "synthetic (seeded Poisson request stream)",
             "config": {"workload": f"{len(specs)} requests, Poisson rate {args.rate}/s, grids "
                                    f"{{401x201,1001x401,2001x801}} x {args.scale}, nt 1000-5000 x "
