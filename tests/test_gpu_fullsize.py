@@ -52,3 +52,36 @@ def test_survey_shots_batched_equal_solo_at_full_size(ssx):
         assert it1 == 1 and float(h1.abs().max()) > 0
         assert torch.equal(h, h1)
         np.testing.assert_array_equal(hh, hh1)
+
+
+def test_lens_solve_operators_commute_with_the_mirror_at_full_size(ssx):
+    """The single-shot lens workload (601 x 301, order 8, 3000 steps) has
+    x_s, the source line and the receivers on or centred on the middle
+    column. With its model made exactly symmetric about that column,
+    reflecting the gathers about x_s commutes with S, S^T, the three
+    thin-slab weights and M^{-1} (the staggered grid, the sponge ramps and
+    |x - x_s| map onto themselves), and the solve of reflected data returns
+    the reflected source: a property of the full-size launches that needs
+    no oracle run."""
+    from paper_2203_16573_gb300 import ssx as S
+    spec = W.c2()
+    v = W.velocity(spec)
+    ctx = ssx.Context.for_problem(spec, 0.5 * (v + v[:, ::-1]))
+    h = dev(W.smooth_random_gather(spec.nt, spec.n_line, 61))
+    d = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 62))
+    flip = lambda a: torch.flip(a, dims=[1])
+    ops = ((ctx.forward, h), (ctx.adjoint, d), (lambda x: ctx.weight_apply(S.W_D, x), d),
+           (lambda x: ctx.weight_apply(S.W_M, x), h), (lambda x: ctx.weight_apply(S.W_M_INV, x), h),
+           (lambda x: ctx.precond_apply(spec.alpha, x), h))
+    for k, (op, x) in enumerate(ops):
+        y = op(x).clone()
+        ym = op(flip(x).contiguous())
+        assert float(y.norm()) > 0, k
+        assert float((flip(y) - ym).norm() / y.norm()) <= 1e-6, k
+    d0 = ctx.point_source_data(spec.x_d, spec.z_d, torch.as_tensor(W.ricker(spec), device="cuda"))
+    d1 = d0 + 0.05 * float(d0.abs().max()) * d     # not symmetric by itself
+    h1, hist1, _, _ = ctx.solve(d1, spec.alpha, 3, 0.0)
+    h1 = h1.clone()
+    h2, hist2, _, _ = ctx.solve(flip(d1).contiguous(), spec.alpha, 3, 0.0)
+    assert float((flip(h1) - h2).norm() / h1.norm()) <= 1e-5
+    np.testing.assert_allclose(hist2, hist1, rtol=1e-5)

@@ -439,10 +439,61 @@ def test_known_minimiser_objective_decreases(oracle):
         assert J[0] < J0 and all(b < a for a, b in zip(J, J[1:])), (mode, J0, J)
 
 
+# ------------------------------------------------ mirror symmetry ----------
+def _mirror_problem(oracle, order, nt=160):
+    """The reduced lens case (133 x 71, x_s on the centre column, source line
+    and receivers centred on it) with the model made exactly symmetric about
+    x_s."""
+    s = W.small(order=order, nt=nt)
+    v = W.velocity(s)
+    v = 0.5 * (v + v[:, ::-1])
+    return s, oracle.Problem(s, v)
+
+
+def _mirror_err(a, b):
+    """relative error of b against the reflection of a about the centre column"""
+    return float(np.linalg.norm(a[:, ::-1] - b) / np.linalg.norm(a))
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_operators_commute_with_the_mirror_about_x_s(oracle, order):
+    """Reflecting x about a p column maps the staggered grid onto itself
+    (p and v_z stay, v_x changes sign), the sponge ramps onto themselves and
+    |x - x_s| onto itself. With the model, the source line and the receivers
+    symmetric about x_s, S, S^T, W~_d, W~_m and W~_m^{-1} therefore commute
+    with reflecting the gathers, and S is linear. A sponge ramp shifted by
+    half a cell at the v_x points, a one-sided x difference or a line placed
+    one column off breaks the reflection."""
+    s, P = _mirror_problem(oracle, order)
+    h = W.random_gather(s.nt, s.n_line, 51)
+    d = W.random_gather(s.nt, s.n_rec, 52)
+    for op, x in ((P.S, h), (P.ST, d), (P.Wd, d), (P.Wm, h), (P.Wminv, h)):
+        y, ym = op(x), op(x[:, ::-1].copy())
+        assert np.linalg.norm(y) > 0
+        assert _mirror_err(y, ym) <= 1e-13, op.__name__
+    h2 = W.random_gather(s.nt, s.n_line, 53)
+    lin = P.S(2.5 * h - 0.75 * h2)
+    ref = 2.5 * P.S(h) - 0.75 * P.S(h2)
+    assert np.linalg.norm(lin - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_pcg_solution_of_mirrored_data_is_the_mirrored_solution(oracle):
+    """Every operator of Algorithm 1 commutes with the reflection, so the
+    iterates for reflected data are the reflected iterates (up to the
+    rounding of the inner products' summation order), for both modes."""
+    s, P = _mirror_problem(oracle, 4, nt=120)
+    d = W.smooth_random_gather(s.nt, s.n_rec, 54)
+    for mode in ("pcg", "cg"):
+        h, hist = oracle.pcg(P, d, s.alpha, 4, 0.0, mode=mode)
+        hm, histm = oracle.pcg(P, d[:, ::-1].copy(), s.alpha, 4, 0.0, mode=mode)
+        assert _mirror_err(h, hm) <= 1e-10, mode
+        np.testing.assert_allclose(histm, hist, rtol=1e-10)
+
 # ------------------------------------------------- planted mistakes --------
 def test_pins_catch_planted_mistakes(oracle, plane_problem):
-    """A wrong sign in c_2, a dropped component exchange, or the paper's
-    printed -1/16 in place of -1 each break a pin above."""
+    """A wrong sign in c_2, a dropped component exchange, the paper's
+    printed -1/16 in place of -1, or the sponge ramp of the v_x points taken
+    at the p points each break a pin above."""
     s, P, x, mid = plane_problem
     Z = s.rho * s.v0
     # (1) dropped exchange: S^T S instead of S^T J S -> negative form
@@ -468,3 +519,10 @@ def test_pins_catch_planted_mistakes(oracle, plane_problem):
     idx = np.arange(1, nt, 2)
     ex = np.array([_greens_pressure(0.3, (k + 1) * 0.2 * h, c, c * c, f, 1.5 / f) for k in idx])
     assert np.abs(tr[idx] - ex).max() / np.abs(ex).max() > 0.05
+    # (4) sponge ramp of the v_x points (half-integer x) read at integer x:
+    #     the reflection about x_s no longer maps the sponge onto itself
+    s4, P4 = _mirror_problem(oracle, 4)
+    bad = P4.g.sx_i.copy()
+    P4.g._c.sx_h = oracle._ptr(bad)
+    h4 = W.random_gather(s4.nt, s4.n_line, 55)
+    assert _mirror_err(P4.S(h4), P4.S(h4[:, ::-1].copy())) > 1e-6
