@@ -638,6 +638,10 @@ std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, in
         J.nt = w.nt;
         J.tiles_x = (w.G->L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx;
         J.tiles = J.tiles_x * ((w.G->L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz);
+        J.tx_shift = 0;
+        while ((1LL << J.tx_shift) < J.tiles_x) J.tx_shift++;
+        J.tx_mul = ((1ULL << (32 + J.tx_shift)) + (unsigned long long)J.tiles_x - 1) /
+                   (unsigned long long)J.tiles_x;
         J.tile_base = base;
         base += J.tiles;
         for (int b = 0; b < 2; b++)

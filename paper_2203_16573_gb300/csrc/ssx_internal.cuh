@@ -102,6 +102,11 @@ struct Job {
     int offset;              // launch index of the sweep's first step
     int nt;
     int tiles_x, tile_base, tiles;
+    // tile row of sweep tile tl: (tl * tx_mul) >> (32 + tx_shift) equals
+    // tl / tiles_x for 0 <= tl < 2^31 (tx_shift = ceil(log2 tiles_x),
+    // tx_mul = ceil(2^(32 + tx_shift) / tiles_x) < 2^33)
+    unsigned long long tx_mul;
+    int tx_shift;
     FwdArgs fa;              // forward: grid, lines, gathers (field pointers unused)
     AdjArgs aa;              // transposed: grid, lines, gathers
     float *f[2][3];          // ping-pong field triples (origin-offset pointers)

@@ -57,7 +57,9 @@ __device__ __forceinline__ float ldf(const float *p) { return __ldcg(p); }
 // Field stores, explicitly global: where a kernel reads the field pointers
 // from shared memory the compiler cannot tell their space and would emit
 // generic stores.
-__device__ __forceinline__ void st_out(float *p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void st_out(float *p, float v) {
+    asm volatile("st.global.cg.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
 
 template <int R, int TX, int TZ>
 struct TileSmem {

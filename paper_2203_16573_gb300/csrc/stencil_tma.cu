@@ -200,13 +200,23 @@ __device__ __forceinline__ int next_active(const TmaJob *__restrict__ jobs, int 
     return total;
 }
 
+// corner of sweep tile tl: tile row by the sweep's reciprocal of tiles_x
+template <int TX, int TZ>
+__device__ __forceinline__ void tile_corner(unsigned long long mul, int shift, int tiles_x, int tl,
+                                            int &i0, int &k0) {
+    const int q = (int)((unsigned)(((unsigned long long)(unsigned)tl * mul) >> 32) >> shift);
+    i0 = (tl - q * tiles_x) * TX;
+    k0 = q * TZ;
+}
+
 // thread 0: start the four copies of `tile` (sweep j) into stage `st`
 template <int TX, int TZ>
 __device__ __forceinline__ void issue(const TmaJob *__restrict__ jobs, int j, int tile, int t,
                                       TmaStage<TX, TZ> &st, unsigned bar) {
     const TmaJob &J = jobs[j];
-    const int tl = tile - __ldg(&J.job.tile_base), tx = __ldg(&J.job.tiles_x);
-    const int i0 = (tl % tx) * TX, k0 = (tl / tx) * TZ;
+    int i0, k0;
+    tile_corner<TX, TZ>(__ldg(&J.job.tx_mul), __ldg(&J.job.tx_shift), __ldg(&J.job.tiles_x),
+                        tile - __ldg(&J.job.tile_base), i0, k0);
     const int odd = (t - __ldg(&J.job.offset)) & 1;   // input buffer of this step
     const bool adj = __ldg(&J.job.adj) != 0;
     mbar_expect_tx(bar, TmaStage<TX, TZ>::bytes(adj));
@@ -232,10 +242,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         if (threadIdx.x == 0) atomicExch(err, 3);
         return;
     }
-    const unsigned bar[2] = {smem_u32(&sm.bar[0]), smem_u32(&sm.bar[1])};
+    // shared addresses of the two stage barriers: bar(s) = bar0 + 8 s (no
+    // runtime-indexed local array)
+    const unsigned bar0 = smem_u32(&sm.bar[0]);
+    auto bar = [bar0](int k) { return bar0 + 8u * (unsigned)k; };
     if (threadIdx.x == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
+        mbar_init(bar(0), 1);
+        mbar_init(bar(1), 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -247,28 +260,28 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
     // stall_tile (test hook, normally -1): that tile's copies are never issued,
     // so its wait must run out
     if (threadIdx.x == 0 && tile < total && tile != stall_tile)
-        issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar[0]);
-    unsigned parity[2] = {0u, 0u};
+        issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar(0));
+    unsigned parity = 0u;   // bit s: the phase stage s waits for next
     int s = 0, cur_job = -1;
     while (tile < total) {
         const int nxt = next_active(jobs, njobs, total, t, tile + G, G, &jn);
         // the other stage was last read before the previous tile's closing barrier
         if (threadIdx.x == 0 && nxt < total && nxt != stall_tile)
-            issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar[s ^ 1]);
+            issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar(s ^ 1));
         if (j != cur_job) {   // the sweep's arguments into shared memory
             const int *src = reinterpret_cast<const int *>(&jobs[j].job);
             int *dst = reinterpret_cast<int *>(&sm.job);
             for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
             cur_job = j;
         }
-        const bool ok = mbar_wait(bar[s], parity[s], timeout_ns);
+        const bool ok = mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(err, 2);
-            mbar_wait(bar[s], parity[s], timeout_ns);   // copies still in flight
-            if (nxt < total && nxt != stall_tile) mbar_wait(bar[s ^ 1], parity[s ^ 1], timeout_ns);
+            mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);   // copies still in flight
+            if (nxt < total && nxt != stall_tile) mbar_wait(bar(s ^ 1), (parity >> (s ^ 1)) & 1u, timeout_ns);
             return;
         }
-        parity[s] ^= 1u;
+        parity ^= 1u << s;
         const Job &J = sm.job;
         const int st = t - J.offset, tl = tile - J.tile_base;
         const int odd = st & 1;
@@ -278,7 +291,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         io.vx_out = J.f[odd ^ 1][1];
         io.vz_out = J.f[odd ^ 1][2];
         io.n = J.adj ? J.nt - 1 - st : st;
-        tma_tile<TX, TZ, NT>(J, io, (tl % J.tiles_x) * TX, (tl / J.tiles_x) * TZ, sm.st[s], sm);
+        int i0, k0;
+        tile_corner<TX, TZ>(J.tx_mul, J.tx_shift, J.tiles_x, tl, i0, k0);
+        tma_tile<TX, TZ, NT>(J, io, i0, k0, sm.st[s], sm);
         // the transposed step rewrote stage s (q = C_p pbar) with ordinary
         // stores; order them before the copies that will refill it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -77,7 +77,14 @@ def test_lens_solve_operators_commute_with_the_mirror_at_full_size(ssx):
         y = op(x).clone()
         ym = op(flip(x).contiguous())
         assert float(y.norm()) > 0, k
-        assert float((flip(y) - ym).norm() / y.norm()) <= 1e-6, k
+        if k < 5:
+            # every term of every update is negated or kept exactly under the
+            # reflection, and each sum keeps its order: bit for bit
+            assert torch.equal(flip(y), ym), k
+        else:
+            # M^-1's scaling D = (1 + alpha |x - x_s|^2)^(-1/2) rounds |x - x_s|
+            # differently on the two sides
+            assert float((flip(y) - ym).norm() / y.norm()) <= 1e-12, k
     d0 = ctx.point_source_data(spec.x_d, spec.z_d, torch.as_tensor(W.ricker(spec), device="cuda"))
     d1 = d0 + 0.05 * float(d0.abs().max()) * d     # not symmetric by itself
     h1, hist1, _, _ = ctx.solve(d1, spec.alpha, 3, 0.0)
