@@ -257,6 +257,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
     const int G = gridDim.x;
     int j = 0, jn = 0;
     int tile = next_active(jobs, njobs, total, t, blockIdx.x, G, &j);
+    // end of sweep j's tiles: a next tile below it is in the same sweep, which
+    // steps in this launch, so the search can be skipped
+    int jend = tile < total ? __ldg(&jobs[j].job.tile_base) + __ldg(&jobs[j].job.tiles) : 0;
     // stall_tile (test hook, normally -1): that tile's copies are never issued,
     // so its wait must run out
     if (threadIdx.x == 0 && tile < total && tile != stall_tile)
@@ -264,8 +267,19 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
     unsigned parity = 0u;   // bit s: the phase stage s waits for next
     int s = 0, cur_job = -1;
     while (tile < total) {
-        const int nxt = next_active(jobs, njobs, total, t, tile + G, G, &jn);
-        // the other stage was last read before the previous tile's closing barrier
+        int nxt = tile + G;
+        if (nxt < jend) jn = j;
+        else nxt = next_active(jobs, njobs, total, t, nxt, G, &jn);
+        const bool ok = mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 2);
+            mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);   // its copies may still be in flight
+            return;
+        }
+        parity ^= 1u << s;
+        // every thread is past the previous tile: stage s ^ 1, svx, svz and
+        // the job are free (its writes to stage s ^ 1 were ordered before the
+        // async proxy by each thread's fence and this barrier)
         if (threadIdx.x == 0 && nxt < total && nxt != stall_tile)
             issue<TX, TZ>(jobs, jn, nxt, t, sm.st[s ^ 1], bar(s ^ 1));
         if (j != cur_job) {   // the sweep's arguments into shared memory
@@ -273,15 +287,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
             int *dst = reinterpret_cast<int *>(&sm.job);
             for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
             cur_job = j;
+            __syncthreads();
         }
-        const bool ok = mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) atomicExch(err, 2);
-            mbar_wait(bar(s), (parity >> s) & 1u, timeout_ns);   // copies still in flight
-            if (nxt < total && nxt != stall_tile) mbar_wait(bar(s ^ 1), (parity >> (s ^ 1)) & 1u, timeout_ns);
-            return;
-        }
-        parity ^= 1u << s;
         const Job &J = sm.job;
         const int st = t - J.offset, tl = tile - J.tile_base;
         const int odd = st & 1;
@@ -295,10 +302,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         tile_corner<TX, TZ>(J.tx_mul, J.tx_shift, J.tiles_x, tl, i0, k0);
         tma_tile<TX, TZ, NT>(J, io, i0, k0, sm.st[s], sm);
         // the transposed step rewrote stage s (q = C_p pbar) with ordinary
-        // stores; order them before the copies that will refill it
+        // stores; order them before the copies that will refill it (issued
+        // after the next tile's barrier)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();   // stage s, svx, svz and the job are free again
         tile = nxt;
+        if (jn != j && nxt < total) jend = __ldg(&jobs[jn].job.tile_base) + __ldg(&jobs[jn].job.tiles);
         j = jn;
         s ^= 1;
     }
