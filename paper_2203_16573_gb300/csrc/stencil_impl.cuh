@@ -623,6 +623,8 @@ struct StripThread {
 // thread's column.
 template <int R, int TX, int TZ, int NT, bool SP>
 struct GlobalIn {
+    // false: the forward step's p is staged by all threads of the CTA
+    static constexpr bool kStaged = false;
     const GridArgs &g;
     const StepIO &io;
     const int i0, k0, pitch;
@@ -693,7 +695,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
 #pragma unroll
     for (int q = 0; q < Q::NQZ; q++) rhz[q] = th.hz_kk[q] >= 0 ? in.hvz(th.hz_kk[q], i) : 0.0f;
     in.template stage<false>();
-    __syncthreads();
+    if (!In::kStaged) __syncthreads();   // p staged by all threads
     float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
 
     // own strip: v_z from a window down the column, v_x from the row

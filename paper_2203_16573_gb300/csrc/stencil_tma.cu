@@ -38,10 +38,10 @@ template <int TX, int TZ>
 struct TmaStage {
     static constexpr int PH = TZ + 4 * kR, PW = TX + 4 * kR;
     static constexpr int VXB = TX + 2 * kR, VZH = TZ + 2 * kR - 1;
-    alignas(128) float p[PH][PW];      // p (forward) or pbar (transposed); q = C_p pbar after staging
+    alignas(128) float p[PH][PW];      // p (forward) or pbar (transposed)
     alignas(128) float vx[TZ][VXB];    // v_x, x = i0-k .. i0+TX+k-1
     alignas(128) float vz[VZH][TX];    // v_z, rows k0-k .. k0+TZ+k-2
-    alignas(128) float k[PH][PW];      // kappa: [TZ][TX] at i0 (forward); C_p over the p box (transposed)
+    alignas(128) float k[PH][PW];      // kappa: [TZ][TX] at i0 (forward); C_p over the p box, then q = C_p pbar (transposed)
     static constexpr unsigned bytes(bool adj) {
         return (unsigned)(sizeof(float) * (PH * PW + TZ * VXB + VZH * TX + (adj ? PH * PW : TZ * TX)));
     }
@@ -112,6 +112,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 // Strip operands read from a stage (same interface as GlobalIn).
 template <int TX, int TZ, int NT, bool SP>
 struct TmaIn {
+    // true: the stage already holds the forward step's p, and every thread
+    // has waited on its barrier (the copies are visible to it)
+    static constexpr bool kStaged = true;
     using St = TmaStage<TX, TZ>;
     St &st;
     const GridArgs &g;
@@ -126,24 +129,26 @@ struct TmaIn {
     __device__ __forceinline__ float own_p(int j) const { return st.p[rs + j + 2 * kR][c + 2 * kR]; }
     __device__ __forceinline__ float hvx(int r, int jj) const { return st.vx[r][jj]; }
     __device__ __forceinline__ float hvz(int kk, int i) const { return st.vz[kk][i - i0]; }
-    // transposed step: q = C_p pbar in place over the box (C_p is 0 outside
-    // the grid), the per-point arithmetic of stage_p; every thread has its own
-    // pbar first
+    // transposed step: q = C_p pbar over the box, written over C_p (which
+    // the step reads nowhere else; C_p is 0 outside the grid), the per-point
+    // arithmetic of stage_p. Each element is read and written by one thread
+    // and pbar stays in place for the others' own values: no barrier first.
+    bool q_in_k = false;
     template <bool PRE>
     __device__ __forceinline__ void stage() {
         if (!PRE) return;
-        __syncthreads();
         constexpr int N = St::PH * St::PW;
 #pragma unroll
         for (int q = 0; q < (N + NT - 1) / NT; q++) {
             const int e = threadIdx.x + q * NT;
             if (e < N) {
                 const int r = e / St::PW, x = e % St::PW;
-                st.p[r][x] = __fmul_rn(st.k[r][x], st.p[r][x]);
+                st.k[r][x] = __fmul_rn(st.k[r][x], st.p[r][x]);
             }
         }
+        q_in_k = true;
     }
-    __device__ __forceinline__ float (&sp())[TZ + 4 * kR][TX + 4 * kR] { return st.p; }
+    __device__ __forceinline__ float (&sp())[TZ + 4 * kR][TX + 4 * kR] { return q_in_k ? st.k : st.p; }
 };
 
 template <int TX, int TZ, int NT>
@@ -301,9 +306,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         int i0, k0;
         tile_corner<TX, TZ>(J.tx_mul, J.tx_shift, J.tiles_x, tl, i0, k0);
         tma_tile<TX, TZ, NT>(J, io, i0, k0, sm.st[s], sm);
-        // the transposed step rewrote stage s (q = C_p pbar) with ordinary
-        // stores; order them before the copies that will refill it (issued
-        // after the next tile's barrier)
+        // the transposed step rewrote stage s (q = C_p pbar over C_p) with
+        // ordinary stores; order them before the copies that will refill it
+        // (issued after the next tile's barrier)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tile = nxt;
         if (jn != j && nxt < total) jend = __ldg(&jobs[jn].job.tile_base) + __ldg(&jobs[jn].job.tiles);
