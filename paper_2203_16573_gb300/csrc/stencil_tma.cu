@@ -10,9 +10,12 @@
 // stage, four 2-D TMA copies (cp.async.bulk.tensor) are already filling the
 // other with the operands of tile n+1 -- the p (or pbar) box with its 2k halo,
 // the v_x box with its k-wide column halo, the v_z box with its row halo and
-// the kappa box -- and signal an mbarrier with their byte count. One thread
-// issues the copies; the address arithmetic of the loads disappears from the
-// other threads. The per-point arithmetic is that of the column-strip tiles
+// the kappa box (in the transposed step the C_p box over the p box, which the
+// step overwrites with q = C_p pbar) -- and signal an mbarrier with their byte
+// count. One thread issues the copies, right after the barrier that follows
+// the wait for tile n (every thread has then left tile n-1, whose stage they
+// refill); the address arithmetic of the loads disappears from the other
+// threads. The per-point arithmetic is that of the column-strip tiles
 // (fwd_strip / adj_strip, the same functions, fed from the stage), so results
 // are identical to every other tile configuration's.
 //
