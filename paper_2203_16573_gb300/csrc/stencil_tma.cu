@@ -101,6 +101,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
         if (globaltimer() - t0 > timeout_ns) return false;
     return true;
 }
+// fetch a tensor map into the descriptor cache ahead of its first copy (a hint)
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(map)) : "memory");
+}
 // 2-D tile copy global -> shared, completion counted on the mbarrier
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             unsigned bar) {
@@ -259,21 +263,32 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         mbar_init(bar(1), 1);
         mbar_init_fence();
     }
-    __syncthreads();
-    griddep_wait();   // the previous step's fields are complete
 
+    // The tile walk, the first sweep's arguments and its tensor maps depend
+    // on nothing the previous step writes: under programmatic dependent
+    // launch they are fetched while that step finishes.
     const int G = gridDim.x;
     int j = 0, jn = 0;
     int tile = next_active(jobs, njobs, total, t, blockIdx.x, G, &j);
     // end of sweep j's tiles: a next tile below it is in the same sweep, which
     // steps in this launch, so the search can be skipped
     int jend = tile < total ? __ldg(&jobs[j].job.tile_base) + __ldg(&jobs[j].job.tiles) : 0;
+    int cur_job = -1;
+    if (tile < total) {
+        const int *src = reinterpret_cast<const int *>(&jobs[j].job);
+        int *dst = reinterpret_cast<int *>(&sm.job);
+        for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+        cur_job = j;
+        if (threadIdx.x < 7) prefetch_map(&jobs[j].map[threadIdx.x]);
+    }
+    __syncthreads();   // barriers initialised, sweep arguments in place
+    griddep_wait();    // the previous step's fields are complete
     // stall_tile (test hook, normally -1): that tile's copies are never issued,
     // so its wait must run out
     if (threadIdx.x == 0 && tile < total && tile != stall_tile)
         issue<TX, TZ>(jobs, j, tile, t, sm.st[0], bar(0));
     unsigned parity = 0u;   // bit s: the phase stage s waits for next
-    int s = 0, cur_job = -1;
+    int s = 0;
     while (tile < total) {
         int nxt = tile + G;
         if (nxt < jend) jn = j;
