@@ -265,24 +265,34 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
     }
 
     // The tile walk, the first sweep's arguments and its tensor maps depend
-    // on nothing the previous step writes: under programmatic dependent
-    // launch they are fetched while that step finishes.
+    // on nothing the previous step writes. In a launch whose CTAs have one
+    // tile each (a short, latency-bound step) they are fetched before the
+    // grid dependency wait, while that step finishes under programmatic
+    // dependent launch; a CTA with many tiles waits first and starts its
+    // first copies as soon as it can.
     const int G = gridDim.x;
+    const bool one_tile = total <= G;
+    if (!one_tile) {
+        __syncthreads();   // barriers initialised
+        griddep_wait();    // the previous step's fields are complete
+    }
     int j = 0, jn = 0;
     int tile = next_active(jobs, njobs, total, t, blockIdx.x, G, &j);
     // end of sweep j's tiles: a next tile below it is in the same sweep, which
     // steps in this launch, so the search can be skipped
     int jend = tile < total ? __ldg(&jobs[j].job.tile_base) + __ldg(&jobs[j].job.tiles) : 0;
     int cur_job = -1;
-    if (tile < total) {
-        const int *src = reinterpret_cast<const int *>(&jobs[j].job);
-        int *dst = reinterpret_cast<int *>(&sm.job);
-        for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
-        cur_job = j;
-        if (threadIdx.x < 7) prefetch_map(&jobs[j].map[threadIdx.x]);
+    if (one_tile) {
+        if (tile < total) {
+            const int *src = reinterpret_cast<const int *>(&jobs[j].job);
+            int *dst = reinterpret_cast<int *>(&sm.job);
+            for (int w = threadIdx.x; w < (int)(sizeof(Job) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+            cur_job = j;
+            if (threadIdx.x < 7) prefetch_map(&jobs[j].map[threadIdx.x]);
+        }
+        __syncthreads();   // barriers initialised, sweep arguments in place
+        griddep_wait();    // the previous step's fields are complete
     }
-    __syncthreads();   // barriers initialised, sweep arguments in place
-    griddep_wait();    // the previous step's fields are complete
     // stall_tile (test hook, normally -1): that tile's copies are never issued,
     // so its wait must run out
     if (threadIdx.x == 0 && tile < total && tile != stall_tile)
