@@ -75,3 +75,30 @@ def test_oracle_shares_no_code_with_the_library():
         if f.endswith((".py", ".c")):
             t = open(os.path.join(ROOT, "oracle", f)).read()
             assert "import paper_2203_16573_gb300" not in t and "libssx.so" not in t, f
+
+
+def test_every_entry_point_rejects_a_null_handle_without_touching_the_device(lib):
+    """Each call on a context or server, and each call with only null
+    buffers, returns SSX_ERR_ARG (1) before any CUDA work: the checks of the
+    boundary's error behaviour that need no GPU."""
+    import ctypes as C
+    skip = {"ssx_version", "ssx_last_error", "ssx_server_last_error"}
+    from paper_2203_16573_gb300 import ssx
+    checked = []
+    for name in ssx.EXPORTS:
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (C.c_int, C.c_size_t):
+                args.append(0)
+            elif t is C.c_double:
+                args.append(0.0)
+            else:
+                args.append(None)       # null handle, descriptor or buffer
+        assert fn(*args) == 1, name
+        checked.append(name)
+    assert len(checked) == len(ssx.EXPORTS) - len(skip)
+    assert lib.ssx_last_error(None) == b"null context"
+    assert lib.ssx_server_last_error(None) == b"null server"
