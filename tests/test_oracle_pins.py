@@ -110,6 +110,45 @@ def test_point_source_dot_product(oracle):
     assert abs(a - b) <= 1e-12 * abs(a)
 
 
+
+def test_lines_between_rows_interpolate_linearly_in_depth(oracle):
+    """Trace sampling and source injection interpolate linearly in z: p lives
+    on rows at k h and v_z on rows at (k + 1/2) h. So a pressure line at depth
+    (k + 0.3) h is 0.7 x the line on row k plus 0.3 x the line on row k + 1,
+    and a v_z line at the p-row depth k h is the mean of the v_z lines at
+    (k - 1/2) h and (k + 1/2) h. Swapped weights, or a v_z line placed on the
+    p rows, fails this. The dot tests cannot see either mistake, since each
+    keeps injection and sampling transposes of one another."""
+    g, _, _ = _grid_with_lines(oracle, 4, nsp=6)
+    h, nt, k = 0.01, 40, 9
+    rng = np.random.default_rng(11)
+    hs = rng.standard_normal((nt, 21))
+    fs = rng.standard_normal((nt, 21))
+
+    def traces(z_src, z_rec, **kw):
+        return oracle.simulate(g, nt, g.line(z_src, 3, 21), g.line(z_rec, 1, 25), want_v=True, **kw)
+
+    def close(a, b):
+        return np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+    # pressure injection between rows
+    a = traces((k + 0.3) * h, 0.05, h=hs)[0]
+    b = 0.7 * traces(k * h, 0.05, h=hs)[0] + 0.3 * traces((k + 1) * h, 0.05, h=hs)[0]
+    assert close(a, b)
+    # pressure and v_z sampling between rows
+    pa, va = traces(k * h, 0.043, h=hs)
+    p0, v0 = traces(k * h, 0.04, h=hs)
+    p1, v1 = traces(k * h, 0.05, h=hs)
+    assert close(pa, 0.7 * p0 + 0.3 * p1)
+    vlo = traces(k * h, 0.035, h=hs)[1]            # v_z row at 0.035 = (3 + 1/2) h
+    vhi = traces(k * h, 0.045, h=hs)[1]            # v_z row at 0.045
+    assert close(v0, 0.5 * vlo + 0.5 * vhi)
+    # v_z (velocity) injection on a p-row depth: mean of the two v_z rows
+    fa = traces(k * h, 0.05, f=fs)[0]
+    flo = traces((k - 0.5) * h, 0.05, f=fs)[0]
+    fhi = traces((k + 0.5) * h, 0.05, f=fs)[0]
+    assert close(fa, 0.5 * flo + 0.5 * fhi)
+    assert np.linalg.norm(fa) > 0 and np.linalg.norm(pa) > 0
+
 # ------------------------------------------------------------------ energy --
 @pytest.mark.parametrize("order", [4, 8])
 def test_leapfrog_energy_is_conserved_without_sponge(oracle, order):
