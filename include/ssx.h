@@ -170,8 +170,8 @@ int ssx_normal_apply(ssx_ctx *ctx, int mode, double alpha, const double *p_dev, 
  * d_dev [nt][n_rec] in; h_out_dev [nt][n_line] out (device).
  * resid_hist_host (host, maxit + 1 doubles, may be NULL) receives ||r_k||_2;
  * iters_out (host, may be NULL) the number of updates made. Krylov vectors,
- * scalars and reductions are float64 on the device; one 16-byte device-to-host
- * read per iteration decides the stop. Returns SSX_ERR_NOT_CONVERGED if maxit
+ * scalars and reductions are float64 on the device; one 56-byte device-to-host
+ * read per iteration (the 7 Krylov scalars) decides the stop. Returns SSX_ERR_NOT_CONVERGED if maxit
  * was reached above rtol (h_out is still the last iterate), SSX_ERR_BREAKDOWN
  * if <p_k,q_k> <= 0 or <g_k,r_k> <= 0 (h_out holds the last good iterate). */
 int ssx_solve_source_subproblem(ssx_ctx *ctx, const double *d_dev, double alpha,
@@ -272,9 +272,29 @@ int ssx_point_source_data(ssx_ctx *ctx, double x_d, double z_d,
  *   0.2 s; or, if the next multi-sweep phase runs on the TMA-staged kernel,
  *   the copies of its first tile in its first step are never issued, so that
  *   CTA's mbarrier wait runs out after 0.2 s. Either way the timeout path is
- *   exercised without a fault, and the call returns SSX_ERR_CUDA. */
+ *   exercised without a fault, and the call returns SSX_ERR_CUDA.
+ * After a wait that timed out for a real reason (not the test hook), treat
+ * the context as unusable and destroy it: a CTA that gave up on tensor copies
+ * which were merely slow waits once more (bounded) and then leaves, and copies
+ * still in flight after that would land in shared memory the CTA no longer
+ * owns, so the context's fields and captured graphs are no longer trusted.
+ * The test hook withholds the copies entirely, which is why its context
+ * stays usable. */
 enum { SSX_SWEEP_AUTO = 0, SSX_SWEEP_STEP = 1, SSX_SWEEP_PERSISTENT = 2, SSX_SWEEP_TEST_STALL = 3 };
 int ssx_set_sweep_mode(ssx_ctx *ctx, int mode);
+
+/* Failure injection for tests, on the host-visible scalar path (no GPU
+ * fault): in the next solve on this context (ssx_solve_source_subproblem, or
+ * this context's shot in ssx_solve_batch / a server), the curvature
+ * <p_k, q_k> of iteration k is overwritten on the device right after it is
+ * formed, before alpha_k: with 0 (SSX_HOOK_BREAKDOWN), so Algorithm 1's
+ * breakdown test fires and the solve returns SSX_ERR_BREAKDOWN; or with a NaN
+ * (SSX_HOOK_NONFINITE), so it returns SSX_ERR_NONFINITE. Either way h_out then
+ * holds h_k, the last good iterate, and k updates are reported. The hook
+ * fires once. SSX_HOOK_NONE clears it. SSX_ERR_ARG for an unknown hook or
+ * k < 0. */
+enum { SSX_HOOK_NONE = 0, SSX_HOOK_BREAKDOWN = 1, SSX_HOOK_NONFINITE = 2 };
+int ssx_set_test_hook(ssx_ctx *ctx, int hook, int k);
 
 /* Tile configuration of the step kernels: -1 (default) lets the library time
  * every configuration on each grid's first sweep in each direction and keep
@@ -310,15 +330,17 @@ int ssx_reset_stats(ssx_ctx *ctx);
  * gather h_dev [nt][n_line] and the output d_dev [nt][n_rec] (float64,
  * device); no context is needed. All scratch (padded kappa field, two
  * ping-pong wavefield triples, sponge tables, the model maximum) lives in
- * one file-scope device array of SSX_NOALLOC_MAX_FLOATS floats that every
- * GPU loading the library holds until the process exits. Nothing is
- * allocated or freed.
+ * one file-scope device array of SSX_NOALLOC_MAX_FLOATS floats. A GPU
+ * reserves the array when the library's module is first used on it (with
+ * CUDA's lazy module loading that can be inside this call's first use) and
+ * holds it until the process exits. Nothing is allocated or freed.
  *
  * The grid must fit: 7 P Q + 2 (nx + nz + 4 n_sponge) + 64 <= SSX_NOALLOC_MAX_FLOATS
  * with P = roundup(roundup(nx + 2 n_sponge, 128) + 64, 32) and
  * Q = roundup(nz + 2 n_sponge, 32) + 16 (the 601 x 301 grid with a
- * 40-point sponge uses 2.33 M floats); larger grids return SSX_ERR_ARG
- * before any device work. Other errors: SSX_ERR_ARG for invalid arguments,
+ * 40-point sponge uses 2.33 M floats); larger grids (including descriptors
+ * whose padded size overflows an int) return SSX_ERR_ARG before any device
+ * work. Results are bit-identical to ssx_forward's on the same inputs. Other errors: SSX_ERR_ARG for invalid arguments,
  * SSX_ERR_CFL, SSX_ERR_CUDA; there is no message string.
  *
  * The first call on a device looks up the array's device address with that

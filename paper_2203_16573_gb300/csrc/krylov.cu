@@ -6,8 +6,8 @@
 // reducing a fixed grid-stride slice with warp shuffles, then one block
 // summing the partials in a fixed tree order. The PCG scalars (alpha_k,
 // beta_k, <g,r>, <p,q>, ||r||^2) stay in device memory; kernels read them
-// from there, so an iteration needs no host round trip except the 16-byte
-// read that decides the stop.
+// from there, so an iteration needs no host round trip except the 56-byte
+// read of the scalar slots that decides the stop.
 #include "ssx_internal.cuh"
 
 namespace ssx {

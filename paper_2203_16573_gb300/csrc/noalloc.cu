@@ -8,10 +8,11 @@
 // work. ssx_forward_noalloc serves them: the caller passes the inputs and the
 // output buffer, and every piece of scratch the sweep needs -- the padded
 // kappa field, the two ping-pong wavefield triples, the sponge tables and the
-// model maximum -- lives in one file-scope device array of fixed size,
-// reserved when the library's module is loaded on a GPU and held by that GPU
-// until the process exits. No cudaMalloc, cudaFree, graph instantiation or
-// other allocating call is made.
+// model maximum -- lives in one file-scope device array of fixed size. The
+// array is reserved on a GPU when the library's module is first used there
+// (with CUDA's lazy module loading that may be inside the first call) and is
+// held by that GPU until the process exits. No cudaMalloc, cudaFree, graph
+// instantiation or other allocating call is made.
 //
 // The array is shared by every call on a device: its contents are the last
 // call's, so each call clears what must start at zero, and calls whose work
@@ -54,53 +55,6 @@ int scratch_address(float **out) {
     return SSX_OK;
 }
 
-int row_of(double zeta, int *k, float *w0, float *w1) {
-    const int kk = (int)std::floor(zeta + 1e-6);
-    double f = zeta - kk;
-    if (f < 1e-6) f = 0.0;
-    *k = kk;
-    *w0 = (float)(1.0 - f);
-    *w1 = (float)f;
-    return 0;
-}
-
-bool line_at(int NX, int NZ, int nx, int nsp, double h, double z, int ix0, int n, Line *L) {
-    const double zeta = z / h + nsp;
-    row_of(zeta, &L->kp, &L->wp0, &L->wp1);
-    row_of(zeta - 0.5, &L->kv, &L->wv0, &L->wv1);
-    if (!(L->kp >= 0 && L->kp + 1 < NZ && L->kv >= 0 && L->kv + 1 < NZ - 1)) return false;
-    if (ix0 < 0 || n < 1 || ix0 + n > nx) return false;
-    (void)NX;
-    L->i0 = ix0 + nsp;
-    L->n = n;
-    L->scale = 1.0f;
-    return true;
-}
-
-// sponge tables from the device-resident model maximum (no host round trip)
-__global__ void k_sponge_from_vmax(float *ti, float *th, int N, int n_phys, int nsp, double h,
-                                   double dt, const float *vmax) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double smax = nsp > 0 ? 3.0 * (double)*vmax * log(1000.0) / (2.0 * nsp * h) : 0.0;
-    for (int half = 0; half < 2; half++) {
-        const double pos = i + 0.5 * half;
-        const double d = fmax(0.0, fmax((double)nsp - pos, pos - (double)(nsp + n_phys - 1)));
-        const double s = nsp > 0 ? 0.5 * dt * smax * (d / nsp) * (d / nsp) : 0.0;
-        (half ? th : ti)[i] = (float)s;
-    }
-}
-
-const float kW[5][kMaxR] = {
-    {0.f, 0.f, 0.f, 0.f},
-    {1.0f, 0.f, 0.f, 0.f},
-    {9.0f / 8.0f, -1.0f / 24.0f, 0.f, 0.f},
-    {75.0f / 64.0f, -25.0f / 384.0f, 3.0f / 640.0f, 0.f},
-    {1225.0f / 1024.0f, -245.0f / 3072.0f, 49.0f / 5120.0f, -5.0f / 7168.0f},
-};
-
-int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
-
 }  // namespace
 
 extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc *gm,
@@ -111,18 +65,18 @@ extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc 
         gd->n_sponge < 0 || gd->space_order < 2 || gd->space_order > 8 || gd->space_order % 2)
         return SSX_ERR_ARG;
     const int R = gd->space_order / 2, nsp = gd->n_sponge;
-    FieldLayout L{};
-    L.NX = gd->nx + 2 * nsp;
-    L.NZ = gd->nz + 2 * nsp;
-    L.pitch = round_up_i(round_up_i(L.NX, TILE_X_MAX) + 2 * GX, 32);
-    L.rows = round_up_i(L.NZ, TILE_Z_MAX) + 2 * GZ;
+    // the padded grid alone must fit the scratch: checked in 64-bit arithmetic
+    // before any int layout arithmetic can overflow
+    const long long NXl = (long long)gd->nx + 2LL * nsp, NZl = (long long)gd->nz + 2LL * nsp;
+    if (NXl * NZl > (long long)kScratchFloats) return SSX_ERR_ARG;
+    const FieldLayout L = field_layout((int)NXl, (int)NZl);
     const size_t E = L.elems();
     const size_t tab = 2 * (size_t)(L.NX + L.NZ);
     const size_t need = 7 * E + tab + 64;
     if (need > kScratchFloats) return SSX_ERR_ARG;   // grid larger than the fixed scratch
     Line src{}, rec{};
-    if (!line_at(L.NX, L.NZ, gd->nx, nsp, gd->h, gm->z_s, gm->ix_line0, gm->n_line, &src) ||
-        !line_at(L.NX, L.NZ, gd->nx, nsp, gd->h, gm->z_r, gm->ix_rec0, gm->n_rec, &rec))
+    if (line_at(gm->z_s / gd->h + nsp, L.NZ, gd->nx, nsp, gm->ix_line0, gm->n_line, 1.0, &src) ||
+        line_at(gm->z_r / gd->h + nsp, L.NZ, gd->nx, nsp, gm->ix_rec0, gm->n_rec, 1.0, &rec))
         return SSX_ERR_ARG;
 
     float *base = nullptr;
@@ -144,21 +98,19 @@ extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc 
     if (cudaMemcpyAsync(&vm, vmax, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return SSX_ERR_CUDA;
-    double asum = 0.0;
-    for (int m = 0; m < R; m++) asum += std::fabs((double)kW[R][m]);
     if (!(vm > 0) || !std::isfinite(vm)) return SSX_ERR_ARG;
-    if (!(vm * gd->dt / gd->h * std::sqrt(2.0) * asum < 1.0)) return SSX_ERR_CFL;
+    if (!(vm * gd->dt / gd->h * std::sqrt(2.0) * kWeightsAbsSum[R] < 1.0)) return SSX_ERR_CFL;
 
     float *kap = kap_mem + L.origin();
     if (launch_fill_kappa(kap, L, v_dev, gd->nx, gd->nz, nsp, 0, rho, gd->dt / gd->h, s) !=
         cudaSuccess)
         return SSX_ERR_CUDA;
-    k_sponge_from_vmax<<<(L.NX + 127) / 128, 128, 0, s>>>(tabs, tabs + L.NX, L.NX, gd->nx, nsp,
-                                                          gd->h, gd->dt, vmax);
-    k_sponge_from_vmax<<<(L.NZ + 127) / 128, 128, 0, s>>>(tabs + 2 * L.NX,
-                                                          tabs + 2 * L.NX + L.NZ, L.NZ, gd->nz,
-                                                          nsp, gd->h, gd->dt, vmax);
-    if (cudaGetLastError() != cudaSuccess) return SSX_ERR_CUDA;
+    // the sponge tables of a context's grid: same scale from the same maximum
+    const double sdt = sponge_scale(vm, nsp, gd->h, gd->dt);
+    if (launch_sponge_table(tabs, tabs + L.NX, L.NX, gd->nx, nsp, sdt, s) != cudaSuccess ||
+        launch_sponge_table(tabs + 2 * L.NX, tabs + 2 * L.NX + L.NZ, L.NZ, gd->nz, nsp, sdt, s) !=
+            cudaSuccess)
+        return SSX_ERR_CUDA;
 
     FwdArgs a{};
     GridArgs &g = a.g;
@@ -171,7 +123,7 @@ extern "C" int ssx_forward_noalloc(const ssx_grid_desc *gd, const ssx_geom_desc 
     g.szi = tabs + 2 * L.NX;
     g.szh = tabs + 2 * L.NX + L.NZ;
     g.cv = (float)(gd->dt / (rho * gd->h));
-    for (int m = 0; m < kMaxR; m++) g.c[m] = kW[R][m];
+    for (int m = 0; m < kMaxR; m++) g.c[m] = kWeights[R][m];
     g.in_x0 = nsp;
     g.in_x1 = nsp + gd->nx - 1;
     g.in_z0 = nsp;

@@ -45,18 +45,6 @@ using namespace ssx;
 
 namespace {
 
-// staggered first-derivative weights of order 2k (Taylor values)
-const float kWeights[5][kMaxR] = {
-    {0.f, 0.f, 0.f, 0.f},
-    {1.0f, 0.f, 0.f, 0.f},
-    {9.0f / 8.0f, -1.0f / 24.0f, 0.f, 0.f},
-    {75.0f / 64.0f, -25.0f / 384.0f, 3.0f / 640.0f, 0.f},
-    {1225.0f / 1024.0f, -245.0f / 3072.0f, 49.0f / 5120.0f, -5.0f / 7168.0f},
-};
-const double kWeightsAbsSum[5] = {0.0, 1.0, 9.0 / 8 + 1.0 / 24,
-                                  75.0 / 64 + 25.0 / 384 + 3.0 / 640,
-                                  1225.0 / 1024 + 245.0 / 3072 + 49.0 / 5120 + 5.0 / 7168};
-
 struct DGrid {
     FieldLayout L{};
     int nx = 0, nz = 0;       // physical points of this grid
@@ -143,6 +131,8 @@ struct ssx_ctx {
     int tma_cap[kNumTileCfgs];        // co-resident CTAs of the TMA-staged phase kernel (-1: unknown)
     int forced_cfg = -1;              // tile configuration fixed by the caller (-1: autotune)
     bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
+    int hook = SSX_HOOK_NONE;         // test hook of ssx_set_test_hook and its iteration
+    int hook_k = -1;
     bool use_graphs = true;
     bool log_tuning = false;          // SSX_LOG_TUNING=1: print the phase tuner's timings
     std::unordered_map<std::string, cudaGraphExec_t> graphs;
@@ -184,11 +174,8 @@ int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) 
     G.nz = nz;
     G.row0 = row0;
     G.z_origin = z_origin;
-    FieldLayout &L = G.L;
-    L.NX = nx + 2 * nsp;
-    L.NZ = nz + 2 * nsp;
-    L.pitch = round_up(round_up(L.NX, TILE_X_MAX) + 2 * GX, 32);
-    L.rows = round_up(L.NZ, TILE_Z_MAX) + 2 * GZ;
+    G.L = field_layout(nx + 2 * nsp, nz + 2 * nsp);
+    const FieldLayout &L = G.L;
     const size_t E = L.elems();
     if (G.mem) cudaFree(G.mem);
     if (G.tab) cudaFree(G.tab);
@@ -270,40 +257,22 @@ int grid_fill(ssx_ctx *c, DGrid &G) {
     const ssx_grid_desc &d = c->gd;
     const int nsp = d.n_sponge;
     CK(launch_fill_kappa(G.kap, G.L, c->vel, d.nx, d.nz, nsp, G.row0, c->rho, d.dt / d.h, c->s));
-    const double smax = nsp > 0 ? 3.0 * c->v_max * std::log(1000.0) / (2.0 * nsp * d.h) : 0.0;
-    CK(launch_sponge_table(G.tab, G.tab + G.L.NX, G.L.NX, G.nx, nsp, smax * d.dt * 0.5, c->s));
+    const double sdt = sponge_scale(c->v_max, nsp, d.h, d.dt);
+    CK(launch_sponge_table(G.tab, G.tab + G.L.NX, G.L.NX, G.nx, nsp, sdt, c->s));
     CK(launch_sponge_table(G.tab + 2 * G.L.NX, G.tab + 2 * G.L.NX + G.L.NZ, G.L.NZ, G.nz, nsp,
-                           smax * d.dt * 0.5, c->s));
+                           sdt, c->s));
     G.args.cv = (float)(d.dt / (c->rho * d.h));
     CK(launch_fill_cpk(G.args, G.L, G.mem + 7 * G.L.elems(), c->s));
     G.ready = true;
     return SSX_OK;
 }
 
-// linear-interpolation weights at fractional row coordinate zeta
-void row_weights(double zeta, int *k, float *w0, float *w1) {
-    const int kk = (int)std::floor(zeta + 1e-6);
-    double f = zeta - kk;
-    if (f < 1e-6) f = 0.0;
-    *k = kk;
-    *w0 = (float)(1.0 - f);
-    *w1 = (float)f;
-}
-
 int make_line(ssx_ctx *c, const DGrid &G, double z, int ix0, int n, double scale, Line *out) {
     const int nsp = c->gd.n_sponge;
     const double zeta = (z - G.z_origin) / c->gd.h + nsp;
-    Line L{};
-    row_weights(zeta, &L.kp, &L.wp0, &L.wp1);
-    row_weights(zeta - 0.5, &L.kv, &L.wv0, &L.wv1);
-    if (!(L.kp >= 0 && L.kp + 1 < G.L.NZ && L.kv >= 0 && L.kv + 1 < G.L.NZ - 1))
-        return fail(c, SSX_ERR_ARG, "line depth outside the grid");
-    if (ix0 < 0 || n < 1 || ix0 + n > G.nx)
-        return fail(c, SSX_ERR_ARG, "line columns outside the physical grid");
-    L.i0 = ix0 + nsp;
-    L.n = n;
-    L.scale = (float)scale;
-    *out = L;
+    const int rc = line_at(zeta, G.L.NZ, G.nx, nsp, ix0, n, scale, out);
+    if (rc == 1) return fail(c, SSX_ERR_ARG, "line depth outside the grid");
+    if (rc == 2) return fail(c, SSX_ERR_ARG, "line columns outside the physical grid");
     return SSX_OK;
 }
 
@@ -1222,6 +1191,12 @@ int engine_round(ssx_ctx *L, std::vector<ShotRun *> &shots) {
         if (sh.state == ShotRun::ITER) {
             double *sc = sh.c->sc;
             CK(launch_dot(sh.c->p, sh.c->q, nl(sh), sh.c->partials, sc + SC_PQ, s));
+            if (sh.c->hook != SSX_HOOK_NONE && sh.c->hook_k == sh.iters) {
+                // test hook: <p_k, q_k> replaced (0, or a NaN pattern) before alpha_k
+                CK(cudaMemsetAsync(sc + SC_PQ, sh.c->hook == SSX_HOOK_BREAKDOWN ? 0 : 0xff,
+                                   sizeof(double), s));
+                sh.c->hook = SSX_HOOK_NONE;
+            }
             CK(launch_pcg_alpha(sc, s));
             CK(launch_pcg_update(sh.c->h, sh.c->r, sh.c->p, sh.c->q, nl(sh), sc, sh.c->partials, s));
             L->st.kernel_launches += 5;
@@ -1997,6 +1972,16 @@ int ssx_set_sweep_mode(ssx_ctx *c, int mode) {
         return fail(c, SSX_ERR_ARG, "unknown sweep mode");
     c->sweep_mode = mode;
     reset_choices(c);
+    return SSX_OK;
+}
+
+int ssx_set_test_hook(ssx_ctx *c, int hook, int k) {
+    if (!c) return SSX_ERR_ARG;
+    if (hook != SSX_HOOK_NONE && hook != SSX_HOOK_BREAKDOWN && hook != SSX_HOOK_NONFINITE)
+        return fail(c, SSX_ERR_ARG, "unknown test hook");
+    if (hook != SSX_HOOK_NONE && k < 0) return fail(c, SSX_ERR_ARG, "hook iteration must be >= 0");
+    c->hook = hook;
+    c->hook_k = k;
     return SSX_OK;
 }
 

@@ -41,6 +41,28 @@ struct Line {
     float scale;
 };
 
+// Staggered first-derivative weights c_1..c_k of order 2k (the Taylor values;
+// row k, zero-padded) and their absolute sums (CFL bound).
+extern const float kWeights[5][kMaxR];
+extern const double kWeightsAbsSum[5];
+
+// Storage layout of a padded grid of NX x NZ points (apron, pitch, rows).
+FieldLayout field_layout(int NX, int NZ);
+
+// Linear-interpolation weights at fractional padded-row coordinate zeta:
+// rows k and k+1 with weights w0 = 1 - f, w1 = f (f < 1e-6 taken as 0).
+void row_weights(double zeta, int *k, float *w0, float *w1);
+
+// Line struct of a line at padded-row coordinate zeta (pressure rows) over
+// physical columns ix0 .. ix0+n-1 of a grid of NZ padded rows, nx physical
+// columns and nsp sponge points: 0 = ok, 1 = depth outside the grid,
+// 2 = columns outside the physical grid.
+int line_at(double zeta, int NZ, int nx, int nsp, int ix0, int n, double scale, Line *out);
+
+// sigma_max dt / 2 of the sponge, sigma_max = 3 v_max ln(1000) / (2 nsp h)
+// (0 without a sponge): the scale the sponge tables are filled with.
+double sponge_scale(double v_max, int nsp, double h, double dt);
+
 // Per-grid constant inputs of a step.
 struct GridArgs {
     int NX, NZ, pitch;

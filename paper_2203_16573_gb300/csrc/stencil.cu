@@ -2,6 +2,8 @@
 // maximum), the adjoint sweep's initial injection, and the dispatch of the
 // step kernels (stencil_impl.cuh, instantiated per half order R in
 // stencil_r<R>.cu) over R and the tile configurations.
+#include <cmath>
+
 #include "stencil_impl.cuh"
 
 namespace ssx {
@@ -87,6 +89,54 @@ __global__ void k_vmax(const float *v, int n, float *out) {
 }
 
 }  // namespace
+
+const float kWeights[5][kMaxR] = {
+    {0.f, 0.f, 0.f, 0.f},
+    {1.0f, 0.f, 0.f, 0.f},
+    {9.0f / 8.0f, -1.0f / 24.0f, 0.f, 0.f},
+    {75.0f / 64.0f, -25.0f / 384.0f, 3.0f / 640.0f, 0.f},
+    {1225.0f / 1024.0f, -245.0f / 3072.0f, 49.0f / 5120.0f, -5.0f / 7168.0f},
+};
+const double kWeightsAbsSum[5] = {0.0, 1.0, 9.0 / 8 + 1.0 / 24,
+                                  75.0 / 64 + 25.0 / 384 + 3.0 / 640,
+                                  1225.0 / 1024 + 245.0 / 3072 + 49.0 / 5120 + 5.0 / 7168};
+
+FieldLayout field_layout(int NX, int NZ) {
+    auto up = [](int a, int b) { return (a + b - 1) / b * b; };
+    FieldLayout L{};
+    L.NX = NX;
+    L.NZ = NZ;
+    L.pitch = up(up(NX, TILE_X_MAX) + 2 * GX, 32);
+    L.rows = up(NZ, TILE_Z_MAX) + 2 * GZ;
+    return L;
+}
+
+void row_weights(double zeta, int *k, float *w0, float *w1) {
+    const int kk = (int)std::floor(zeta + 1e-6);
+    double f = zeta - kk;
+    if (f < 1e-6) f = 0.0;
+    *k = kk;
+    *w0 = (float)(1.0 - f);
+    *w1 = (float)f;
+}
+
+int line_at(double zeta, int NZ, int nx, int nsp, int ix0, int n, double scale, Line *out) {
+    Line L{};
+    row_weights(zeta, &L.kp, &L.wp0, &L.wp1);
+    row_weights(zeta - 0.5, &L.kv, &L.wv0, &L.wv1);
+    if (!(L.kp >= 0 && L.kp + 1 < NZ && L.kv >= 0 && L.kv + 1 < NZ - 1)) return 1;
+    if (ix0 < 0 || n < 1 || ix0 > nx - n) return 2;
+    L.i0 = ix0 + nsp;
+    L.n = n;
+    L.scale = (float)scale;
+    *out = L;
+    return 0;
+}
+
+double sponge_scale(double v_max, int nsp, double h, double dt) {
+    const double smax = nsp > 0 ? 3.0 * v_max * std::log(1000.0) / (2.0 * nsp * h) : 0.0;
+    return smax * dt * 0.5;
+}
 
 const TileCfg kTileCfgs[kNumTileCfgs] = {
 #define SSX_CFG_ROW(id, TX, TZ, NT) {TX, TZ, NT},

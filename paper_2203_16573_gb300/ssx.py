@@ -21,6 +21,7 @@ STATUS = {0: "SSX_OK", 1: "SSX_ERR_ARG", 2: "SSX_ERR_CUDA", 3: "SSX_ERR_CFL", 4:
 MODE_PCG, MODE_CG = 0, 1
 SWEEP_AUTO, SWEEP_STEP, SWEEP_PERSISTENT, SWEEP_TEST_STALL = 0, 1, 2, 3
 W_D, W_M, W_M_INV = 0, 1, 2
+HOOK_NONE, HOOK_BREAKDOWN, HOOK_NONFINITE = 0, 1, 2
 
 # every symbol the header declares, in declaration order
 N_TILE_CONFIGS = 8    # SSX_NUM_TILE_CONFIGS of include/ssx.h
@@ -33,7 +34,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
            "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
-           "ssx_velocity_gradient", "ssx_last_objective"]
+           "ssx_velocity_gradient", "ssx_last_objective", "ssx_set_test_hook"]
 
 
 class SSXError(RuntimeError):
@@ -110,6 +111,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_server_last_error": ([vp], ctypes.c_char_p),
         "ssx_velocity_gradient": ([vp, vp, vp, d, i, vp, P(d)], i),
         "ssx_last_objective": ([vp, P(d)], i),
+        "ssx_set_test_hook": ([vp, i, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -257,15 +259,20 @@ class Context:
         self._check(self._lib.ssx_last_objective(self._c, ctypes.byref(obj)))
         return obj.value
 
-    def solve(self, d, alpha, maxit, rtol, mode=MODE_PCG, out=None, allow_not_converged=True):
-        """Algorithm 1. Returns (h, residual history (numpy), iterations, status)."""
+    def solve(self, d, alpha, maxit, rtol, mode=MODE_PCG, out=None, allow_not_converged=True,
+              allow_breakdown=False):
+        """Algorithm 1. Returns (h, residual history (numpy), iterations, status).
+        SSX_ERR_NOT_CONVERGED is returned as a status unless allow_not_converged
+        is False; SSX_ERR_BREAKDOWN and SSX_ERR_NONFINITE raise unless
+        allow_breakdown is True (h then holds the last good iterate)."""
         out = self._empty(self.n_line) if out is None else out
         hist = (ctypes.c_double * (maxit + 1))()
         iters = ctypes.c_int(0)
         rc = self._lib.ssx_solve_source_subproblem(self._c, self._rec(d, "d"), float(alpha),
                                                    int(maxit), float(rtol), int(mode),
                                                    self._line(out, "h"), hist, ctypes.byref(iters))
-        if rc != SSX_OK and not (allow_not_converged and rc == 7):
+        if rc != SSX_OK and not ((allow_not_converged and rc == 7) or
+                                 (allow_breakdown and rc in (5, 6))):
             self._check(rc)
         k = iters.value
         return out, np.array(hist[: k + 1]), k, STATUS[rc]
@@ -279,6 +286,10 @@ class Context:
 
     def set_sweep_mode(self, mode: int):
         self._check(self._lib.ssx_set_sweep_mode(self._c, int(mode)))
+
+    def set_test_hook(self, hook: int, k: int = 0):
+        """Failure injection of the next solve (ssx_set_test_hook)."""
+        self._check(self._lib.ssx_set_test_hook(self._c, int(hook), int(k)))
 
     def set_tile_config(self, cfg: int):
         self._check(self._lib.ssx_set_tile_config(self._c, int(cfg)))

@@ -120,7 +120,9 @@ def _check_solve(ctx, P, spec, d, mode, maxit, rtol):
     h_or, hist_or = oracle_pcg(P, d, spec.alpha, maxit, rtol, mode)
     h_gpu, hist_gpu, iters, status = ctx.solve(dev(d), spec.alpha, maxit, rtol, m)
     assert iters == len(hist_or) - 1, (iters, len(hist_or))
-    np.testing.assert_array_less(np.abs(hist_gpu - hist_or) / hist_or, HIST_TOL)
+    herr = np.abs(hist_gpu - hist_or) / hist_or
+    print(f"\nsolve parity: h rel L2 {rel(h_gpu, h_or):.3e}, history max rel {herr.max():.3e}")
+    np.testing.assert_array_less(herr, HIST_TOL)
     assert rel(h_gpu, h_or) <= TOL
     return h_gpu, hist_gpu, status
 
@@ -149,18 +151,23 @@ def test_config1_solve_parity(ssx, oracle):
     _check_solve(ctx, P, spec, d, "pcg", spec.maxit, spec.rtol)
 
 
-def test_config2_full_size_sampled(ssx, oracle):
-    """Full 601 x 301, order 8, 3000-step lens workload at the bench's launch
-    configuration: the data gather and the first residual r_0 = S^T W~_d d
-    against the oracle, plus the dot-product test."""
+def test_config2_full_solve_parity(ssx, oracle):
+    """The bench's workload, solved as the bench solves it: full 601 x 301,
+    order 8, 3000-step lens model, 30 preconditioned CG iterations with the
+    tile configurations the autotuner picks per phase. Against the oracle:
+    the data gather, r_0 = S^T W~_d d as a gather (element by element), the
+    whole residual history (1e-3 per entry) and the recovered source h
+    (1e-4 relative L2); then the FP32 dot-product test at this size."""
     spec = W.c2()
     ctx, P = make(ssx, oracle, spec)
     w = W.ricker(spec)
     d = P.point_source_data(w, spec.x_d, spec.z_d)
     assert rel(ctx.point_source_data(spec.x_d, spec.z_d, dev(w)), d) <= TOL
     r0 = P.rhs(d)
-    _, hist, iters, _ = ctx.solve(dev(d), spec.alpha, 0, spec.rtol)
-    assert iters == 0 and abs(hist[0] - np.linalg.norm(r0)) <= TOL * np.linalg.norm(r0)
+    assert rel(ctx.adjoint(ctx.weight_apply(ssx.W_D, dev(d))), r0) <= TOL
+    h_gpu, hist_gpu, status = _check_solve(ctx, P, spec, d, "pcg", spec.maxit, spec.rtol)
+    print(f"\nc2 solve: {len(hist_gpu) - 1} iterations, status {status}, "
+          f"final relative residual {hist_gpu[-1] / hist_gpu[0]:.4e}")
     h = dev(W.random_gather(spec.nt, spec.n_line, 8))
     y = dev(W.random_gather(spec.nt, spec.n_rec, 9))
     a, b = float((ctx.forward(h) * y).sum()), float((h * ctx.adjoint(y)).sum())

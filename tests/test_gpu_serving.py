@@ -64,3 +64,40 @@ def test_memory_budget_admits_one_at_a_time_and_results_hold(env):
         assert r["done"] and torch.equal(outs[i], solo[i][0])
     assert srv.poll(ids[2])["queue_ms"] > 0
     srv.close()
+
+
+def test_requests_served_in_a_mix_match_the_oracle(oracle):
+    """Three requests of different grids served together (the third joins
+    while the first two are mid-solve), each compared with the FP64 oracle's
+    Algorithm 1 on the same inputs: the same iteration count and h within
+    1e-4 relative L2 (element by element). The data gathers are the
+    oracle's own point-source data."""
+    from paper_2203_16573_gb300 import build, serve, ssx, workloads as W
+    build.build()
+    specs = serve.request_specs(3, 50.0, seed=5, scale=0.12, maxit=5, rtol=0.0)
+    probs, ins = [], []
+    for _, sp in specs:
+        vel = W.velocity(sp)
+        P = oracle.Problem(sp, vel)
+        d = P.point_source_data(W.ricker(sp), sp.x_d, sp.z_d)
+        probs.append((P, d))
+        ins.append((torch.as_tensor(vel, dtype=torch.float32, device="cuda").contiguous(),
+                    torch.as_tensor(d, dtype=torch.float64, device="cuda")))
+    srv = ssx.Server(8, 80 * 10 ** 9)
+    outs = [torch.full((sp.nt, sp.n_line), float("nan"), dtype=torch.float64, device="cuda")
+            for _, sp in specs]
+    ids = [srv.submit(specs[i][1], *ins[i], outs[i]) for i in range(2)]
+    srv.step()
+    srv.step()
+    ids.append(srv.submit(specs[2][1], *ins[2], outs[2]))
+    for _ in range(100):
+        a, q = srv.step()
+        if a == 0 and q == 0:
+            break
+    for (_, sp), (P, d), rid, h in zip(specs, probs, ids, outs):
+        r = srv.poll(rid)
+        assert r["done"] and r["iters"] == sp.maxit
+        h_or, hist_or = oracle.pcg(P, d, sp.alpha, sp.maxit, sp.rtol)
+        err = float(np.linalg.norm(h.cpu().numpy() - h_or) / np.linalg.norm(h_or))
+        assert err <= 1e-4, (sp.name, err)
+    srv.close()
