@@ -12,7 +12,11 @@ from paper_2203_16573_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-GTOL = 2e-3    # relative L2, FP32 wavefields against the FP64 oracle
+# relative L2, FP32 wavefields against the FP64 oracle: the measured errors
+# on GB300 are 1.9e-7 (order 4) and 4.7e-7 (order 8), the FP32 rounding of the
+# forward and adjoint fields (the FP32 difference p^{n+1} - A_p p^n alone
+# accounts for ~1e-8); the bar is ~3x the larger
+GTOL = 1.5e-6
 
 
 @pytest.fixture(scope="module")
