@@ -137,6 +137,7 @@ struct ssx_ctx {
     bool log_tuning = false;          // SSX_LOG_TUNING=1: print the phase tuner's timings
     std::unordered_map<std::string, cudaGraphExec_t> graphs;
     std::unordered_map<std::string, long long> graph_nodes;
+    std::unordered_map<std::string, int> key_uses;   // runs of each key not yet captured
 
     bool timing = false;
     std::vector<EvPair> evs;
@@ -308,8 +309,17 @@ int run_cached(ssx_ctx *c, const std::string &key, long long nodes, long long st
         ev->points = points;
         CK(cudaEventRecord(ev->a, c->s));
     }
-    if (c->use_graphs) {
-        auto it = c->graphs.find(key);
+    // A key's launches are captured into a graph the second time it runs:
+    // work that never repeats (a batch whose set of shots changes every
+    // round, a shot's set-up) is launched directly instead of being captured
+    // once and thrown away.
+    auto it = c->graphs.end();
+    bool capture = false;
+    if (c->use_graphs && !key.empty()) {
+        it = c->graphs.find(key);
+        if (it == c->graphs.end()) capture = ++c->key_uses[key] >= 2;
+    }
+    if (it != c->graphs.end() || capture) {
         if (it == c->graphs.end()) {
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
@@ -326,6 +336,7 @@ int run_cached(ssx_ctx *c, const std::string &key, long long nodes, long long st
             CK(ei);
             it = c->graphs.emplace(key, exec).first;
             c->graph_nodes[key] = nodes;
+            c->key_uses.erase(key);
         }
         CK(cudaGraphLaunch(it->second, c->s));
     } else {
@@ -764,12 +775,56 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
     return SSX_OK;
 }
 
+// Phase tuning results, shared by every context of the process: phases of up
+// to kMaxJobs sweeps by their exact shape (each sweep's padded grid,
+// direction and lockstep offset), larger ones (batches, whose set of shots a
+// server changes every few rounds) by size class -- sweep count, total points
+// (half octaves) and direction mix -- so that a batch of a new composition
+// reuses the choice of one of similar size instead of timing every
+// configuration again. All configurations give identical results.
+std::mutex g_phase_mu;
+std::map<std::vector<long long>, int> g_phase_tuned;
+
+std::vector<long long> phase_signature(ssx_ctx *c, const std::vector<Sweep> &sw) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<long long> k{dev, c->R, c->sweep_mode, (long long)sw.size()};
+    if (sw.size() <= (size_t)kMaxJobs) {
+        for (const Sweep &w : sw) {
+            k.push_back(w.G->L.NX);
+            k.push_back(w.G->L.NZ);
+            k.push_back(w.adj);
+            k.push_back(w.offset);
+        }
+        return k;
+    }
+    double pts = 0;
+    int nadj = 0;
+    for (const Sweep &w : sw) {
+        pts += (double)w.G->L.NX * w.G->L.NZ;
+        nadj += w.adj ? 1 : 0;
+    }
+    k[3] = -(long long)std::ceil(std::log2((double)sw.size()));
+    k.push_back((long long)std::floor(2.0 * std::log2(pts)));
+    k.push_back(nadj == 0 ? 0 : nadj == (int)sw.size() ? 2 : 1);
+    return k;
+}
+
 // time each admissible tile configuration on a short source-free run of the phase
 int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *best_cfg) {
     if (c->forced_cfg >= 0) {
         const int f = c->forced_cfg;
         *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
         return SSX_OK;
+    }
+    const std::vector<long long> sig = phase_signature(c, sw);
+    {
+        std::lock_guard<std::mutex> lock(g_phase_mu);
+        auto it = g_phase_tuned.find(sig);
+        if (it != g_phase_tuned.end()) {
+            *best_cfg = it->second;
+            return SSX_OK;
+        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
@@ -817,6 +872,10 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
     if (ttmp) cudaFree(ttmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc == SSX_OK) {
+        std::lock_guard<std::mutex> lock(g_phase_mu);
+        g_phase_tuned[sig] = *best_cfg;
+    }
     return rc;
 }
 
@@ -1093,6 +1152,7 @@ void drop_graphs(ssx_ctx *c) {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     c->graph_nodes.clear();
+    c->key_uses.clear();
 }
 
 // Forget tuned configurations. The captured graphs embed the configuration
@@ -2116,7 +2176,8 @@ int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued) {
             changed = true;
         }
         sv->active.swap(keep);
-        if (changed) drop_phases(L);   // phase tables of departed requests
+        // phase tables of departed requests, and the graphs that read them
+        if (changed) drop_graphs(L);
         CK(cudaEventRecord(L->ev_out, L->s));
         CK(cudaStreamWaitEvent(L->user, L->ev_out, 0));
     }

@@ -45,6 +45,23 @@ __device__ __forceinline__ void damp(float s, float &A, float &B) {
     A = fmaf(2.0f, B, -1.0f);
 }
 
+// Programmatic dependent launch: let the next step's grid become resident
+// while this one runs, and wait here until the previous step's grid has
+// finished and its writes are visible (a no-op without the launch attribute).
+__device__ __forceinline__ void griddep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// corner of sweep tile tl: tile row by the sweep's reciprocal of tiles_x
+template <int TX, int TZ>
+__device__ __forceinline__ void tile_corner(unsigned long long mul, int shift, int tiles_x, int tl,
+                                            int &i0, int &k0) {
+    const int q = (int)((unsigned)(((unsigned long long)(unsigned)tl * mul) >> 32) >> shift);
+    i0 = (tl - q * tiles_x) * TX;
+    k0 = q * TZ;
+}
+
 __device__ __forceinline__ float row_weight(int k, int k0, float w0, float w1) {
     return (k == k0) ? w0 : ((k == k0 + 1) ? w1 : 0.0f);
 }
@@ -88,37 +105,72 @@ __device__ __forceinline__ bool interior_tile(const GridArgs &g, int i0, int k0)
            k0 + TZ + 2 * R <= g.in_z1;
 }
 
-// Loops over the shared-memory regions: warp w takes rows w, w+8, ...; lanes
-// take columns lane, lane+32, ... (trip counts are compile-time constants).
-#define FOR_ROWS(r, n) _Pragma("unroll") for (int r##_u = 0; r##_u < ((n) + NT / 32 - 1) / (NT / 32); r##_u++) \
-    if (const int r = wy + (NT / 32) * r##_u; r < (n))
-#define FOR_COLS(c, n) _Pragma("unroll") for (int c##_u = 0; c##_u < ((n) + 31) / 32; c##_u++) \
-    if (const int c = lane + 32 * c##_u; c < (n))
+// The elements of the tile + 2k halo region a thread stages (corners are
+// never used and not loaded): f(slot, smem row, smem column, k - k0, i - i0)
+// for each, slot a compile-time index 0 .. Staged::N - 1 once unrolled. Warp
+// w takes rows w, w + NT/32, ...; lanes take columns lane, lane + 32, ...
+template <int R, int TX, int TZ, int NT>
+struct Staged {
+    static constexpr int H = 2 * R, PW = TX + 2 * H, NW = NT / 32;
+    static constexpr int NR1 = (TZ + NW - 1) / NW, NC1 = (PW + 31) / 32;      // tile rows, x halo
+    static constexpr int NR2 = (2 * H + NW - 1) / NW, NC2 = (TX + 31) / 32;   // z halo rows
+    static constexpr int N = NR1 * NC1 + NR2 * NC2;
+    template <class F>
+    __device__ __forceinline__ static void each(F &&f) {
+        const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+#pragma unroll
+        for (int a = 0; a < NR1; a++)
+#pragma unroll
+            for (int b = 0; b < NC1; b++) {
+                const int r = wy + NW * a, c = lane + 32 * b;
+                if (r < TZ && c < PW) f(a * NC1 + b, r + H, c, r, c - H);
+            }
+#pragma unroll
+        for (int a = 0; a < NR2; a++)
+#pragma unroll
+            for (int b = 0; b < NC2; b++) {
+                const int r = wy + NW * a, c = lane + 32 * b;
+                if (r < 2 * H && c < TX) {
+                    const int rr = r < H ? r : r + TZ;
+                    f(NR1 * NC1 + a * NC2 + b, rr, c + H, rr - H, c);
+                }
+            }
+    }
+};
 
-// Stage a field over tile + 2k halo (corners are never used and not loaded);
-// with PRE the staged value is C_p * field (transpose step), C_p from the
-// grid's precomputed field (B_p kappa~ inside the grid, 0 outside: the
-// storage's apron makes every address valid).
+// Stage a field over tile + 2k halo; with PRE the staged value is C_p * field
+// (transpose step), C_p from the grid's precomputed field (B_p kappa~ inside
+// the grid, 0 outside: the storage's apron makes every address valid). The
+// C_p factors may be read ahead (stage_cp, before the grid dependency wait:
+// they never change during a sweep) and passed in.
+template <int R, int TX, int TZ, int NT>
+__device__ __forceinline__ void stage_cp(const GridArgs &g, int i0, int k0,
+                                         float (&cp)[Staged<R, TX, TZ, NT>::N]) {
+    const float *base = g.cpk + k0 * g.pitch + i0;
+    const int pitch = g.pitch;
+    Staged<R, TX, TZ, NT>::each([&](int e, int, int, int dk, int di) { cp[e] = __ldg(base + dk * pitch + di); });
+}
+template <int R, int TX, int TZ, int NT, bool PRE>
+__device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i0, int k0,
+                                        float (&sp)[TZ + 4 * R][TX + 4 * R],
+                                        const float (&cp)[Staged<R, TX, TZ, NT>::N]) {
+    const float *base = f + k0 * g.pitch + i0;
+    const int pitch = g.pitch;
+    Staged<R, TX, TZ, NT>::each([&](int e, int sr, int sc, int dk, int di) {
+        const float v = ldf(base + dk * pitch + di);
+        sp[sr][sc] = PRE ? __fmul_rn(cp[e], v) : v;
+    });
+}
 template <int R, int TX, int TZ, int NT, bool SP, bool PRE>
 __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i0, int k0,
                                         float (&sp)[TZ + 4 * R][TX + 4 * R]) {
-    constexpr int H = 2 * R, PW = TX + 2 * H;
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const float *base = f + k0 * g.pitch + i0, *cbase = g.cpk + k0 * g.pitch + i0;
     const int pitch = g.pitch;
-    auto val = [&](int k, int i) -> float {
-        const int o = k * pitch + i;
-        if (!PRE) return ldf(f + o);
-        return __fmul_rn(__ldg(g.cpk + o), ldf(f + o));
-    };
-    // tile rows with the x halo
-    FOR_ROWS(r, TZ) {
-        FOR_COLS(c, PW) { sp[r + H][c] = val(k0 + r, i0 - H + c); }
-    }
-    // z halo rows, tile columns
-    FOR_ROWS(r, 2 * H) {
-        const int rr = r < H ? r : r + TZ;
-        FOR_COLS(c, TX) { sp[rr][c + H] = val(k0 - H + rr, i0 + c); }
-    }
+    Staged<R, TX, TZ, NT>::each([&](int, int sr, int sc, int dk, int di) {
+        const int o = dk * pitch + di;
+        const float v = ldf(base + o);
+        sp[sr][sc] = PRE ? __fmul_rn(__ldg(cbase + o), v) : v;
+    });
 }
 
 // Per-thread point sets of a tile (compile-time counts): warp w owns rows
@@ -144,6 +196,7 @@ __device__ __forceinline__ void fwd_tile_impl(const FwdArgs &a, const StepIO &io
     using T = TileShape<R, TX, TZ, NT>;
     constexpr int kWarps = NT / 32;
     constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
+    griddep_wait();   // the previous step's fields are complete
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
@@ -341,6 +394,7 @@ __device__ __forceinline__ void adj_tile_impl(const AdjArgs &a, const StepIO &io
     using T = TileShape<R, TX, TZ, NT>;
     constexpr int kWarps = NT / 32;
     constexpr int H = S::H, VXW = S::VXW, VZH = S::VZH;
+    griddep_wait();   // the previous step's fields are complete
     const GridArgs &g = a.g;
     const int pitch = g.pitch;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
@@ -649,8 +703,27 @@ struct GlobalIn {
     __device__ __forceinline__ float hvz(int kk, int i) const {
         return ldf(io.vz_in + (k0 - R + kk) * pitch + i);
     }
+    // the transposed step's C_p factors of the staged region, read before the
+    // grid dependency wait (set-up data, unchanged by the previous step) where
+    // the register budget allows it (CTAs of up to 256 threads); larger CTAs
+    // read them with the field
+    static constexpr bool kCpAhead = NT <= 256;
+    // the grid's constants are read ahead of the wait in CTAs of up to 256
+    // threads; larger CTAs (64 registers a thread) wait first, so that the
+    // constants need not stay live across the wait
+    static constexpr bool kAhead = NT <= 256;
+    float cpre[Staged<R, TX, TZ, NT>::N];
     template <bool PRE>
-    __device__ __forceinline__ void stage() { stage_p<R, TX, TZ, NT, SP, PRE>(g, io.p_in, i0, k0, spa); }
+    __device__ __forceinline__ void prestage() {
+        if (PRE && kCpAhead) stage_cp<R, TX, TZ, NT>(g, i0, k0, cpre);
+    }
+    // the previous step's fields are complete from here on
+    __device__ __forceinline__ void wait() const { griddep_wait(); }
+    template <bool PRE>
+    __device__ __forceinline__ void stage() {
+        if (kCpAhead) stage_p<R, TX, TZ, NT, PRE>(g, io.p_in, i0, k0, spa, cpre);
+        else stage_p<R, TX, TZ, NT, SP, PRE>(g, io.p_in, i0, k0, spa);
+    }
     __device__ __forceinline__ float (&sp())[TZ + 4 * R][TX + 4 * R] { return spa; }
 };
 
@@ -672,9 +745,12 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
     const bool colp = !SP || i < NX;        // p, v_z column inside the grid
     const bool colx = !SP || i < NX - 1;    // v_x column inside the grid
 
-    // every global operand of the step, in one batch
+    // every global operand of the step, in two batches: the grid's constants
+    // (kappa, sponge profiles) before the wait for the previous step, the
+    // fields after it
     float rvx[L], rvz[L], rk[L], rhx[Q::NQX], rhz[Q::NQZ];
     float sxi = 0.0f, sxh = 0.0f, szi[L], szh[L];
+    if (!In::kAhead) in.wait();
     if (SP) {
         sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
         sxh = __ldg(g.sxh + min(i, NX - 1));
@@ -682,13 +758,17 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
 #pragma unroll
     for (int j = 0; j < L; j++) {
         const int k = k0 + rs + j;
-        rvx[j] = in.own_vx(j);
-        rvz[j] = in.own_vz(j);
         rk[j] = in.own_kap(j);
         if (SP) {
             szi[j] = __ldg(g.szi + min(k, NZ - 1));
             szh[j] = __ldg(g.szh + min(k, NZ - 1));
         }
+    }
+    if (In::kAhead) in.wait();
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        rvx[j] = in.own_vx(j);
+        rvz[j] = in.own_vz(j);
     }
 #pragma unroll
     for (int q = 0; q < Q::NQX; q++) rhx[q] = th.hx_jj[q] >= 0 ? in.hvx(th.hx_r[q], th.hx_jj[q]) : 0.0f;
@@ -862,6 +942,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
 
     float rvx[L], rvz[L], rp[L], rhx[Q::NQX], rhz[Q::NQZ];
     float sxi = 0.0f, sxh = 0.0f, szi[L], szh[L];
+    if (!In::kAhead) in.wait();
     if (SP) {
         sxi = __ldg(g.sxi + min(i, NX - 1));   // clamped: masked points take any value
         sxh = __ldg(g.sxh + min(i, NX - 1));
@@ -869,13 +950,18 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
 #pragma unroll
     for (int j = 0; j < L; j++) {
         const int k = k0 + rs + j;
-        rvx[j] = in.own_vx(j);
-        rvz[j] = in.own_vz(j);
-        rp[j] = in.own_p(j);
         if (SP) {
             szi[j] = __ldg(g.szi + min(k, NZ - 1));
             szh[j] = __ldg(g.szh + min(k, NZ - 1));
         }
+    }
+    in.template prestage<true>();   // C_p of the staged region (constants)
+    if (In::kAhead) in.wait();
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        rvx[j] = in.own_vx(j);
+        rvz[j] = in.own_vz(j);
+        rp[j] = in.own_p(j);
     }
 #pragma unroll
     for (int q = 0; q < Q::NQX; q++) rhx[q] = th.hx_jj[q] >= 0 ? in.hvx(th.hx_r[q], th.hx_jj[q]) : 0.0f;
@@ -1082,14 +1168,6 @@ constexpr int min_ctas(int nt, int rows_per_thread = 4) {
 template <int TX, int TZ, int NT>
 constexpr int tile_min_ctas() { return min_ctas(NT, NT >= TX ? TZ / (NT / TX) : 1); }
 
-// Programmatic dependent launch: let the next step's grid become resident
-// while this one runs, and wait here until the previous step's grid has
-// finished and its writes are visible (a no-op without the launch attribute).
-__device__ __forceinline__ void griddep_launch() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 template <int R, int TX, int TZ>
 __device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
     extern __shared__ __align__(16) unsigned char ssx_smem[];
@@ -1098,8 +1176,7 @@ __device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
 
 template <int R, int TX, int TZ, int NT>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_fwd(const FwdArgs a) {
-    griddep_launch();
-    griddep_wait();
+    griddep_launch();   // the tile step waits for the previous step itself
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
     fwd_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
 }
@@ -1107,7 +1184,6 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_fwd(const
 template <int R, int TX, int TZ, int NT>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_adj(const AdjArgs a) {
     griddep_launch();
-    griddep_wait();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
     adj_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
 }
@@ -1234,8 +1310,8 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(con
     const Job &J = P.job[j];
     const int st = t - J.offset;
     if (st < 0 || st >= J.nt) return;
-    const int tl = blockIdx.x - J.tile_base;
-    const int i0 = (tl % J.tiles_x) * TX, k0 = (tl / J.tiles_x) * TZ;
+    int i0, k0;
+    tile_corner<TX, TZ>(J.tx_mul, J.tx_shift, J.tiles_x, blockIdx.x - J.tile_base, i0, k0);
     const bool odd = st & 1;
     StepIO io;
     io.p_in = odd ? J.f[1][0] : J.f[0][0];
@@ -1245,7 +1321,8 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(con
     io.vx_out = odd ? J.f[0][1] : J.f[1][1];
     io.vz_out = odd ? J.f[0][2] : J.f[1][2];
     io.n = J.adj ? J.nt - 1 - st : st;
-    griddep_wait();
+    // the tile step reads the grid's constants, then waits for the previous
+    // step (griddepcontrol.wait) before its field loads
     if (J.adj)
         adj_tile<R, TX, TZ, NT>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>());
     else
@@ -1277,8 +1354,8 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi_tab
     __syncthreads();
     const int st = t - sj.offset;
     if (st < 0 || st >= sj.nt) return;
-    const int tl = blockIdx.x - sj.tile_base;
-    const int i0 = (tl % sj.tiles_x) * TX, k0 = (tl / sj.tiles_x) * TZ;
+    int i0, k0;
+    tile_corner<TX, TZ>(sj.tx_mul, sj.tx_shift, sj.tiles_x, blockIdx.x - sj.tile_base, i0, k0);
     const bool odd = st & 1;
     StepIO io;
     io.p_in = odd ? sj.f[1][0] : sj.f[0][0];
@@ -1288,6 +1365,8 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi_tab
     io.vx_out = odd ? sj.f[0][1] : sj.f[1][1];
     io.vz_out = odd ? sj.f[0][2] : sj.f[1][2];
     io.n = sj.adj ? sj.nt - 1 - st : st;
+    // batches of many shots are bound by throughput, not by the step's
+    // latency: wait here (the tile step's own wait is then a no-op)
     griddep_wait();
     if (sj.adj)
         adj_tile<R, TX, TZ, NT>(sj.aa, io, i0, k0, tile_smem<R, TX, TZ>());

@@ -136,6 +136,12 @@ struct TmaIn {
     __device__ __forceinline__ float own_p(int j) const { return st.p[rs + j + 2 * kR][c + 2 * kR]; }
     __device__ __forceinline__ float hvx(int r, int jj) const { return st.vx[r][jj]; }
     __device__ __forceinline__ float hvz(int kk, int i) const { return st.vz[kk][i - i0]; }
+    // the stage is complete (every thread waited on its barrier): nothing to
+    // read ahead, nothing to wait for
+    static constexpr bool kAhead = true;
+    template <bool PRE>
+    __device__ __forceinline__ void prestage() {}
+    __device__ __forceinline__ void wait() const {}
     // transposed step: q = C_p pbar over the box, written over C_p (which
     // the step reads nowhere else; C_p is 0 outside the grid), the per-point
     // arithmetic of stage_p. Each element is read and written by one thread
@@ -210,15 +216,6 @@ __device__ __forceinline__ int next_active(const TmaJob *__restrict__ jobs, int 
     }
     *jo = 0;
     return total;
-}
-
-// corner of sweep tile tl: tile row by the sweep's reciprocal of tiles_x
-template <int TX, int TZ>
-__device__ __forceinline__ void tile_corner(unsigned long long mul, int shift, int tiles_x, int tl,
-                                            int &i0, int &k0) {
-    const int q = (int)((unsigned)(((unsigned long long)(unsigned)tl * mul) >> 32) >> shift);
-    i0 = (tl - q * tiles_x) * TX;
-    k0 = q * TZ;
 }
 
 // thread 0: start the four copies of `tile` (sweep j) into stage `st`
