@@ -303,8 +303,12 @@ int ssx_set_test_hook(ssx_ctx *ctx, int hook, int k);
  * shape k with the multi-sweep steps run by the TMA-staged kernel (operand
  * tiles copied by the tensor memory accelerator into a two-stage shared-memory
  * pipeline, persistent CTAs), available for space order 8; for other orders
- * 8 + k runs shape k. All configurations compute identical results. */
+ * 8 + k runs shape k; 16 + m fixes the marching kernel of shape m (tiles of
+ * 64 x 128, 64 x 64, 128 x 64, 32 x 128 points, one thread per column walking
+ * down it in blocks of 8 rows fed by tensor copies), available for space
+ * order 8 (else shape 0 runs). All configurations compute identical results. */
 #define SSX_NUM_TILE_CONFIGS 8
+#define SSX_NUM_MARCH_CONFIGS 4
 int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
 
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the

@@ -103,6 +103,7 @@ struct ssx_ctx {
         JobSet jobs{};          // small phases: by-value kernel parameter
         Job *dtab = nullptr;    // large phases (batches): device table
         TmaJob *ttab = nullptr; // TMA-staged kernel: sweeps with their tensor maps
+        MarchJob *mtab = nullptr;  // marching kernel: sweeps with their tensor maps
         int njobs = 0, total = 0, T = 0, cap = 0;
     };
     std::unordered_map<std::string, PhaseInfo> phases;
@@ -129,6 +130,7 @@ struct ssx_ctx {
     int sweep_mode = SSX_SWEEP_AUTO;
     int cap[kNumTileCfgs][2];         // co-resident CTAs of the persistent kernels (-1: unknown)
     int tma_cap[kNumTileCfgs];        // co-resident CTAs of the TMA-staged phase kernel (-1: unknown)
+    int march_cap[kNumMarchCfgs];     // co-resident CTAs of the marching phase kernel (-1: unknown)
     int forced_cfg = -1;              // tile configuration fixed by the caller (-1: autotune)
     bool stall_next = false;          // test hook: stall one tile of the next persistent sweep
     int hook = SSX_HOOK_NONE;         // test hook of ssx_set_test_hook and its iteration
@@ -167,6 +169,17 @@ int fail(ssx_ctx *c, int code, const std::string &msg) {
     } while (0)
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Phase-kernel configuration ids: 0 .. 7 the plain tile kernel (shape id),
+// 8 .. 15 the TMA-staged tile kernel of shape id - 8, 16 .. 19 the marching
+// kernel of shape id - 16.
+constexpr int kCfgMarch0 = 2 * kNumTileCfgs;
+constexpr int kNumAllCfgs = kCfgMarch0 + kNumMarchCfgs;
+void tile_dims(int cfg, int *tx, int *tz) {
+    const TileCfg &t = cfg >= kCfgMarch0 ? kMarchCfgs[cfg - kCfgMarch0] : kTileCfgs[cfg % kNumTileCfgs];
+    *tx = t.tx;
+    *tz = t.tz;
+}
 
 // ---------------------------------------------------------------- grids --
 int grid_alloc(ssx_ctx *c, DGrid &G, int nx, int nz, int row0, double z_origin) {
@@ -606,7 +619,8 @@ Sweep adj_sweep(DGrid &G, const Line &src, double *hb, double *fb, const Line &r
 }
 
 std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, int *total) {
-    cfg %= kNumTileCfgs;   // the TMA-staged kernel tiles like the shape it is built on
+    int TX = 0, TZ = 0;
+    tile_dims(cfg, &TX, &TZ);   // the TMA-staged kernel tiles like the shape it is built on
     std::vector<Job> jobs(sw.size());
     int base = 0;
     for (size_t j = 0; j < sw.size(); j++) {
@@ -616,8 +630,8 @@ std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, in
         J.adj = w.adj ? 1 : 0;
         J.offset = w.offset;
         J.nt = w.nt;
-        J.tiles_x = (w.G->L.NX + kTileCfgs[cfg].tx - 1) / kTileCfgs[cfg].tx;
-        J.tiles = J.tiles_x * ((w.G->L.NZ + kTileCfgs[cfg].tz - 1) / kTileCfgs[cfg].tz);
+        J.tiles_x = (w.G->L.NX + TX - 1) / TX;
+        J.tiles = J.tiles_x * ((w.G->L.NZ + TZ - 1) / TZ);
         J.tx_shift = 0;
         while ((1LL << J.tx_shift) < J.tiles_x) J.tx_shift++;
         J.tx_mul = ((1ULL << (32 + J.tx_shift)) + (unsigned long long)J.tiles_x - 1) /
@@ -656,6 +670,7 @@ struct PhaseArgs {
     JobSet set{};
     Job *dtab = nullptr;
     TmaJob *ttab = nullptr;
+    MarchJob *mtab = nullptr;
     int njobs = 0, total = 0, cap = 0;
 };
 
@@ -687,6 +702,13 @@ bool field_map(CUtensorMap *m, const float *f, const FieldLayout &L, int bx, int
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// the marching kernel runs shape m for this context (order 8 only)
+bool march_usable(ssx_ctx *c, int m) {
+    if (c->R != kMaxR || m < 0 || m >= kNumMarchCfgs) return false;
+    if (c->march_cap[m] < 0) c->march_cap[m] = march_capacity(m);
+    return c->march_cap[m] > 0 && tensor_map_encoder() != nullptr;
+}
+
 // the TMA-staged kernel runs shape `base` for this context (order 8 only)
 bool tma_usable(ssx_ctx *c, int base) {
     if (c->R != kMaxR || base < 0 || base >= kNumTileCfgs || !tma_shape_supported(base)) return false;
@@ -695,11 +717,38 @@ bool tma_usable(ssx_ctx *c, int base) {
 }
 
 int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
-               Job **dtab, TmaJob **ttab) {
+               Job **dtab, TmaJob **ttab, MarchJob **mtab) {
     std::vector<Job> jobs = make_jobs(sw, cfg, quiet, &pa->total);
     pa->njobs = (int)jobs.size();
     pa->dtab = nullptr;
     pa->ttab = nullptr;
+    pa->mtab = nullptr;
+    if (cfg >= kCfgMarch0) {
+        // boxes of one block of kMarchB rows: p and C_p over the tile with a 2k
+        // column halo, v_x with a k halo, v_z and kappa over the tile
+        const int m = cfg - kCfgMarch0, TX = kMarchCfgs[m].tx, R = kMaxR, B = kMarchB;
+        std::vector<MarchJob> mj(jobs.size());
+        for (size_t j = 0; j < jobs.size(); j++) {
+            memset(&mj[j], 0, sizeof(MarchJob));
+            mj[j].job = jobs[j];
+            const DGrid &G = *sw[j].G;
+            bool ok = true;
+            for (int b = 0; b < 2; b++) {
+                ok = ok && field_map(&mj[j].map[b], G.f[b][0], G.L, TX + 4 * R, B);
+                ok = ok && field_map(&mj[j].map[2 + b], G.f[b][1], G.L, TX + 2 * R, B);
+                ok = ok && field_map(&mj[j].map[4 + b], G.f[b][2], G.L, TX, B);
+            }
+            ok = ok && field_map(&mj[j].map[6], G.args.kap, G.L, TX, B);
+            ok = ok && field_map(&mj[j].map[7], G.args.cpk, G.L, TX + 4 * R, B);
+            if (!ok) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
+        }
+        if (!*mtab) CK(cudaMalloc(mtab, mj.size() * sizeof(MarchJob)));
+        CK(cudaMemcpyAsync(*mtab, mj.data(), mj.size() * sizeof(MarchJob), cudaMemcpyHostToDevice, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        pa->mtab = *mtab;
+        pa->cap = c->march_cap[m];
+        return SSX_OK;
+    }
     if (cfg >= kNumTileCfgs) {
         const int base = cfg - kNumTileCfgs;
         const int TX = kTileCfgs[base].tx, TZ = kTileCfgs[base].tz, R = kMaxR;
@@ -763,7 +812,11 @@ int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa,
                     a.vz_in = w.G->f[0][2];
                     CK(launch_adj_init(a, w.nt, s));
                 }
-        if (pa.ttab)
+        if (pa.mtab)
+            CK(launch_march(pa.mtab, pa.njobs, pa.total, t, cfg - kCfgMarch0, pa.cap, c->d_err,
+                            stall && t == 0 ? 200000000ull : 2000000000ull,
+                            stall && t == 0 ? 0 : -1, s, true));
+        else if (pa.ttab)
             CK(launch_multi_tma(pa.ttab, pa.njobs, pa.total, t, cfg - kNumTileCfgs, pa.cap, c->d_err,
                                 stall && t == 0 ? 200000000ull : 2000000000ull,
                                 stall && t == 0 ? 0 : -1, s, true));
@@ -814,7 +867,8 @@ std::vector<long long> phase_signature(ssx_ctx *c, const std::vector<Sweep> &sw)
 int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *best_cfg) {
     if (c->forced_cfg >= 0) {
         const int f = c->forced_cfg;
-        *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
+        if (f >= kCfgMarch0) *best_cfg = march_usable(c, f - kCfgMarch0) ? f : 0;
+        else *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
         return SSX_OK;
     }
     const std::vector<long long> sig = phase_signature(c, sw);
@@ -834,10 +888,15 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
     int rc = SSX_OK;
     Job *tmp = nullptr;
     TmaJob *ttmp = nullptr;
-    for (int k = 0; k < 2 * kNumTileCfgs && rc == SSX_OK; k++) {
-        if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) continue;
+    MarchJob *mtmp = nullptr;
+    for (int k = 0; k < kNumAllCfgs && rc == SSX_OK; k++) {
+        if (k >= kCfgMarch0) {
+            if (!march_usable(c, k - kCfgMarch0)) continue;
+        } else if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) {
+            continue;
+        }
         PhaseArgs pa;
-        rc = phase_args(c, sw, k, true, &pa, &tmp, &ttmp);
+        rc = phase_args(c, sw, k, true, &pa, &tmp, &ttmp, &mtmp);
         if (rc != SSX_OK) break;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -870,6 +929,7 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
     }
     if (tmp) cudaFree(tmp);
     if (ttmp) cudaFree(ttmp);
+    if (mtmp) cudaFree(mtmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == SSX_OK) {
@@ -899,7 +959,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         TRY(tune_phase(c, name, sw, &info.cfg));
         TRY(check_sweeps_quiet(c));
         PhaseArgs pa;
-        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab, &info.ttab));
+        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab, &info.ttab, &info.mtab));
         info.cap = pa.cap;
         info.jobs = pa.set;
         info.njobs = pa.njobs;
@@ -912,6 +972,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     pa.set = info.jobs;
     pa.dtab = info.dtab;
     pa.ttab = info.ttab;
+    pa.mtab = info.mtab;
     pa.cap = info.cap;
     pa.njobs = info.njobs;
     pa.total = info.total;
@@ -1143,6 +1204,7 @@ void drop_phases(ssx_ctx *c) {
     for (auto &kv : c->phases) {
         if (kv.second.dtab) cudaFree(kv.second.dtab);
         if (kv.second.ttab) cudaFree(kv.second.ttab);
+        if (kv.second.mtab) cudaFree(kv.second.mtab);
     }
     c->phases.clear();
 }
@@ -1508,6 +1570,7 @@ int ssx_create(ssx_ctx **out, const ssx_grid_desc *gd, void *stream) {
     auto init = [&]() -> int {
         for (auto &row : c->cap) row[0] = row[1] = -1;
         for (int &v : c->tma_cap) v = -1;
+        for (int &v : c->march_cap) v = -1;
         // SSX_GRAPHS=0: launch every step directly instead of replaying CUDA
         // graphs (profilers treat each graph replay as a rebuild)
         if (const char *e = std::getenv("SSX_GRAPHS")) c->use_graphs = std::strcmp(e, "0") != 0;
@@ -2047,7 +2110,7 @@ int ssx_set_test_hook(ssx_ctx *c, int hook, int k) {
 
 int ssx_set_tile_config(ssx_ctx *c, int cfg) {
     if (!c) return SSX_ERR_ARG;
-    if (cfg < -1 || cfg >= 2 * kNumTileCfgs) return fail(c, SSX_ERR_ARG, "unknown tile configuration");
+    if (cfg < -1 || cfg >= kNumAllCfgs) return fail(c, SSX_ERR_ARG, "unknown tile configuration");
     c->forced_cfg = cfg;
     reset_choices(c);
     return SSX_OK;

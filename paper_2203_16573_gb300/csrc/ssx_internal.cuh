@@ -142,6 +142,16 @@ struct alignas(128) TmaJob {
     CUtensorMap map[7];
     Job job;
 };
+// A sweep of a phase run by the marching kernel (order 8, grids far larger
+// than L2): its arguments and the tensor maps of its storage, boxes of one
+// block of kMarchB rows -- p of ping-pong buffers 0 and 1 over the tile with a
+// 2k column halo (maps 0-1), v_x with a k halo (2-3), v_z (4-5), kappa (6)
+// and C_p over the p box width (7).
+constexpr int kMarchB = 8;
+struct alignas(128) MarchJob {
+    CUtensorMap map[8];
+    Job job;
+};
 // The sweeps of a phase, passed by value as the kernel parameter (constant
 // bank): a CTA reads its sweep's arguments without a global-memory round trip.
 struct JobSet {
@@ -167,6 +177,14 @@ struct TileCfg {
     int tx, tz, threads;
 };
 extern const TileCfg kTileCfgs[kNumTileCfgs];
+// Marching-kernel shapes: (id, tile width = threads per CTA, tile height).
+#define SSX_MARCH_CONFIGS(X) \
+    X(0, 64, 128)            \
+    X(1, 64, 64)             \
+    X(2, 128, 64)            \
+    X(3, 32, 128)
+constexpr int kNumMarchCfgs = 4;
+extern const TileCfg kMarchCfgs[kNumMarchCfgs];
 
 // Kernel launchers (stencil.cu). Return the launch's cudaError_t. `pdl` sets
 // programmatic dependent launch (the step waits in-kernel for the previous one).
@@ -194,6 +212,15 @@ cudaError_t prepare_tma_kernels();
 cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,
                              int cap, int *err, unsigned long long timeout_ns, int stall_tile,
                              cudaStream_t s, bool pdl);
+// The marching phase kernel (stencil_march.cu), order 8 only: tall tiles, one
+// thread per column, marched down in blocks of kMarchB rows.
+int march_capacity(int m);                         // its co-resident CTAs (the launch's grid cap)
+cudaError_t prepare_march_kernels();
+// stall_tile >= 0 (test hook): that tile's first copies are never issued, so
+// the CTA's bounded wait runs out and reports error 2
+cudaError_t launch_march(const MarchJob *jobs, int njobs, int total_tiles, int t, int m, int cap,
+                         int *err, unsigned long long timeout_ns, int stall_tile, cudaStream_t s,
+                         bool pdl);
 
 // per-R instantiations (stencil_r<R>.cu)
 #define SSX_DECLARE_R(RR)                                                                       \

@@ -130,6 +130,23 @@ def c4_shots(n_shots: int = 32, nt: int = 4000) -> list[Spec]:
     return out
 
 
+def paper_pcg(alpha: float = 0.0, lens: bool = True) -> Spec:
+    """The setting of the paper's CG / PCG comparison ("Preconditioned CG
+    iteration"): an 8 km x 4 km medium at h = 20 m (401 x 201), order 8,
+    40-point sponge, dt = 2 ms, 1500 steps (3 s); receivers on z = 1 km and
+    the extended-source line on z = 3 km, both over x = 2 .. 6 km (201
+    points); a point source at (3.5 km, 3.5 km) with the paper's bandpass
+    wavelet (``bandpass``); penalty centre x_s = 3.5 km. lens=True is the
+    model the data are simulated in (``paper_lens``: kappa = 4 GPa with a
+    central low-velocity lens down to 1.6 GPa); lens=False the homogeneous
+    model (kappa = 4 GPa, v = 2 km/s) the problem is solved in."""
+    return Spec(name=f"paper_pcg_401x201_o8_nt1500_{'lens' if lens else 'homog'}", nx=401, nz=201,
+                h=0.02, dt=2e-3, nt=1500, order=8, n_sponge=40, rho=1.0, z_s=3.0,
+                ix_line0=100, n_line=201, z_r=1.0, ix_rec0=100, n_rec=201, x_s=3.5, x_d=3.5,
+                z_d=3.5, f_peak=7.5, alpha=alpha, maxit=60, rtol=0.0,
+                model="paper_lens" if lens else "homogeneous", v0=2.0)
+
+
 def background(spec: Spec) -> Spec:
     """The same workload on the unperturbed linear-gradient model."""
     return dataclasses.replace(spec, model="gradient")
@@ -195,7 +212,31 @@ def velocity(spec: Spec) -> np.ndarray:
         v = spec.v0 * (1.0 + zz / zmax)
         lens = 1.0 - 0.2 * np.exp(-((xx - xc) ** 2 + (zz - zc) ** 2) / (2.0 * sig ** 2))
         return v * lens
+    if spec.model == "paper_lens":
+        # kappa = 4 GPa (rho = 1: v = 2 km/s) falling to 1.6 GPa at the centre
+        # of the rectangle through a Gaussian of sigma = 0.5 km (the paper
+        # gives the end values, not the lens profile)
+        xc, zc = 0.5 * (spec.nx - 1) * spec.h, 0.5 * (spec.nz - 1) * spec.h
+        zz, xx = np.meshgrid(z, x, indexing="ij")
+        kappa = 4.0 - 2.4 * np.exp(-((xx - xc) ** 2 + (zz - zc) ** 2) / (2.0 * 0.5 ** 2))
+        return np.sqrt(kappa / spec.rho)
     raise ValueError(spec.model)
+
+
+def bandpass(spec: Spec, corners=(1.0, 2.5, 7.5, 12.5), delay: float = 0.4) -> np.ndarray:
+    """The paper's source wavelet: a zero-phase bandpass filter with a
+    trapezoidal amplitude spectrum (0 below 1 Hz, rising to 1 at 2.5 Hz, flat
+    to 7.5 Hz, falling to 0 at 12.5 Hz), delayed by `delay` s and normalised
+    to a unit peak, sampled at the half-step times (n + 1/2) dt; the first
+    0.2 s are tapered by a half cosine so that the source starts from rest."""
+    n = 1 << int(math.ceil(math.log2(8 * spec.nt)))
+    f = np.fft.rfftfreq(n, spec.dt)
+    f1, f2, f3, f4 = corners
+    amp = np.clip(np.minimum((f - f1) / (f2 - f1), (f4 - f) / (f4 - f3)), 0.0, 1.0)
+    w = np.fft.irfft(amp * np.exp(-2j * math.pi * f * (delay + 0.5 * spec.dt)), n)[: spec.nt]
+    t = (np.arange(spec.nt) + 0.5) * spec.dt
+    w = w * np.where(t < 0.2, 0.5 - 0.5 * np.cos(math.pi * t / 0.2), 1.0)
+    return w / np.max(np.abs(w))
 
 
 def ricker(spec: Spec) -> np.ndarray:

@@ -39,6 +39,9 @@ def test_binding_constants_match_the_header():
     assert ssx.N_TILE_CONFIGS == n
     src = open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "ssx_internal.cuh")).read()
     assert re.search(r"constexpr int kNumTileCfgs = (\d+);", src).group(1) == str(n)
+    nm = int(re.search(r"#define SSX_NUM_MARCH_CONFIGS (\d+)", text).group(1))
+    assert ssx.N_MARCH_CONFIGS == nm
+    assert re.search(r"constexpr int kNumMarchCfgs = (\d+);", src).group(1) == str(nm)
 
 
 def test_version_string(lib):

@@ -287,6 +287,31 @@ def test_persistent_wait_timeout_is_reported_and_context_survives(ssx, oracle):
     assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
 
 
+@pytest.mark.parametrize("cfg_offset", [0, 2])
+def test_march_kernel_parity_and_copy_wait_timeout(ssx, oracle, cfg_offset):
+    """The marching phase kernel on its own: S, S^T, W~_d and one preconditioned
+    solve against the oracle on a grid of several tall tiles with ragged edges;
+    then a tile whose copies are withheld (test hook) makes its CTA's bounded
+    wait run out (0.2 s), the call returns SSX_ERR_CUDA, and the next call on
+    the same context gives the same bits as before."""
+    spec = frac_spec(8, nt=160)
+    ctx, P = make(ssx, oracle, spec)
+    ctx.set_tile_config(2 * ssx.N_TILE_CONFIGS + cfg_offset)
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 23)
+    d = W.smooth_random_gather(spec.nt, spec.n_rec, 24)
+    assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
+    assert rel(ctx.adjoint(dev(d)), P.ST(d)) <= TOL
+    assert rel(ctx.weight_apply(ssx.W_D, dev(d)), P.Wd(d)) <= TOL
+    _check_solve(ctx, P, spec, d, "pcg", 4, 0.0)
+    ref = ctx.forward(dev(h)).clone()
+    ctx.set_sweep_mode(ssx.SWEEP_TEST_STALL)
+    with pytest.raises(ssx.SSXError) as e:
+        ctx.forward(dev(h))
+    assert e.value.code == 2 and "timed out" in e.value.msg
+    assert torch.equal(ctx.forward(dev(h)), ref)
+    ctx.set_tile_config(-1)
+
+
 def test_tma_copy_wait_timeout_is_reported_and_context_survives(ssx):
     """The TMA-staged phase kernel: a tile whose copies are withheld (test
     hook) makes its CTA's bounded mbarrier wait run out (0.2 s); the call
@@ -307,9 +332,10 @@ def test_tma_copy_wait_timeout_is_reported_and_context_survives(ssx):
 
 @pytest.mark.parametrize("order", [4, 8])
 def test_every_tile_configuration_gives_identical_results(ssx, order):
-    """All tile shapes / CTA sizes, both launch forms and the TMA-staged phase
-    kernel (ids N..2N-1; order 8) run the same per-point arithmetic:
-    bitwise-identical sweeps (ragged tiles on both grid edges)."""
+    """All tile shapes / CTA sizes, both launch forms, the TMA-staged phase
+    kernel (ids N..2N-1) and the marching kernel (ids 2N..; order 8) run the
+    same per-point arithmetic: bitwise-identical sweeps (ragged tiles on both
+    grid edges, lines between rows)."""
     spec = frac_spec(order, nt=120)
     ctx = ssx.Context.for_problem(spec, W.velocity(spec))
     x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 19))
@@ -318,7 +344,7 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     for mode in (ssx.SWEEP_STEP, ssx.SWEEP_PERSISTENT):
         ctx.set_sweep_mode(mode)
         N = ssx.N_TILE_CONFIGS
-        for cfg in range(2 * N if mode == ssx.SWEEP_STEP else N):
+        for cfg in range(2 * N + ssx.N_MARCH_CONFIGS if mode == ssx.SWEEP_STEP else N):
             ctx.set_tile_config(cfg)
             got = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
                    ctx.weight_apply(ssx.W_D, y).clone())

@@ -4,6 +4,7 @@ Ricker wavelet, against the numbers the workload descriptions state."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2203_16573_gb300 import workloads as W
 
@@ -72,3 +73,30 @@ def test_ricker_wavelet():
     assert abs(t[k] - 1.5 / s.f_peak) <= s.dt
     assert math.isclose(r[k], 1.0, rel_tol=1e-3)
     assert abs(r.sum()) * s.dt < 1e-6          # zero mean
+
+
+def test_paper_comparison_setting():
+    """The setting of the paper's CG / PCG comparison: 8 km x 4 km at 20 m,
+    lines at 1 km and 3 km over x = 2 .. 6 km, point source at (3.5, 3.5) km,
+    kappa = 4 GPa falling to 1.6 GPa at the lens centre, and a bandpass
+    wavelet whose spectrum is the 1 - 2.5 - 7.5 - 12.5 Hz trapezoid."""
+    lens, homog = W.paper_pcg(lens=True), W.paper_pcg(lens=False)
+    assert (lens.nx - 1) * lens.h == pytest.approx(8.0) and (lens.nz - 1) * lens.h == pytest.approx(4.0)
+    assert lens.ix_line0 * lens.h == pytest.approx(2.0)
+    assert (lens.ix_line0 + lens.n_line - 1) * lens.h == pytest.approx(6.0)
+    assert (lens.z_r, lens.z_s, lens.x_d, lens.z_d) == (1.0, 3.0, 3.5, 3.5)
+    kl = lens.rho * W.velocity(lens) ** 2
+    kh = homog.rho * W.velocity(homog) ** 2
+    assert np.allclose(kh, 4.0)
+    assert kl[100, 200] == pytest.approx(1.6) and kl.min() == pytest.approx(1.6)
+    assert kl[0, 0] == pytest.approx(4.0, abs=1e-6)
+    w = W.bandpass(lens)
+    assert abs(w[0]) < 1e-4 and np.max(np.abs(w)) == pytest.approx(1.0)
+    F = np.abs(np.fft.rfft(w, 1 << 14))
+    f = np.fft.rfftfreq(1 << 14, lens.dt)
+    at = lambda fr: F[np.argmin(np.abs(f - fr))] / F.max()
+    assert at(5.0) > 0.9 and at(7.0) > 0.9
+    assert at(0.5) < 0.1 and at(14.0) < 0.05
+    assert 0.3 < at(1.75) < 0.7 and 0.3 < at(10.0) < 0.7   # half way up and down the ramps
+    # CFL of the order-8 scheme at the lens model's maximum speed
+    assert W.velocity(lens).max() * lens.dt / lens.h * np.sqrt(2) * 1.3713 < 0.5
