@@ -569,8 +569,14 @@ def run_serve(args):
                                 maxit=args.maxit, rtol=1e-3)
     inputs = serve.make_inputs(specs)
     serve.serve(specs[:2], inputs[:2], realtime=False)          # warm-up (kernels, allocator)
+    clocks = ClockSampler(0)
+    clocks.start()
     outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9)
+    clk_b = clocks.stop()
+    clocks = ClockSampler(0)
+    clocks.start()
     outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs)
+    clk_s = clocks.stop()
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
     pb, ps = serve.percentiles(rec_b), serve.percentiles(rec_s)
     line = {"metric": "served PCG solves/s (continuous batching) with p50/p99 latency",
@@ -581,11 +587,15 @@ def run_serve(args):
             "config": {"workload": f"{len(specs)} requests, Poisson rate {args.rate}/s, grids "
                                    f"{{401x201,1001x401,2001x801}} x {args.scale}, nt 1000-5000 x "
                                    f"{args.scale}, order 8, maxit {args.maxit}, rtol 1e-3, "
-                                   f"HBM budget {args.budget_gb} GB"},
+                                   f"HBM budget {args.budget_gb} GB",
+                       "arrival_span_s": specs[-1][0]},
             "latency_ms": pb, "one_at_a_time": {"value": len(specs) / wall_s, "unit": "solves/s",
                                                 "latency_ms": ps},
             "results_identical_to_solo": same,
-            "iterations": [r["iters"] for r in rec_b]}
+            "iterations": [r["iters"] for r in rec_b],
+            "status_counts": {k: sum(1 for r in rec_b if r["status"] == k)
+                              for k in sorted(set(r["status"] for r in rec_b))},
+            "clocks": clk_b, "clocks_one_at_a_time": clk_s}
     print(json.dumps(line), flush=True)
     return 0
 
