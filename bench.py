@@ -573,6 +573,10 @@ def run_serve(args):
     clocks.start()
     outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9)
     clk_b = clocks.stop()
+    # the batched arm on its own first, on stderr (kept if the second arm fails)
+    print(json.dumps({"partial": "continuous batching", "value": len(specs) / wall_b,
+                      "latency_ms": serve.percentiles(rec_b), "clocks": clk_b}),
+          file=sys.stderr, flush=True)
     clocks = ClockSampler(0)
     clocks.start()
     outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs)

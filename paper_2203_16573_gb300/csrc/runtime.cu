@@ -727,6 +727,9 @@ int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, Ph
         // boxes of one block of kMarchB rows: p and C_p over the tile with a 2k
         // column halo, v_x with a k halo, v_z and kappa over the tile
         const int m = cfg - kCfgMarch0, TX = kMarchCfgs[m].tx, R = kMaxR, B = kMarchB;
+        // the choice may come from another context's tuning: this context's
+        // grid cap is looked up here if it is not known yet
+        if (!march_usable(c, m)) return fail(c, SSX_ERR_ARG, "marching kernel not available");
         std::vector<MarchJob> mj(jobs.size());
         for (size_t j = 0; j < jobs.size(); j++) {
             memset(&mj[j], 0, sizeof(MarchJob));
@@ -751,6 +754,7 @@ int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, Ph
     }
     if (cfg >= kNumTileCfgs) {
         const int base = cfg - kNumTileCfgs;
+        if (!tma_usable(c, base)) return fail(c, SSX_ERR_ARG, "TMA-staged kernel not available");
         const int TX = kTileCfgs[base].tx, TZ = kTileCfgs[base].tz, R = kMaxR;
         std::vector<TmaJob> tj(jobs.size());
         for (size_t j = 0; j < jobs.size(); j++) {

@@ -138,6 +138,42 @@ struct Staged {
     }
 };
 
+// The same region by 16-byte quads, where every staged row starts on a
+// 16-byte boundary (2k and the tile width multiples of 4 floats: orders 4
+// and 8): f(slot, smem row, smem column, k - k0, i - i0) for each quad of 4
+// consecutive columns, slot 0 .. StagedQ::N - 1 once unrolled. The quads of
+// the tile rows (with their x halo) and of the z halo rows are numbered
+// through the CTA's threads.
+template <int R, int TX, int TZ, int NT>
+struct StagedQ {
+    static constexpr int H = 2 * R, PW = TX + 2 * H, Q1 = PW / 4, Q2 = TX / 4;
+    static constexpr bool ok = H % 4 == 0 && TX % 4 == 0;
+    static constexpr int N1 = TZ * Q1, N2 = 2 * H * Q2;
+    static constexpr int NI1 = (N1 + NT - 1) / NT, NI2 = (N2 + NT - 1) / NT;
+    static constexpr int N = NI1 + NI2;
+    template <class F>
+    __device__ __forceinline__ static void each(F &&f) {
+#pragma unroll
+        for (int a = 0; a < NI1; a++) {
+            const int q = threadIdx.x + a * NT;
+            if (N1 % NT == 0 || q < N1) {
+                const int r = q / Q1, cq = q - r * Q1;
+                f(a, r + H, 4 * cq, r, 4 * cq - H);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NI2; a++) {
+            const int q = threadIdx.x + a * NT;
+            if (N2 % NT == 0 || q < N2) {
+                const int r = q / Q2, cq = q - r * Q2;
+                const int rr = r < H ? r : r + TZ;
+                f(NI1 + a, rr, H + 4 * cq, rr - H, 4 * cq);
+            }
+        }
+    }
+};
+__device__ __forceinline__ float4 ldf4(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+
 // Stage a field over tile + 2k halo; with PRE the staged value is C_p * field
 // (transpose step), C_p from the grid's precomputed field (B_p kappa~ inside
 // the grid, 0 outside: the storage's apron makes every address valid). The
@@ -159,6 +195,33 @@ __device__ __forceinline__ void stage_p(const GridArgs &g, const float *f, int i
     Staged<R, TX, TZ, NT>::each([&](int e, int sr, int sc, int dk, int di) {
         const float v = ldf(base + dk * pitch + di);
         sp[sr][sc] = PRE ? __fmul_rn(cp[e], v) : v;
+    });
+}
+// by quads (StagedQ::ok): C_p read ahead by stage_cp4, then the field
+template <int R, int TX, int TZ, int NT>
+__device__ __forceinline__ void stage_cp4(const GridArgs &g, int i0, int k0,
+                                          float4 (&cp)[StagedQ<R, TX, TZ, NT>::N]) {
+    const float *base = g.cpk + k0 * g.pitch + i0;
+    const int pitch = g.pitch;
+    StagedQ<R, TX, TZ, NT>::each([&](int e, int, int, int dk, int di) {
+        cp[e] = __ldg(reinterpret_cast<const float4 *>(base + dk * pitch + di));
+    });
+}
+template <int R, int TX, int TZ, int NT, bool PRE>
+__device__ __forceinline__ void stage_p4(const GridArgs &g, const float *f, int i0, int k0,
+                                         float (&sp)[TZ + 4 * R][TX + 4 * R],
+                                         const float4 (&cp)[StagedQ<R, TX, TZ, NT>::N]) {
+    const float *base = f + k0 * g.pitch + i0;
+    const int pitch = g.pitch;
+    StagedQ<R, TX, TZ, NT>::each([&](int e, int sr, int sc, int dk, int di) {
+        float4 v = ldf4(base + dk * pitch + di);
+        if (PRE) {
+            v.x = __fmul_rn(cp[e].x, v.x);
+            v.y = __fmul_rn(cp[e].y, v.y);
+            v.z = __fmul_rn(cp[e].z, v.z);
+            v.w = __fmul_rn(cp[e].w, v.w);
+        }
+        *reinterpret_cast<float4 *>(&sp[sr][sc]) = v;
     });
 }
 template <int R, int TX, int TZ, int NT, bool SP, bool PRE>
@@ -712,17 +775,30 @@ struct GlobalIn {
     // threads; larger CTAs (64 registers a thread) wait first, so that the
     // constants need not stay live across the wait
     static constexpr bool kAhead = NT <= 256;
-    float cpre[Staged<R, TX, TZ, NT>::N];
+    // orders 4 and 8 stage by 16-byte quads
+    static constexpr bool kQuad = StagedQ<R, TX, TZ, NT>::ok;
+    using SQ = StagedQ<R, TX, TZ, NT>;
+    float cpre[kQuad ? 1 : Staged<R, TX, TZ, NT>::N];
+    float4 cpre4[kQuad ? SQ::N : 1];
     template <bool PRE>
     __device__ __forceinline__ void prestage() {
-        if (PRE && kCpAhead) stage_cp<R, TX, TZ, NT>(g, i0, k0, cpre);
+        if (PRE && kCpAhead) {
+            if constexpr (kQuad) stage_cp4<R, TX, TZ, NT>(g, i0, k0, cpre4);
+            else stage_cp<R, TX, TZ, NT>(g, i0, k0, cpre);
+        }
     }
     // the previous step's fields are complete from here on
     __device__ __forceinline__ void wait() const { griddep_wait(); }
     template <bool PRE>
     __device__ __forceinline__ void stage() {
-        if (kCpAhead) stage_p<R, TX, TZ, NT, PRE>(g, io.p_in, i0, k0, spa, cpre);
-        else stage_p<R, TX, TZ, NT, SP, PRE>(g, io.p_in, i0, k0, spa);
+        if constexpr (kQuad) {
+            if (PRE && !kCpAhead) stage_cp4<R, TX, TZ, NT>(g, i0, k0, cpre4);
+            stage_p4<R, TX, TZ, NT, PRE>(g, io.p_in, i0, k0, spa, cpre4);
+        } else if (kCpAhead) {
+            stage_p<R, TX, TZ, NT, PRE>(g, io.p_in, i0, k0, spa, reinterpret_cast<const float(&)[Staged<R, TX, TZ, NT>::N]>(cpre));
+        } else {
+            stage_p<R, TX, TZ, NT, SP, PRE>(g, io.p_in, i0, k0, spa);
+        }
     }
     __device__ __forceinline__ float (&sp())[TZ + 4 * R][TX + 4 * R] { return spa; }
 };
@@ -1300,13 +1376,18 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
 // One time step of every sweep of a phase (launch t). The sweeps arrive as
 // the kernel parameter; the CTA finds its sweep and steps its tile if that
 // sweep is active in this launch.
-template <int R, int TX, int TZ, int NT>
+// ONE: the phase has a single sweep, so its arguments sit at fixed offsets of
+// the parameter bank and the step reads them as constant operands instead of
+// loading them through a runtime sweep index.
+template <int R, int TX, int TZ, int NT, bool ONE>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(const JobSet P, int t) {
     griddep_launch();
     int j = 0;
+    if (!ONE) {
 #pragma unroll
-    for (int q = 1; q < kMaxJobs; q++)
-        if (q < P.njobs && (int)blockIdx.x >= P.job[q].tile_base) j = q;
+        for (int q = 1; q < kMaxJobs; q++)
+            if (q < P.njobs && (int)blockIdx.x >= P.job[q].tile_base) j = q;
+    }
     const Job &J = P.job[j];
     const int st = t - J.offset;
     if (st < 0 || st >= J.nt) return;
@@ -1418,7 +1499,8 @@ struct Stencil {
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = pdl ? at : nullptr;
         cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT>, jobs, t);
+        if (jobs.njobs == 1) return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, true>, jobs, t);
+        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, false>, jobs, t);
     }
     template <int TX, int TZ, int NT>
     static cudaError_t multi_tab(const Job *jobs, int njobs, int total, int t, cudaStream_t s,
@@ -1460,7 +1542,8 @@ struct Stencil {
         if ((e = cudaFuncSetAttribute(k_fwd<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_adj<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_fwd_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_multi_tab<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_adj_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }

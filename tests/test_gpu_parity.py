@@ -174,6 +174,24 @@ def test_config2_full_solve_parity(ssx, oracle):
     assert abs(a - b) <= 1e-5 * abs(a)
 
 
+def test_second_context_reuses_the_phase_tuning(ssx):
+    """Phase tile choices are kept per shape for the process: a second
+    context of the single-shot workload's shapes runs its solve on the first
+    context's choices (including the TMA-staged kernel, whose grid cap the
+    second context looks up itself) and gets the same bits."""
+    spec = W.c2()
+    vel = W.velocity(spec)
+    a = ssx.Context.for_problem(spec, vel)
+    d = a.point_source_data(spec.x_d, spec.z_d, dev(W.ricker(spec)))
+    ha, hista, ita, _ = a.solve(d, spec.alpha, 3, 0.0)
+    ha = ha.clone()
+    a.close()
+    b = ssx.Context.for_problem(spec, vel)
+    hb, histb, itb, _ = b.solve(d, spec.alpha, 3, 0.0)
+    assert ita == itb == 3 and torch.equal(ha, hb)
+    np.testing.assert_array_equal(hista, histb)
+
+
 # ------------------------------------------------------------- edge cases --
 @pytest.mark.parametrize("nt", [1, 2, 7])
 def test_few_steps_and_single_point_lines(ssx, oracle, nt):
