@@ -23,14 +23,15 @@
 // not per strip), and only the x differences read shared memory.
 //
 // Operands come by TMA (2-D cp.async.bulk.tensor) in blocks of 8 rows: a ring
-// of four p chunks over the tile's width plus a 2k column halo (two in use,
-// two in flight), and three stages of the block's v_x (k halo), v_z and
-// kappa -- or, in the transposed step, C_p of the next p chunk, which each
-// thread multiplies into its own column (and 16 threads into the halo
-// columns) of that chunk, keeping its own pbar for the update. One mbarrier
-// per stage counts the bytes of one block's copies; thread 0 issues the
-// copies two blocks ahead, right after the barrier that retires the buffers
-// they overwrite.
+// of three p chunks over the tile's width plus a 2k column halo, and two
+// stages of the block's v_x (k halo), v_z and kappa -- or, in the transposed
+// step, C_p of the next p chunk, which each thread multiplies into its own
+// column (and 16 threads into the halo columns) of that chunk, keeping its
+// own pbar for the update. One mbarrier per stage counts the bytes of one
+// block's copies. Each thread takes what the p update needs from the block's
+// buffers (its old p, kappa) into registers before the block's barrier, so
+// that right after it thread 0 can refill the block's stage and ring slot
+// with the copies of the block two ahead.
 //
 // Every point takes the arithmetic of fwd_strip / adj_strip term for term,
 // through the plain formula where its block of rows and its warp's columns
@@ -52,8 +53,8 @@ namespace {
 
 constexpr int kR = 4;        // spatial order 8
 constexpr int kB = kMarchB;  // rows per block
-constexpr int kRing = 4;     // p chunks in shared memory
-constexpr int kStages = 3;   // per-block operand stages
+constexpr int kRing = 3;     // p chunks in shared memory
+constexpr int kStages = 2;   // per-block operand stages
 constexpr int kW = kB + 2 * kR - 1;   // p / q window down a column
 
 template <int TX>
@@ -65,7 +66,7 @@ struct MarchSmem {
         alignas(128) float vz[kB][TX];        // v_z old, half rows of v_z chunk b
         alignas(128) float k[kB][PW];         // kappa [kB][TX] (forward) | C_p of p chunk b+1 (transposed)
     } st[kStages];
-    float vxn[2][kB][VW];                     // the block's new v_x (or C_v vbar_x'), by block parity
+    float vxn[kB][VW];                        // the block's new v_x (or C_v vbar_x')
     Job job;                                  // the current tile's sweep
     alignas(8) unsigned long long bar[kStages];
 };
@@ -117,12 +118,18 @@ __device__ __forceinline__ void fwd_vz(const FwdArgs &a, const MarchThread &th, 
                                        float *vz_out, float (&zwin)[2 * kB]) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch, i = th.i;
+    // the rows' difference chains interleaved (each row's own order kept)
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++) dd[j] = fmaf(cc[m - 1], pw[j + kR - 1 + m] - pw[j + kR - m], dd[j]);
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int kz = k0 - kR + kB * b + j;
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) d = fmaf(cc[m - 1], pw[j + kR - 1 + m] - pw[j + kR - m], d);
+        const float d = dd[j];
         const float old = vzo[j][th.c];
         const bool own = kz >= k0 && kz < k0 + TZ;
         float vz;
@@ -160,16 +167,21 @@ __device__ __forceinline__ void fwd_vx(const FwdArgs &a, const MarchThread &th, 
                                        const float (&cc)[kR], float cv,
                                        const float (&ring)[kB][TX + 4 * kR],
                                        const float (&vxo)[kB][TX + 2 * kR], float *vx_out,
-                                       float (&vxn)[kB][TX + 2 * kR]) {
+                                       float (&vxn)[kB][TX + 2 * kR], float (&pold)[kB]) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch;
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++)
+            dd[j] = fmaf(cc[m - 1], ring[j][th.c + 2 * kR + m] - ring[j][th.c + 2 * kR + 1 - m], dd[j]);
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int k = kp0 + j;
-        const float *row = &ring[j][th.c + 2 * kR];
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
+        const float d = dd[j];
         const float old = vxo[j][th.c + kR];
         float vx;
         bool okx = true;
@@ -184,6 +196,7 @@ __device__ __forceinline__ void fwd_vx(const FwdArgs &a, const MarchThread &th, 
         }
         if (okx) st_out(vx_out + k * pitch, vx);
         vxn[j][th.c + kR] = vx;
+        pold[j] = ring[j][th.c + 2 * kR];   // p^n of the row, for its update after the barrier
     }
 }
 
@@ -226,22 +239,26 @@ __device__ __forceinline__ void vx_halo(const GridArgs &g, int i0, int kp0, cons
 template <int TX, bool GEN>
 __device__ __forceinline__ void fwd_p(const FwdArgs &a, const MarchThread &th, int kp0, int n,
                                       const float (&cc)[kR], const float (&zwin)[2 * kB],
-                                      const float (&vxn)[kB][TX + 2 * kR],
-                                      const float (&ring)[kB][TX + 4 * kR],
-                                      const float (&kap)[kB][TX], float *p_out) {
+                                      const float (&vxn)[kB][TX + 2 * kR], const float (&pold)[kB],
+                                      const float (&kap)[kB], float *p_out) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch, i = th.i;
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++) {
+            dd[j] = fmaf(cc[m - 1], vxn[j][th.c + kR + m - 1] - vxn[j][th.c + kR - m], dd[j]);
+            dd[j] = fmaf(cc[m - 1], zwin[j + kR + m - 1] - zwin[j + kR - m], dd[j]);
+        }
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int k = kp0 + j;
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) {
-            d = fmaf(cc[m - 1], vxn[j][th.c + kR + m - 1] - vxn[j][th.c + kR - m], d);
-            d = fmaf(cc[m - 1], zwin[j + kR + m - 1] - zwin[j + kR - m], d);
-        }
-        const float old = ring[j][th.c + 2 * kR];
-        float cp = kap[j][th.c], val;
+        const float d = dd[j];
+        const float old = pold[j];
+        float cp = kap[j], val;
         bool okp = true;
         if (!GEN) {
             val = fmaf(-cp, d, old);
@@ -278,13 +295,17 @@ __device__ __forceinline__ void adj_vz(const AdjArgs &a, const MarchThread &th, 
                                        float *vz_out, float (&zwin)[2 * kB]) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch, i = th.i;
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++) dd[j] = fmaf(cc[m - 1], qw[j + kR - 1 + m] - qw[j + kR - m], dd[j]);
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int kz = k0 - kR + kB * b + j;
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) d = fmaf(cc[m - 1], qw[j + kR - 1 + m] - qw[j + kR - m], d);
-        const float vb = vzo[j][th.c] + d;
+        const float vb = vzo[j][th.c] + dd[j];
         const bool own = kz >= k0 && kz < k0 + TZ;
         float vz, out;
         bool okz = true;
@@ -325,20 +346,25 @@ __device__ __forceinline__ void adj_vx(const AdjArgs &a, const MarchThread &th, 
                                        float (&vxn)[kB][TX + 2 * kR]) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch, i = th.i;
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++)
+            dd[j] = fmaf(cc[m - 1], ring[j][th.c + 2 * kR + m] - ring[j][th.c + 2 * kR + 1 - m], dd[j]);
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int k = kp0 + j;
-        const float *row = &ring[j][th.c + 2 * kR];
         if (GEN && a.hbar && th.colp) {   // hbar[n] = scale sum_k w_k q
             const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
             const int jl = i - a.src.i0;
             if (w != 0.0f && jl >= 0 && jl < a.src.n)
-                atomicAdd(&a.hbar[(size_t)n * a.src.n + jl], (double)(w * a.src.scale) * (double)row[0]);
+                atomicAdd(&a.hbar[(size_t)n * a.src.n + jl],
+                          (double)(w * a.src.scale) * (double)ring[j][th.c + 2 * kR]);
         }
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) d = fmaf(cc[m - 1], row[m] - row[1 - m], d);
-        const float vbx = vxo[j][th.c + kR] + d;
+        const float vbx = vxo[j][th.c + kR] + dd[j];
         float vx, ox;
         bool okx = true;
         if (!GEN) {
@@ -364,15 +390,20 @@ __device__ __forceinline__ void adj_p(const AdjArgs &a, const MarchThread &th, i
                                       float *p_out) {
     const GridArgs &g = a.g;
     const int NZ = g.NZ, pitch = g.pitch, i = th.i;
+    float dd[kB];
+#pragma unroll
+    for (int j = 0; j < kB; j++) dd[j] = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= kR; m++)
+#pragma unroll
+        for (int j = 0; j < kB; j++) {
+            dd[j] = fmaf(cc[m - 1], vxn[j][th.c + kR + m - 1] - vxn[j][th.c + kR - m], dd[j]);
+            dd[j] = fmaf(cc[m - 1], zwin[j + kR + m - 1] - zwin[j + kR - m], dd[j]);
+        }
 #pragma unroll
     for (int j = 0; j < kB; j++) {
         const int k = kp0 + j;
-        float d = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= kR; m++) {
-            d = fmaf(cc[m - 1], vxn[j][th.c + kR + m - 1] - vxn[j][th.c + kR - m], d);
-            d = fmaf(cc[m - 1], zwin[j + kR + m - 1] - zwin[j + kR - m], d);
-        }
+        const float d = dd[j];
         float out;
         bool okp = true;
         if (!GEN) {
@@ -465,18 +496,17 @@ __device__ __forceinline__ bool march_tile(const MarchJob *__restrict__ mj, cons
     if (threadIdx.x == 0 && !stall) {
         march_issue<TX>(mj, ADJ, odd, i0, k0, -1, NB, sm, bar0);
         march_issue<TX>(mj, ADJ, odd, i0, k0, 0, NB, sm, bar0);
-        march_issue<TX>(mj, ADJ, odd, i0, k0, 1, NB, sm, bar0);
     }
-    if (!wait(kStages - 1)) {
+    if (!wait((kStages - 1 + kStages) % kStages)) {
         if (stall) {   // nothing was issued: nothing in flight
             if (threadIdx.x == 0) atomicExch(err, 2);
         } else {
-            drain(-1, 1);
+            drain(-1, 0);
         }
         return false;
     }
     // the window of p (q) down the column: rows k0-2k+1 .. k0-1 of p chunk 0
-    float pw[kW], zwin[2 * kB], rp_cur[kB], rp_next[kB];
+    float pw[kW], zwin[2 * kB], rp_cur[kB], rp_next[kB], pold[kB], kap[kB];
     if (ADJ) {
         convert_chunk<TX>(sm.ring[0], sm.st[kStages - 1].k, c, false, rp_next);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // before TMA refills the slot
@@ -486,7 +516,9 @@ __device__ __forceinline__ bool march_tile(const MarchJob *__restrict__ mj, cons
 #pragma unroll
     for (int w = 0; w < 2 * kB; w++) zwin[w] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < kB; j++) rp_cur[j] = 0.0f;
+    for (int j = 0; j < kB; j++) rp_cur[j] = pold[j] = kap[j] = 0.0f;
+    __syncthreads();   // the prologue's stage is free again
+    if (threadIdx.x == 0) march_issue<TX>(mj, ADJ, odd, i0, k0, 1, NB, sm, bar0);
 
     for (int b = 0; b <= NB; b++) {
         const int s = b % kStages;
@@ -518,7 +550,6 @@ __device__ __forceinline__ bool march_tile(const MarchJob *__restrict__ mj, cons
             if (zfast) fwd_vz<TX, false>(J.fa, th, k0, TZ, b, n, cc, cv, pw, sm.st[s].vz, vz_out, zwin);
             else fwd_vz<TX, true>(J.fa, th, k0, TZ, b, n, cc, cv, pw, sm.st[s].vz, vz_out, zwin);
         }
-        float(&vxn)[kB][TX + 2 * kR] = sm.vxn[b & 1];
         const int rc = b % kRing;   // p chunk b: the rows whose v_x and p are updated
         bool pfast = false;
         if (b >= 1) {
@@ -528,26 +559,28 @@ __device__ __forceinline__ bool march_tile(const MarchJob *__restrict__ mj, cons
                          : !((J.fa.hsrc && hits(J.fa.src.kp, kp0, kp0 + kB)) ||
                              (J.fa.outp && hits(J.fa.rec.kp, kp0, kp0 + kB))));
             if (ADJ) {
-                if (xfast) adj_vx<TX, false>(J.aa, th, kp0, n, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, vxn);
-                else adj_vx<TX, true>(J.aa, th, kp0, n, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, vxn);
+                if (xfast) adj_vx<TX, false>(J.aa, th, kp0, n, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, sm.vxn);
+                else adj_vx<TX, true>(J.aa, th, kp0, n, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, sm.vxn);
             } else {
-                if (xfast) fwd_vx<TX, false>(J.fa, th, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, vxn);
-                else fwd_vx<TX, true>(J.fa, th, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, vxn);
+                if (xfast) fwd_vx<TX, false>(J.fa, th, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, sm.vxn, pold);
+                else fwd_vx<TX, true>(J.fa, th, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vx_out, sm.vxn, pold);
+                const float(&ks)[kB][TX] = reinterpret_cast<const float(&)[kB][TX]>(sm.st[s].k);
+#pragma unroll
+                for (int j = 0; j < kB; j++) kap[j] = ks[j][c];
             }
-            if (xhalo_in && pin) vx_halo<TX, false, ADJ>(g, i0, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vxn);
-            else vx_halo<TX, true, ADJ>(g, i0, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, vxn);
+            if (xhalo_in && pin) vx_halo<TX, false, ADJ>(g, i0, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, sm.vxn);
+            else vx_halo<TX, true, ADJ>(g, i0, kp0, cc, cv, sm.ring[rc], sm.st[s].vx, sm.vxn);
         }
-        __syncthreads();   // vxn complete; every thread is past block b-1
-        // copies two blocks ahead, into the stage and ring slot block b-1 used
+        __syncthreads();   // vxn complete; the block's stage and ring slot are read out
+        // copies two blocks ahead, into this block's stage and ring slot
         if (threadIdx.x == 0 && b + 2 <= NB) march_issue<TX>(mj, ADJ, odd, i0, k0, b + 2, NB, sm, bar0);
         if (b >= 1) {
             if (ADJ) {
-                if (pfast) adj_p<TX, false>(J.aa, th, kp0, n, cc, zwin, vxn, rp_cur, p_out);
-                else adj_p<TX, true>(J.aa, th, kp0, n, cc, zwin, vxn, rp_cur, p_out);
+                if (pfast) adj_p<TX, false>(J.aa, th, kp0, n, cc, zwin, sm.vxn, rp_cur, p_out);
+                else adj_p<TX, true>(J.aa, th, kp0, n, cc, zwin, sm.vxn, rp_cur, p_out);
             } else {
-                const float(&kap)[kB][TX] = reinterpret_cast<const float(&)[kB][TX]>(sm.st[s].k);
-                if (pfast) fwd_p<TX, false>(J.fa, th, kp0, n, cc, zwin, vxn, sm.ring[rc], kap, p_out);
-                else fwd_p<TX, true>(J.fa, th, kp0, n, cc, zwin, vxn, sm.ring[rc], kap, p_out);
+                if (pfast) fwd_p<TX, false>(J.fa, th, kp0, n, cc, zwin, sm.vxn, pold, kap, p_out);
+                else fwd_p<TX, true>(J.fa, th, kp0, n, cc, zwin, sm.vxn, pold, kap, p_out);
             }
         }
         // slide the windows by one block

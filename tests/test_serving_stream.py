@@ -37,9 +37,11 @@ def test_every_request_follows_the_recipe():
         assert 1000 <= s.nt <= 5000
         assert math.isclose(3.0 * s.dt / s.h, 0.25)           # CFL 0.25 at 3 km/s
         assert s.order == 8 and s.n_sponge == 40
-        k_s = s.z_s / s.h                                      # line on a grid row at 80 % depth
-        assert abs(k_s - round(k_s)) < 1e-9
-        assert abs(s.z_s - 0.8 * (s.nz - 1) * s.h) <= s.h / 2 + 1e-12
+        k_s = s.z_s / s.h                                      # line on a grid row at 80 % depth,
+        assert abs(k_s - round(k_s)) < 1e-9                    # or 0.6 km per second of record
+        zmax, T = (s.nz - 1) * s.h, s.nt * s.dt
+        assert abs(s.z_s - min(0.8 * zmax, max(0.6 * T, s.dz_datum + 4 * s.h))) <= s.h + 1e-12
+        assert s.z_s - s.dz_datum >= 4 * s.h - 1e-12
         i_s = s.x_s / s.h                                      # shot on a column, inside the middle 3/5
         assert abs(i_s - round(i_s)) < 1e-9 and s.nx // 5 <= round(i_s) < 4 * s.nx // 5
         assert (s.x_d, s.z_d) == (s.x_s, s.z_s)
@@ -50,10 +52,12 @@ def test_every_request_follows_the_recipe():
 
 
 def test_scaled_stream_keeps_odd_grids_and_minimum_sizes():
-    for _, s in serve.request_specs(50, 4.0, seed=3, scale=0.05):
-        assert s.nx % 2 == 1 and s.nz % 2 == 1
-        assert s.nx >= 33 and s.nz >= 25 and s.nt >= 60
-        assert s.n_sponge == 20
+    for scale in (0.05, 0.12):
+        for _, s in serve.request_specs(50, 4.0, seed=3, scale=scale):
+            assert s.nx % 2 == 1 and s.nz % 2 == 1
+            assert s.nx >= 33 and s.nz >= 25 and s.nt >= 60
+            assert s.n_sponge == 20
+            assert s.z_s - s.dz_datum >= 4 * s.h - 1e-12 and s.z_s <= (s.nz - 1) * s.h
 
 
 def test_latency_percentiles():
