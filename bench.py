@@ -571,7 +571,8 @@ def run_serve(args):
     serve.serve(specs[:2], inputs[:2], realtime=False)          # warm-up (kernels, allocator)
     clocks = ClockSampler(0)
     clocks.start()
-    outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9)
+    st_b, st_s = {}, {}
+    outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9, stats=st_b)
     clk_b = clocks.stop()
     # the batched arm on its own first, on stderr (kept if the second arm fails)
     print(json.dumps({"partial": "continuous batching", "value": len(specs) / wall_b,
@@ -579,7 +580,7 @@ def run_serve(args):
           file=sys.stderr, flush=True)
     clocks = ClockSampler(0)
     clocks.start()
-    outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs)
+    outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs, stats=st_s)
     clk_s = clocks.stop()
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
     pb, ps = serve.percentiles(rec_b), serve.percentiles(rec_s)
@@ -599,7 +600,16 @@ def run_serve(args):
             "iterations": [r["iters"] for r in rec_b],
             "status_counts": {k: sum(1 for r in rec_b if r["status"] == k)
                               for k in sorted(set(r["status"] for r in rec_b))},
-            "clocks": clk_b, "clocks_one_at_a_time": clk_s}
+            "clocks": clk_b, "clocks_one_at_a_time": clk_s,
+            "device": {"batched": {"wall_s": wall_b, "sweep_s": st_b.get("sweep_ms", 0) / 1000.0,
+                                   "gpt_updates_per_sweep_s": st_b.get("timed_point_updates", 0) /
+                                   max(st_b.get("sweep_ms", 0), 1e-9) / 1e6,
+                                   "rounds": st_b.get("rounds"),
+                                   "requests_per_round": st_b.get("request_rounds", 0) /
+                                   max(st_b.get("rounds", 0) or 1, 1)},
+                       "one_at_a_time": {"wall_s": wall_s, "sweep_s": st_s.get("sweep_ms", 0) / 1000.0,
+                                         "gpt_updates_per_sweep_s": st_s.get("timed_point_updates", 0) /
+                                         max(st_s.get("sweep_ms", 0), 1e-9) / 1e6}}}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -247,6 +247,14 @@ int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued);
  * submit-to-done latency and submit-to-admit wait in ms (host clock). */
 int ssx_server_poll(ssx_server *sv, int id, int *done, int *status, int *iters, double *latency_ms,
                     double *queue_ms);
+/* Instrumentation of the server's shared launches: ssx_server_set_timing
+ * brackets them with CUDA events (as ssx_set_timing does for a context);
+ * ssx_server_get_stats returns their counters since creation (kernel
+ * launches, point updates, event-timed phase time; synchronises when timing)
+ * and, if not NULL, the engine rounds run and the requests in them summed
+ * over the rounds. */
+int ssx_server_set_timing(ssx_server *sv, int on);
+int ssx_server_get_stats(ssx_server *sv, ssx_stats *out, long long *rounds, long long *request_rounds);
 int ssx_server_destroy(ssx_server *sv);
 const char *ssx_server_last_error(const ssx_server *sv);
 

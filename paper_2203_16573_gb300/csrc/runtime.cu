@@ -1514,6 +1514,7 @@ struct ssx_server {
     std::vector<Req *> active;
     std::unordered_map<int, Req *> all;
     std::string err;
+    long long rounds = 0, request_rounds = 0;   // engine rounds run, and requests in them
 };
 
 namespace {
@@ -2220,6 +2221,8 @@ int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued) {
         }
         std::vector<ShotRun *> runs;
         for (auto *q : sv->active) runs.push_back(&q->run);
+        sv->rounds++;
+        sv->request_rounds += (long long)runs.size();
         int rc = engine_round(L, runs);
         if (rc != SSX_OK) {
             sv->err = L->err;
@@ -2250,6 +2253,23 @@ int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued) {
     }
     if (n_active) *n_active = (int)sv->active.size();
     if (n_queued) *n_queued = (int)sv->queue.size();
+    return SSX_OK;
+}
+
+int ssx_server_set_timing(ssx_server *sv, int on) {
+    if (!sv) return SSX_ERR_ARG;
+    return ssx_set_timing(sv->lead, on);
+}
+
+int ssx_server_get_stats(ssx_server *sv, ssx_stats *out, long long *rounds, long long *request_rounds) {
+    if (!sv || !out) return SSX_ERR_ARG;
+    const int rc = ssx_get_stats(sv->lead, out);
+    if (rc != SSX_OK) {
+        sv->err = sv->lead->err;
+        return rc;
+    }
+    if (rounds) *rounds = sv->rounds;
+    if (request_rounds) *request_rounds = sv->request_rounds;
     return SSX_OK;
 }
 

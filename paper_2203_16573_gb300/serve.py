@@ -76,11 +76,14 @@ def make_inputs(specs, device="cuda"):
     return inputs
 
 
-def serve(specs, inputs, hbm_budget_bytes=80 * 10 ** 9, order=8, realtime=True):
+def serve(specs, inputs, hbm_budget_bytes=80 * 10 ** 9, order=8, realtime=True, stats=None):
     """Continuous batching: requests are submitted at their arrival times
     (host clock from the start) and served by one ssx_server. Returns
-    (outputs, per-request records, wall seconds)."""
+    (outputs, per-request records, wall seconds); `stats` (a dict, optional)
+    receives the server's counters with its shared launches event-timed."""
     srv = ssx.Server(order, hbm_budget_bytes)
+    if stats is not None:
+        srv.set_timing(True)
     outs = [torch.empty(sp.nt, sp.n_line, dtype=torch.float64, device="cuda") for _, sp in specs]
     ids = [None] * len(specs)
     t0 = time.perf_counter()
@@ -104,14 +107,18 @@ def serve(specs, inputs, hbm_budget_bytes=80 * 10 ** 9, order=8, realtime=True):
         if a == 0 and q == 0 and nxt < len(specs):   # idle until the next arrival
             time.sleep(max(0.0, min(0.01, specs[nxt][0] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
+    if stats is not None:
+        stats.update(srv.stats())
     srv.close()
     return outs, records, wall
 
 
-def serve_one_at_a_time(specs, inputs, realtime=True):
+def serve_one_at_a_time(specs, inputs, realtime=True, stats=None):
     """The plain one-shot-at-a-time solve: requests in arrival order, each
-    solved alone; latency = completion - arrival."""
+    solved alone; latency = completion - arrival. `stats` (optional) receives
+    the summed event-timed sweep time and point updates of the solves."""
     outs, records = [], []
+    tot = {"sweep_ms": 0.0, "timed_point_updates": 0.0, "kernel_launches": 0}
     t0 = time.perf_counter()
     for (arr, sp), (vel, d) in zip(specs, inputs):
         if realtime:
@@ -123,14 +130,22 @@ def serve_one_at_a_time(specs, inputs, realtime=True):
         ctx.set_velocity_model(vel, sp.rho)
         ctx.set_geometry(sp.z_s, sp.ix_line0, sp.n_line, sp.z_r, sp.ix_rec0, sp.n_rec, sp.x_s,
                          sp.dz_datum)
+        if stats is not None:
+            ctx.set_timing(True)
         h, hist, iters, status = ctx.solve(d, sp.alpha, sp.maxit, sp.rtol, allow_breakdown=True)
         torch.cuda.synchronize()
+        if stats is not None:
+            st = ctx.stats()
+            for k in tot:
+                tot[k] += st[k]
         ctx.close()
         end = time.perf_counter() - t0
         outs.append(h)
         records.append({"done": True, "status": status, "iters": iters,
                         "latency_ms": 1000.0 * (end - (arr if realtime else 0.0)),
                         "queue_ms": 1000.0 * (start - (arr if realtime else 0.0))})
+    if stats is not None:
+        stats.update(tot)
     return outs, records, time.perf_counter() - t0
 
 

@@ -35,7 +35,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_set_tile_config", "ssx_lambda_apply", "ssx_time_reversal_inverse",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
            "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
-           "ssx_velocity_gradient", "ssx_last_objective", "ssx_set_test_hook"]
+           "ssx_velocity_gradient", "ssx_last_objective", "ssx_set_test_hook",
+           "ssx_server_set_timing", "ssx_server_get_stats"]
 
 
 class SSXError(RuntimeError):
@@ -113,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         "ssx_velocity_gradient": ([vp, vp, vp, d, i, vp, P(d)], i),
         "ssx_last_objective": ([vp, P(d)], i),
         "ssx_set_test_hook": ([vp, i, i], i),
+        "ssx_server_set_timing": ([vp, i], i),
+        "ssx_server_get_stats": ([vp, P(Stats), P(ctypes.c_longlong), P(ctypes.c_longlong)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -381,6 +384,21 @@ class Server:
             self._keep.pop(rid, None)
         return {"done": bool(done.value), "status": STATUS[st.value], "iters": it.value,
                 "latency_ms": lat.value, "queue_ms": wait.value}
+
+    def set_timing(self, on: bool):
+        rc = self._lib.ssx_server_set_timing(self._s, 1 if on else 0)
+        if rc != SSX_OK:
+            raise SSXError(rc, self._lib.ssx_server_last_error(self._s).decode())
+
+    def stats(self) -> dict:
+        """The shared launches' counters (ssx_server_get_stats)."""
+        st, r, rr = Stats(), ctypes.c_longlong(0), ctypes.c_longlong(0)
+        rc = self._lib.ssx_server_get_stats(self._s, ctypes.byref(st), ctypes.byref(r), ctypes.byref(rr))
+        if rc != SSX_OK:
+            raise SSXError(rc, self._lib.ssx_server_last_error(self._s).decode())
+        d = st.as_dict()
+        d["rounds"], d["request_rounds"] = r.value, rr.value
+        return d
 
     def close(self):
         if self._s:
