@@ -28,7 +28,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <deque>
 #include <functional>
 #include <map>
@@ -67,6 +69,23 @@ struct EvPair {
     double points = 0.0;
 };
 
+// Kernel arguments of a phase: small phases by value, large ones in a device
+// table; for the TMA-staged and the marching kernels, a table of sweeps with
+// their tensor maps.
+struct PhaseArgs {
+    JobSet set{};
+    Job *dtab = nullptr;
+    TmaJob *ttab = nullptr;
+    MarchJob *mtab = nullptr;
+    int njobs = 0, total = 0, cap = 0;
+};
+// Launches [t0, t1) of a phase: the span over which the same sweeps step,
+// and the arguments of those sweeps alone.
+struct PhaseSeg {
+    int t0 = 0, t1 = 0;
+    PhaseArgs pa;
+};
+
 struct Slab {
     DGrid g;
     Line plane{}, datum{};         // lines in slab coordinates
@@ -99,12 +118,9 @@ struct ssx_ctx {
 
     // multi-sweep phases: tile configuration and device job table per phase
     struct PhaseInfo {
-        int cfg = -1;
-        JobSet jobs{};          // small phases: by-value kernel parameter
-        Job *dtab = nullptr;    // large phases (batches): device table
-        TmaJob *ttab = nullptr; // TMA-staged kernel: sweeps with their tensor maps
-        MarchJob *mtab = nullptr;  // marching kernel: sweeps with their tensor maps
-        int njobs = 0, total = 0, T = 0, cap = 0;
+        int cfg = -1, T = 0;
+        std::vector<PhaseSeg> segs;   // spans of launches with the same stepping sweeps
+        void *tabmem = nullptr;       // their device tables (one allocation)
     };
     std::unordered_map<std::string, PhaseInfo> phases;
 
@@ -168,7 +184,6 @@ int fail(ssx_ctx *c, int code, const std::string &msg) {
         if (rc_ != SSX_OK) return rc_; \
     } while (0)
 
-int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // Phase-kernel configuration ids: 0 .. 7 the plain tile kernel (shape id),
 // 8 .. 15 the TMA-staged tile kernel of shape id - 8, 16 .. 19 the marching
@@ -664,15 +679,6 @@ std::vector<Job> make_jobs(const std::vector<Sweep> &sw, int cfg, bool quiet, in
     return jobs;
 }
 
-// Kernel arguments of a phase: small phases by value, large ones in a device
-// table; for the TMA-staged kernel, a table of sweeps with their tensor maps.
-struct PhaseArgs {
-    JobSet set{};
-    Job *dtab = nullptr;
-    TmaJob *ttab = nullptr;
-    MarchJob *mtab = nullptr;
-    int njobs = 0, total = 0, cap = 0;
-};
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -716,65 +722,80 @@ bool tma_usable(ssx_ctx *c, int base) {
     return c->tma_cap[base] > 0 && tensor_map_encoder() != nullptr;
 }
 
-int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
-               Job **dtab, TmaJob **ttab, MarchJob **mtab) {
+// tensor maps of one sweep for the marching kernel of shape m: boxes of one
+// block of kMarchB rows -- p and C_p over the tile with a 2k column halo, v_x
+// with a k halo, v_z and kappa over the tile
+bool march_job(const Sweep &w, const Job &job, int m, MarchJob *out) {
+    const int TX = kMarchCfgs[m].tx, R = kMaxR, B = kMarchB;
+    memset(out, 0, sizeof(MarchJob));
+    out->job = job;
+    const DGrid &G = *w.G;
+    bool ok = true;
+    for (int b = 0; b < 2; b++) {
+        ok = ok && field_map(&out->map[b], G.f[b][0], G.L, TX + 4 * R, B);
+        ok = ok && field_map(&out->map[2 + b], G.f[b][1], G.L, TX + 2 * R, B);
+        ok = ok && field_map(&out->map[4 + b], G.f[b][2], G.L, TX, B);
+    }
+    ok = ok && field_map(&out->map[6], G.args.kap, G.L, TX, B);
+    ok = ok && field_map(&out->map[7], G.args.cpk, G.L, TX + 4 * R, B);
+    return ok;
+}
+
+// tensor maps of one sweep for the TMA-staged kernel of shape `base`: boxes
+// of the tile with its halos
+bool tma_job(const Sweep &w, const Job &job, int base, TmaJob *out) {
+    const int TX = kTileCfgs[base].tx, TZ = kTileCfgs[base].tz, R = kMaxR;
+    memset(out, 0, sizeof(TmaJob));
+    out->job = job;
+    const DGrid &G = *w.G;
+    bool ok = true;
+    for (int b = 0; b < 2; b++) {
+        ok = ok && field_map(&out->map[b], G.f[b][0], G.L, TX + 4 * R, TZ + 4 * R);
+        ok = ok && field_map(&out->map[2 + b], G.f[b][1], G.L, TX + 2 * R, TZ);
+        ok = ok && field_map(&out->map[4 + b], G.f[b][2], G.L, TX, TZ + 2 * R - 1);
+    }
+    ok = ok && (job.adj ? field_map(&out->map[6], G.args.cpk, G.L, TX + 4 * R, TZ + 4 * R)
+                        : field_map(&out->map[6], G.args.kap, G.L, TX, TZ));
+    return ok;
+}
+
+// Kernel arguments of a set of sweeps in configuration cfg, with any device
+// table appended to `host` at a 128-byte aligned offset (recorded in the
+// PhaseArgs pointer fields as an offset until the table is uploaded).
+int stage_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
+               std::vector<unsigned char> &host) {
     std::vector<Job> jobs = make_jobs(sw, cfg, quiet, &pa->total);
     pa->njobs = (int)jobs.size();
     pa->dtab = nullptr;
     pa->ttab = nullptr;
     pa->mtab = nullptr;
+    auto append = [&](const void *src, size_t bytes) -> size_t {
+        const size_t off = (host.size() + 127) / 128 * 128;
+        host.resize(off + bytes);
+        memcpy(host.data() + off, src, bytes);
+        return off;
+    };
+    // offsets are kept +1 in the pointer fields until the upload resolves them
+    auto tag = [](size_t off) { return (void *)(off + 1); };
     if (cfg >= kCfgMarch0) {
-        // boxes of one block of kMarchB rows: p and C_p over the tile with a 2k
-        // column halo, v_x with a k halo, v_z and kappa over the tile
-        const int m = cfg - kCfgMarch0, TX = kMarchCfgs[m].tx, R = kMaxR, B = kMarchB;
+        const int m = cfg - kCfgMarch0;
         // the choice may come from another context's tuning: this context's
         // grid cap is looked up here if it is not known yet
         if (!march_usable(c, m)) return fail(c, SSX_ERR_ARG, "marching kernel not available");
         std::vector<MarchJob> mj(jobs.size());
-        for (size_t j = 0; j < jobs.size(); j++) {
-            memset(&mj[j], 0, sizeof(MarchJob));
-            mj[j].job = jobs[j];
-            const DGrid &G = *sw[j].G;
-            bool ok = true;
-            for (int b = 0; b < 2; b++) {
-                ok = ok && field_map(&mj[j].map[b], G.f[b][0], G.L, TX + 4 * R, B);
-                ok = ok && field_map(&mj[j].map[2 + b], G.f[b][1], G.L, TX + 2 * R, B);
-                ok = ok && field_map(&mj[j].map[4 + b], G.f[b][2], G.L, TX, B);
-            }
-            ok = ok && field_map(&mj[j].map[6], G.args.kap, G.L, TX, B);
-            ok = ok && field_map(&mj[j].map[7], G.args.cpk, G.L, TX + 4 * R, B);
-            if (!ok) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
-        }
-        if (!*mtab) CK(cudaMalloc(mtab, mj.size() * sizeof(MarchJob)));
-        CK(cudaMemcpyAsync(*mtab, mj.data(), mj.size() * sizeof(MarchJob), cudaMemcpyHostToDevice, c->s));
-        CK(cudaStreamSynchronize(c->s));
-        pa->mtab = *mtab;
+        for (size_t j = 0; j < jobs.size(); j++)
+            if (!march_job(sw[j], jobs[j], m, &mj[j])) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
+        pa->mtab = (MarchJob *)tag(append(mj.data(), mj.size() * sizeof(MarchJob)));
         pa->cap = c->march_cap[m];
         return SSX_OK;
     }
     if (cfg >= kNumTileCfgs) {
         const int base = cfg - kNumTileCfgs;
         if (!tma_usable(c, base)) return fail(c, SSX_ERR_ARG, "TMA-staged kernel not available");
-        const int TX = kTileCfgs[base].tx, TZ = kTileCfgs[base].tz, R = kMaxR;
         std::vector<TmaJob> tj(jobs.size());
-        for (size_t j = 0; j < jobs.size(); j++) {
-            memset(&tj[j], 0, sizeof(TmaJob));
-            tj[j].job = jobs[j];
-            const DGrid &G = *sw[j].G;
-            bool ok = true;
-            for (int b = 0; b < 2; b++) {
-                ok = ok && field_map(&tj[j].map[b], G.f[b][0], G.L, TX + 4 * R, TZ + 4 * R);
-                ok = ok && field_map(&tj[j].map[2 + b], G.f[b][1], G.L, TX + 2 * R, TZ);
-                ok = ok && field_map(&tj[j].map[4 + b], G.f[b][2], G.L, TX, TZ + 2 * R - 1);
-            }
-            ok = ok && (jobs[j].adj ? field_map(&tj[j].map[6], G.args.cpk, G.L, TX + 4 * R, TZ + 4 * R)
-                                    : field_map(&tj[j].map[6], G.args.kap, G.L, TX, TZ));
-            if (!ok) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
-        }
-        if (!*ttab) CK(cudaMalloc(ttab, tj.size() * sizeof(TmaJob)));
-        CK(cudaMemcpyAsync(*ttab, tj.data(), tj.size() * sizeof(TmaJob), cudaMemcpyHostToDevice, c->s));
-        CK(cudaStreamSynchronize(c->s));
-        pa->ttab = *ttab;
+        for (size_t j = 0; j < jobs.size(); j++)
+            if (!tma_job(sw[j], jobs[j], base, &tj[j])) return fail(c, SSX_ERR_CUDA, "tensor map encoding failed");
+        pa->ttab = (TmaJob *)tag(append(tj.data(), tj.size() * sizeof(TmaJob)));
         pa->cap = c->tma_cap[base];
         return SSX_OK;
     }
@@ -782,14 +803,40 @@ int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, Ph
         memset(&pa->set, 0, sizeof pa->set);
         pa->set.njobs = pa->njobs;
         for (size_t j = 0; j < jobs.size(); j++) pa->set.job[j] = jobs[j];
-        pa->dtab = nullptr;
         return SSX_OK;
     }
-    if (!*dtab) CK(cudaMalloc(dtab, jobs.size() * sizeof(Job)));
-    CK(cudaMemcpyAsync(*dtab, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, c->s));
-    CK(cudaStreamSynchronize(c->s));
-    pa->dtab = *dtab;
+    pa->dtab = (Job *)tag(append(jobs.data(), jobs.size() * sizeof(Job)));
     return SSX_OK;
+}
+
+// upload the tables staged by stage_args (one allocation, one copy) and turn
+// the recorded offsets into device pointers
+int upload_args(ssx_ctx *c, const std::vector<unsigned char> &host, std::vector<PhaseArgs *> args,
+                void **mem) {
+    *mem = nullptr;
+    if (host.empty()) return SSX_OK;
+    CK(cudaMalloc(mem, host.size()));
+    CK(cudaMemcpyAsync(*mem, host.data(), host.size(), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    unsigned char *base = (unsigned char *)*mem;
+    auto fix = [&](auto *&ptr) {
+        if (ptr) ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + ((size_t)ptr - 1));
+    };
+    for (PhaseArgs *pa : args) {
+        fix(pa->dtab);
+        fix(pa->ttab);
+        fix(pa->mtab);
+    }
+    return SSX_OK;
+}
+
+// Kernel arguments of a phase in one set (the tuner's short runs); *mem
+// receives the device table, if any, for the caller to free.
+int phase_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, PhaseArgs *pa,
+               void **mem) {
+    std::vector<unsigned char> host;
+    TRY(stage_args(c, sw, cfg, quiet, pa, host));
+    return upload_args(c, host, {pa}, mem);
 }
 
 int phase_len(const std::vector<Sweep> &sw) {
@@ -800,9 +847,9 @@ int phase_len(const std::vector<Sweep> &sw) {
 
 // the launches of a phase: transposed sweeps get their initial state (the
 // transposed sampling of their last data sample) just before their first step
-int enqueue_phase(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int T, int cfg,
-                  cudaStream_t s, bool with_init, bool stall = false) {
-    for (int t = 0; t < T; t++) {
+int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int t0, int t1,
+                     int cfg, cudaStream_t s, bool with_init, bool stall = false) {
+    for (int t = t0; t < t1; t++) {
         if (with_init)
             for (const Sweep &w : sw)
                 if (w.adj && w.offset == t) {
@@ -890,9 +937,6 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
     const int T = std::min(phase_len(sw), 48);
     float best = 1e30f;
     int rc = SSX_OK;
-    Job *tmp = nullptr;
-    TmaJob *ttmp = nullptr;
-    MarchJob *mtmp = nullptr;
     for (int k = 0; k < kNumAllCfgs && rc == SSX_OK; k++) {
         if (k >= kCfgMarch0) {
             if (!march_usable(c, k - kCfgMarch0)) continue;
@@ -900,14 +944,18 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
             continue;
         }
         PhaseArgs pa;
-        rc = phase_args(c, sw, k, true, &pa, &tmp, &ttmp, &mtmp);
+        void *tmem = nullptr;
+        rc = phase_args(c, sw, k, true, &pa, &tmem);
         if (rc != SSX_OK) break;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_phase(c, sw, pa, T, k, c->s, false);
+        rc = enqueue_launches(c, sw, pa, 0, T, k, c->s, false);
         cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
-        if (rc != SSX_OK) break;
+        if (rc != SSX_OK) {
+            if (tmem) cudaFree(tmem);
+            break;
+        }
         CK(ec);
         cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -923,6 +971,7 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
             if (rep > 0) ms = std::min(ms, t);
         }
         cudaGraphExecDestroy(exec);
+        if (tmem) cudaFree(tmem);
         if (c->log_tuning)
             std::fprintf(stderr, "ssx tune: phase %s (%zu sweeps, %d tiles) config %d: %.3f us/step\n",
                          name, sw.size(), pa.total, k, 1000.0 * ms / T);
@@ -931,9 +980,6 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
             *best_cfg = k;
         }
     }
-    if (tmp) cudaFree(tmp);
-    if (ttmp) cudaFree(ttmp);
-    if (mtmp) cudaFree(mtmp);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == SSX_OK) {
@@ -962,24 +1008,35 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         ssx_ctx::PhaseInfo info;
         TRY(tune_phase(c, name, sw, &info.cfg));
         TRY(check_sweeps_quiet(c));
-        PhaseArgs pa;
-        TRY(phase_args(c, sw, info.cfg, false, &pa, &info.dtab, &info.ttab, &info.mtab));
-        info.cap = pa.cap;
-        info.jobs = pa.set;
-        info.njobs = pa.njobs;
-        info.total = pa.total;
+        // The phase's launches split where a sweep starts or ends: each span
+        // launches only the sweeps that step in it (a batch whose shots have
+        // different step counts launches no CTAs for finished sweeps).
+        std::vector<int> bounds;
+        for (const Sweep &w : sw) {
+            bounds.push_back(w.offset);
+            bounds.push_back(w.offset + w.nt);
+        }
+        std::sort(bounds.begin(), bounds.end());
+        bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
+        std::vector<unsigned char> host;
+        for (size_t q = 0; q + 1 < bounds.size(); q++) {
+            std::vector<Sweep> sub;
+            for (const Sweep &w : sw)
+                if (w.offset <= bounds[q] && bounds[q] < w.offset + w.nt) sub.push_back(w);
+            if (sub.empty()) continue;
+            PhaseSeg seg;
+            seg.t0 = bounds[q];
+            seg.t1 = bounds[q + 1];
+            TRY(stage_args(c, sub, info.cfg, false, &seg.pa, host));
+            info.segs.push_back(seg);
+        }
+        std::vector<PhaseArgs *> args;
+        for (PhaseSeg &seg : info.segs) args.push_back(&seg.pa);
+        TRY(upload_args(c, host, args, &info.tabmem));
         info.T = phase_len(sw);
-        it = c->phases.emplace(key, info).first;
+        it = c->phases.emplace(key, std::move(info)).first;
     }
     const ssx_ctx::PhaseInfo &info = it->second;
-    PhaseArgs pa;
-    pa.set = info.jobs;
-    pa.dtab = info.dtab;
-    pa.ttab = info.ttab;
-    pa.mtab = info.mtab;
-    pa.cap = info.cap;
-    pa.njobs = info.njobs;
-    pa.total = info.total;
     // test hook: the next TMA-staged phase withholds the copies of its first
     // tile in its first launch (run uncached, so no graph keeps the stall)
     const bool stall = c->stall_next && info.cfg >= kNumTileCfgs;
@@ -995,7 +1052,9 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
             if (w.fb) CK(cudaMemsetAsync(w.fb, 0, ns, s));
             CK(cudaMemsetAsync(w.G->mem + E, 0, 3 * E * sizeof(float), s));
         }
-        return enqueue_phase(c, sw, pa, info.T, info.cfg, s, true, stall);
+        for (const PhaseSeg &seg : info.segs)
+            TRY(enqueue_launches(c, sw, seg.pa, seg.t0, seg.t1, info.cfg, s, true, stall));
+        return SSX_OK;
     };
     double pts = 0;
     long long inits = 0;
@@ -1205,11 +1264,8 @@ int slab_setup(ssx_ctx *c, Slab &sl, double z0, double zd, int ix0, int n) {
 }
 
 void drop_phases(ssx_ctx *c) {
-    for (auto &kv : c->phases) {
-        if (kv.second.dtab) cudaFree(kv.second.dtab);
-        if (kv.second.ttab) cudaFree(kv.second.ttab);
-        if (kv.second.mtab) cudaFree(kv.second.mtab);
-    }
+    for (auto &kv : c->phases)
+        if (kv.second.tabmem) cudaFree(kv.second.tabmem);
     c->phases.clear();
 }
 
