@@ -312,7 +312,7 @@ int ssx_set_test_hook(ssx_ctx *ctx, int hook, int k);
  * tiles copied by the tensor memory accelerator into a two-stage shared-memory
  * pipeline, persistent CTAs), available for space order 8; for other orders
  * 8 + k runs shape k; 16 + m fixes the marching kernel of shape m (tiles of
- * 64 x 128, 64 x 64, 128 x 64, 32 x 128 points, one thread per column walking
+ * 64 x 128, 128 x 64, 128 x 128, 128 x 32 points, one thread per column walking
  * down it in blocks of 8 rows fed by tensor copies), available for space
  * order 8 (else shape 0 runs). All configurations compute identical results. */
 #define SSX_NUM_TILE_CONFIGS 8

@@ -945,8 +945,10 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
         }
         PhaseArgs pa;
         void *tmem = nullptr;
-        rc = phase_args(c, sw, k, true, &pa, &tmem);
-        if (rc != SSX_OK) break;
+        if (phase_args(c, sw, k, true, &pa, &tmem) != SSX_OK) {   // a candidate that cannot be set up
+            if (tmem) cudaFree(tmem);
+            continue;
+        }
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));

@@ -180,9 +180,9 @@ extern const TileCfg kTileCfgs[kNumTileCfgs];
 // Marching-kernel shapes: (id, tile width = threads per CTA, tile height).
 #define SSX_MARCH_CONFIGS(X) \
     X(0, 64, 128)            \
-    X(1, 64, 64)             \
-    X(2, 128, 64)            \
-    X(3, 32, 128)
+    X(1, 128, 64)            \
+    X(2, 128, 128)           \
+    X(3, 128, 32)
 constexpr int kNumMarchCfgs = 4;
 extern const TileCfg kMarchCfgs[kNumMarchCfgs];
 

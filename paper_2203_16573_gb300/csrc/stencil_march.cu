@@ -9,7 +9,7 @@
 // survey that is ~210 instructions per grid point, and the step is bound by
 // instruction issue, not by DRAM.
 //
-// Here one thread owns one column of a TX x TZ tile (TZ = 64 or 128 rows) and
+// Here one thread owns one column of a TX x TZ tile (TZ = 32 to 128 rows) and
 // walks down it in blocks of kMarchB = 8 rows, carrying the windows down the
 // column in registers: the last 2k-1 values of p (or q = C_p pbar) for the
 // D+ of v_z, and the v_z of the previous block for the D- of p. Block b
@@ -60,6 +60,8 @@ constexpr int kW = kB + 2 * kR - 1;   // p / q window down a column
 template <int TX>
 struct MarchSmem {
     static constexpr int PW = TX + 4 * kR, VW = TX + 2 * kR;
+    static_assert(PW <= 256, "a tensor-copy box spans at most 256 elements a dimension");
+    static_assert(TX % 32 == 0, "one thread a column, whole warps");
     alignas(128) float ring[kRing][kB][PW];   // p (forward) or q = C_p pbar (transposed), x = i0-2k ..
     struct alignas(128) Stage {
         alignas(128) float vx[kB][VW];        // v_x old, x = i0-k .. i0+TX+k-1, rows of p chunk b
