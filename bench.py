@@ -572,7 +572,9 @@ def run_serve(args):
     clocks = ClockSampler(0)
     clocks.start()
     st_b, st_s = {}, {}
-    outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9, stats=st_b)
+    cache = None if args.cache_mb < 0 else int(args.cache_mb * 1e6)
+    outs_b, rec_b, wall_b = serve.serve(specs, inputs, args.budget_gb * 1e9, stats=st_b,
+                                        cache_budget=cache)
     clk_b = clocks.stop()
     # the batched arm on its own first, on stderr (kept if the second arm fails)
     print(json.dumps({"partial": "continuous batching", "value": len(specs) / wall_b,
@@ -592,7 +594,8 @@ def run_serve(args):
             "config": {"workload": f"{len(specs)} requests, Poisson rate {args.rate}/s, grids "
                                    f"{{401x201,1001x401,2001x801}} x {args.scale}, nt 1000-5000 x "
                                    f"{args.scale}, order 8, maxit {args.maxit}, rtol 1e-3, "
-                                   f"HBM budget {args.budget_gb} GB",
+                                   f"HBM budget {args.budget_gb} GB, working-set limit "
+                                   f"{'L2 size' if args.cache_mb < 0 else str(args.cache_mb) + ' MB'}",
                        "arrival_span_s": specs[-1][0]},
             "latency_ms": pb, "one_at_a_time": {"value": len(specs) / wall_s, "unit": "solves/s",
                                                 "latency_ms": ps},
@@ -716,6 +719,8 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--cache-mb", type=float, default=-1,
+                    help="serve: working-set admission limit in MB (0: off; default: the L2 size)")
     ap.add_argument("--tile-config", type=int, default=-1,
                     help="fix the stencil tile configuration (0-7; 8-15: TMA-staged phase kernel of shape 0-7) instead of autotuning")
     ap.add_argument("--shots", type=int, default=64)

@@ -1537,18 +1537,24 @@ int solve_batch(std::vector<ShotRun> &shots) {
 // admitted while their estimated device memory fits the budget, join the
 // engine at the next round (sharing every launch with the solves already
 // running), and leave when they stop, freeing their memory for the queue.
-static size_t estimate_bytes(const ssx_grid_desc &g, const ssx_geom_desc &m) {
+// Device memory of a request's grids (the full grid and its three slabs:
+// kappa, two ping-pong field triples and C_p each), which its sweeps step
+// through every phase: the request's working set.
+static size_t field_bytes(const ssx_grid_desc &g, const ssx_geom_desc &m) {
     const int nsp = g.n_sponge;
     auto grid_bytes = [&](int nx, int nz) {
-        const int NX = nx + 2 * nsp, NZ = nz + 2 * nsp;
-        const size_t pitch = ((((NX + TILE_X_MAX - 1) / TILE_X_MAX) * TILE_X_MAX + 2 * GX + 31) / 32) * 32;
-        const size_t rows = ((NZ + TILE_Z_MAX - 1) / TILE_Z_MAX) * TILE_Z_MAX + 2 * GZ;
-        return 8 * pitch * rows * 4 + (size_t)4096 * 4;
+        const FieldLayout L = field_layout(nx + 2 * nsp, nz + 2 * nsp);
+        return 8 * L.elems() * sizeof(float) + (size_t)4096 * 4;
     };
     const int slab_rows = (int)std::ceil(m.dz_datum / g.h) + 3 + g.space_order;
+    return grid_bytes(g.nx, g.nz) + 3 * grid_bytes(g.nx, slab_rows);
+}
+
+// A request's device memory: its grids, gathers and model copy.
+static size_t estimate_bytes(const ssx_grid_desc &g, const ssx_geom_desc &m) {
     const size_t nl = (size_t)g.nt * m.n_line, nr = (size_t)g.nt * m.n_rec;
-    return grid_bytes(g.nx, g.nz) + 3 * grid_bytes(g.nx, slab_rows) +
-           (7 * nl + 2 * nr + 4 * nl + 2 * nr) * 8 + (size_t)g.nx * g.nz * 4 + ((size_t)1 << 20);
+    return field_bytes(g, m) + (7 * nl + 2 * nr + 4 * nl + 2 * nr) * 8 + (size_t)g.nx * g.nz * 4 +
+           ((size_t)1 << 20);
 }
 
 struct ssx_server {
@@ -1560,12 +1566,16 @@ struct ssx_server {
         double rho = 1.0;
         ShotRun run;
         ssx_ctx *c = nullptr;
-        size_t bytes = 0;
+        size_t bytes = 0, ws = 0;   // device memory, working set (field_bytes)
         double t_submit = 0, t_admit = 0, t_done = 0;
         bool done = false;
     };
     ssx_ctx *lead = nullptr;       // owns the stream, the phase launches and their statistics
     size_t budget = 0, used = 0;
+    // admission also keeps the active requests' working sets within this many
+    // bytes (the L2 cache by default; 0: no limit), so that a batch's fields
+    // stay cache-resident between time steps
+    size_t cache_budget = 0, used_ws = 0;
     int order = 8;
     int next_id = 1;
     std::deque<Req *> queue;
@@ -1585,7 +1595,11 @@ double now_ms() {
 int server_admit(ssx_server *sv) {
     while (!sv->queue.empty()) {
         ssx_server::Req *q = sv->queue.front();
-        if (sv->used + q->bytes > sv->budget && !sv->active.empty()) break;   // wait for memory
+        // first in, first out: the head waits until it fits (or runs alone)
+        if (!sv->active.empty() &&
+            (sv->used + q->bytes > sv->budget ||
+             (sv->cache_budget && sv->used_ws + q->ws > sv->cache_budget)))
+            break;
         sv->queue.pop_front();
         ssx_ctx *c = nullptr;
         int rc = ssx_create(&c, &q->g, sv->lead->user);
@@ -1603,6 +1617,7 @@ int server_admit(ssx_server *sv) {
         q->run.c = c;
         q->t_admit = now_ms();
         sv->used += q->bytes;
+        sv->used_ws += q->ws;
         sv->active.push_back(q);
     }
     return SSX_OK;
@@ -2227,11 +2242,21 @@ int ssx_server_create(ssx_server **out, int space_order, size_t hbm_budget_bytes
         delete sv;
         return rc;
     }
-    // requests come and go every round: launch phases directly (no graph
-    // capture per membership) with one fixed tile configuration
+    // requests come and go every few rounds: launch phases directly (no graph
+    // capture per membership); tile configurations come from the phase tuner,
+    // which keeps its choice per size class of batch for the process
     sv->lead->use_graphs = false;
-    sv->lead->forced_cfg = 1;
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
+        sv->cache_budget = (size_t)l2;
     *out = sv;
+    return SSX_OK;
+}
+
+int ssx_server_set_cache_budget(ssx_server *sv, size_t bytes) {
+    if (!sv) return SSX_ERR_ARG;
+    sv->cache_budget = bytes;
     return SSX_OK;
 }
 
@@ -2258,6 +2283,7 @@ int ssx_server_submit(ssx_server *sv, const ssx_grid_desc *grid, const ssx_geom_
     q->run.d = d_dev;
     q->run.h_out = h_out_dev;
     q->bytes = estimate_bytes(*grid, *geom);
+    q->ws = field_bytes(*grid, *geom);
     q->t_submit = now_ms();
     sv->queue.push_back(q);
     sv->all[q->id] = q;
@@ -2301,6 +2327,7 @@ int ssx_server_step(ssx_server *sv, int *n_active, int *n_queued) {
             q->c = nullptr;
             q->run.c = nullptr;
             sv->used -= q->bytes;
+            sv->used_ws -= q->ws;
             changed = true;
         }
         sv->active.swap(keep);

@@ -76,12 +76,15 @@ def make_inputs(specs, device="cuda"):
     return inputs
 
 
-def serve(specs, inputs, hbm_budget_bytes=80 * 10 ** 9, order=8, realtime=True, stats=None):
+def serve(specs, inputs, hbm_budget_bytes=80 * 10 ** 9, order=8, realtime=True, stats=None,
+          cache_budget=None):
     """Continuous batching: requests are submitted at their arrival times
     (host clock from the start) and served by one ssx_server. Returns
     (outputs, per-request records, wall seconds); `stats` (a dict, optional)
     receives the server's counters with its shared launches event-timed."""
     srv = ssx.Server(order, hbm_budget_bytes)
+    if cache_budget is not None:
+        srv.set_cache_budget(cache_budget)
     if stats is not None:
         srv.set_timing(True)
     outs = [torch.empty(sp.nt, sp.n_line, dtype=torch.float64, device="cuda") for _, sp in specs]

@@ -36,7 +36,7 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
            "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
            "ssx_velocity_gradient", "ssx_last_objective", "ssx_set_test_hook",
-           "ssx_server_set_timing", "ssx_server_get_stats"]
+           "ssx_server_set_timing", "ssx_server_get_stats", "ssx_server_set_cache_budget"]
 
 
 class SSXError(RuntimeError):
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "ssx_last_objective": ([vp, P(d)], i),
         "ssx_set_test_hook": ([vp, i, i], i),
         "ssx_server_set_timing": ([vp, i], i),
+        "ssx_server_set_cache_budget": ([vp, ctypes.c_size_t], i),
         "ssx_server_get_stats": ([vp, P(Stats), P(ctypes.c_longlong), P(ctypes.c_longlong)], i),
     }
     for name, (args, res) in sig.items():
@@ -384,6 +385,12 @@ class Server:
             self._keep.pop(rid, None)
         return {"done": bool(done.value), "status": STATUS[st.value], "iters": it.value,
                 "latency_ms": lat.value, "queue_ms": wait.value}
+
+    def set_cache_budget(self, nbytes: int):
+        """Working-set admission limit in bytes (0: off; default: the L2 size)."""
+        rc = self._lib.ssx_server_set_cache_budget(self._s, int(nbytes))
+        if rc != SSX_OK:
+            raise SSXError(rc, "ssx_server_set_cache_budget failed")
 
     def set_timing(self, on: bool):
         rc = self._lib.ssx_server_set_timing(self._s, 1 if on else 0)
