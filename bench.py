@@ -580,6 +580,10 @@ def run_serve(args):
     print(json.dumps({"partial": "continuous batching", "value": len(specs) / wall_b,
                       "latency_ms": serve.percentiles(rec_b), "clocks": clk_b}),
           file=sys.stderr, flush=True)
+    if args.no_solo:   # the batched arm alone (policy sweeps)
+        print(json.dumps({"value": len(specs) / wall_b, "latency_ms": serve.percentiles(rec_b),
+                          "cache_mb": args.cache_mb, "device": st_b}), flush=True)
+        return 0
     clocks = ClockSampler(0)
     clocks.start()
     outs_s, rec_s, wall_s = serve.serve_one_at_a_time(specs, inputs, stats=st_s)
@@ -719,6 +723,8 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--no-solo", action="store_true",
+                    help="serve: run the batched arm only (no one-at-a-time comparison)")
     ap.add_argument("--cache-mb", type=float, default=-1,
                     help="serve: working-set admission limit in MB (0: off; default: the L2 size)")
     ap.add_argument("--tile-config", type=int, default=-1,
