@@ -599,7 +599,7 @@ def run_serve(args):
                                    f"{{401x201,1001x401,2001x801}} x {args.scale}, nt 1000-5000 x "
                                    f"{args.scale}, order 8, maxit {args.maxit}, rtol 1e-3, "
                                    f"HBM budget {args.budget_gb} GB, working-set limit "
-                                   f"{'L2 size' if args.cache_mb < 0 else str(args.cache_mb) + ' MB'}",
+                                   f"{'4x L2 size' if args.cache_mb < 0 else str(args.cache_mb) + ' MB'}",
                        "arrival_span_s": specs[-1][0]},
             "latency_ms": pb, "one_at_a_time": {"value": len(specs) / wall_s, "unit": "solves/s",
                                                 "latency_ms": ps},
@@ -726,7 +726,7 @@ def main():
     ap.add_argument("--no-solo", action="store_true",
                     help="serve: run the batched arm only (no one-at-a-time comparison)")
     ap.add_argument("--cache-mb", type=float, default=-1,
-                    help="serve: working-set admission limit in MB (0: off; default: the L2 size)")
+                    help="serve: working-set admission limit in MB (0: off; default: 4x the L2 size)")
     ap.add_argument("--tile-config", type=int, default=-1,
                     help="fix the stencil tile configuration (0-7; 8-15: TMA-staged phase kernel of shape 0-7) instead of autotuning")
     ap.add_argument("--shots", type=int, default=64)

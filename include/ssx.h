@@ -249,11 +249,11 @@ int ssx_server_poll(ssx_server *sv, int id, int *done, int *status, int *iters, 
                     double *queue_ms);
 /* Working-set admission: besides the memory budget, requests are admitted
  * (first in, first out) only while the active requests' grids -- the fields
- * their sweeps step through at every time step -- fit in `bytes`, so that a
- * batch stays resident in the L2 cache between time steps instead of
- * streaming from HBM; a request that does not fit waits until it fits or
- * would run alone. The default is the device's L2 size; 0 switches the limit
- * off (admission by the memory budget alone). */
+ * their sweeps step through -- fit in `bytes`, so that a batch stays close to
+ * the L2 cache's size instead of growing into one long all-request round
+ * that streams from HBM; a request that does not fit waits until it fits or
+ * would run alone. The default is four times the device's L2 size; 0
+ * switches the limit off (admission by the memory budget alone). */
 int ssx_server_set_cache_budget(ssx_server *sv, size_t bytes);
 /* Instrumentation of the server's shared launches: ssx_server_set_timing
  * brackets them with CUDA events (as ssx_set_timing does for a context);

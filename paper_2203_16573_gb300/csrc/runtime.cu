@@ -2246,10 +2246,12 @@ int ssx_server_create(ssx_server **out, int space_order, size_t hbm_budget_bytes
     // capture per membership); tile configurations come from the phase tuner,
     // which keeps its choice per size class of batch for the process
     sv->lead->use_graphs = false;
+    // working-set limit: four times the L2 size (on the full-size serving mix
+    // 4x L2 served more requests per second than 1x, 2x or no limit)
     int dev = 0, l2 = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
-        sv->cache_budget = (size_t)l2;
+        sv->cache_budget = 4 * (size_t)l2;
     *out = sv;
     return SSX_OK;
 }

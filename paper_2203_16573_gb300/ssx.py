@@ -387,7 +387,7 @@ class Server:
                 "latency_ms": lat.value, "queue_ms": wait.value}
 
     def set_cache_budget(self, nbytes: int):
-        """Working-set admission limit in bytes (0: off; default: the L2 size)."""
+        """Working-set admission limit in bytes (0: off; default: 4x the L2 size)."""
         rc = self._lib.ssx_server_set_cache_budget(self._s, int(nbytes))
         if rc != SSX_OK:
             raise SSXError(rc, "ssx_server_set_cache_budget failed")
