@@ -270,6 +270,11 @@ def run_ours(args):
     clk = clocks.stop()
     ctx.set_timing(False)
     st = ctx.stats()
+    phases = [{"phase": r["phase"], "sweeps": r["sweeps"], "tiles": r["tiles"],
+               "kernel": _kernel_name(r["tile_config"]), "tile_config": r["tile_config"],
+               "us_per_step": 1000.0 * r["ms"] / max(r["steps"], 1), "steps": r["steps"],
+               "share": r["ms"] / max(st["sweep_ms"], 1e-9)}
+              for r in ctx.phase_stats()]
     t_max = reduce_max(t_dev, dev)
     ms_per_step = t_max / args.steps
     value = replica_throughput(world, args.steps, t_max)
@@ -347,6 +352,7 @@ def run_ours(args):
             "stencil_gpt_updates_per_s": gpts,
             "stencil_share_of_timed_region": st["sweep_ms"] / t_dev if t_dev else None,
             "point_updates_per_solve": st["point_updates"] / args.steps,
+            "phases": phases,
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "solves/s",
                     "h2d_bytes_per_step": d_host.numel() * 8, "d2h_bytes_per_step": h_host.numel() * 8},
@@ -684,6 +690,22 @@ def run_pcgcg(args):
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def _kernel_name(cfg):
+    """The phase kernel and tile shape a tile configuration id names."""
+    from paper_2203_16573_gb300 import ssx
+    nt = ssx.N_TILE_CONFIGS
+    shapes = ["64x16/256", "64x16/512", "32x32/256", "64x32/512", "64x32/1024", "128x16/512",
+              "128x32/1024", "32x16/256"]
+    march = ["64x128", "128x64", "128x128", "128x32"]
+    if 0 <= cfg < nt:
+        return "k_multi " + shapes[cfg]
+    if nt <= cfg < 2 * nt:
+        return "k_multi_tma " + shapes[cfg - nt]
+    if 2 * nt <= cfg < 2 * nt + len(march):
+        return "k_march " + march[cfg - 2 * nt]
+    return str(cfg)
 
 
 def _stencil_hash():

@@ -335,6 +335,19 @@ int ssx_set_timing(ssx_ctx *ctx, int on);
 int ssx_get_stats(ssx_ctx *ctx, ssx_stats *out);
 int ssx_reset_stats(ssx_ctx *ctx);
 
+/* Per-phase breakdown of the timed sweeps (timing mode), since creation or
+ * the last reset. A phase is one set of sweeps stepped together, one launch a
+ * time step (the solve's phases e1-e4 of Algorithm 1's operators); phases of
+ * the same name, sweep count, tile count and kernel configuration share a
+ * row. Row k (from 0, in order of first appearance): the phase's name
+ * (NUL-terminated, truncated to name_len - 1 characters), its sweeps, the
+ * tiles of its largest launch, its tile configuration (0-7 plain kernel,
+ * 8-15 TMA-staged, 16-19 marching), its event-timed device time and its
+ * time steps (launches). SSX_ERR_ARG for k past the last row or a NULL
+ * output. Synchronises. */
+int ssx_get_phase_stats(ssx_ctx *ctx, int k, char *name, int name_len, int *sweeps, int *tiles,
+                        int *tile_cfg, double *ms, long long *steps);
+
 /* Capacity, in floats (16 MiB), of the fixed device scratch array used by
  * ssx_forward_noalloc. */
 #define SSX_NOALLOC_MAX_FLOATS 4194304

@@ -67,6 +67,16 @@ struct EvPair {
     cudaEvent_t a = nullptr, b = nullptr;
     long long steps = 0;
     double points = 0.0;
+    int tag = -1;          // row of the phase breakdown (-1: not a phase)
+};
+
+// One row of the per-phase breakdown of timed sweeps: a phase name with its
+// sweep count, tile count and kernel configuration.
+struct PhaseRow {
+    std::string name;
+    int sweeps = 0, tiles = 0, cfg = -1;
+    double ms = 0.0;
+    long long steps = 0;
 };
 
 // Kernel arguments of a phase: small phases by value, large ones in a device
@@ -161,6 +171,9 @@ struct ssx_ctx {
     std::vector<EvPair> evs;
     size_t ev_used = 0;
     ssx_stats st{};
+    std::vector<PhaseRow> phase_rows;          // timed phases, in order of first appearance
+    std::unordered_map<std::string, int> phase_row_of;
+    int cur_tag = -1;                          // row of the phase being enqueued
 };
 
 namespace {
@@ -335,6 +348,7 @@ int run_cached(ssx_ctx *c, const std::string &key, long long nodes, long long st
         ev = &c->evs[c->ev_used++];
         ev->steps = steps;
         ev->points = points;
+        ev->tag = c->cur_tag;
         CK(cudaEventRecord(ev->a, c->s));
     }
     // A key's launches are captured into a graph the second time it runs:
@@ -1065,6 +1079,27 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         inits += w.adj ? 1 : 0;
     }
     c->st.sweeps += (long long)sw.size() - 1;   // run_cached counts one
+    if (c->timing) {   // the phase's row of the timing breakdown
+        int tiles = 0;
+        for (const PhaseSeg &seg : info.segs) tiles = std::max(tiles, seg.pa.total);
+        const std::string rk = std::string(name) + "|" + std::to_string(sw.size()) + "|" +
+                               std::to_string(tiles) + "|" + std::to_string(info.cfg);
+        auto r = c->phase_row_of.find(rk);
+        if (r == c->phase_row_of.end()) {
+            PhaseRow row;
+            row.name = name;
+            row.sweeps = (int)sw.size();
+            row.tiles = tiles;
+            row.cfg = info.cfg;
+            c->phase_rows.push_back(row);
+            r = c->phase_row_of.emplace(rk, (int)c->phase_rows.size() - 1).first;
+        }
+        c->cur_tag = r->second;
+    }
+    struct TagReset {
+        ssx_ctx *c;
+        ~TagReset() { c->cur_tag = -1; }
+    } tag_reset{c};
     if (stall) {
         const bool g0 = c->use_graphs;
         c->use_graphs = false;
@@ -2200,19 +2235,29 @@ int ssx_set_timing(ssx_ctx *c, int on) {
     return SSX_OK;
 }
 
+// Folds the recorded sweep events into the counters (synchronises).
+static int resolve_events(ssx_ctx *c) {
+    if (!c->ev_used) return SSX_OK;
+    CK(cudaStreamSynchronize(c->s));
+    for (size_t i = 0; i < c->ev_used; i++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->evs[i].a, c->evs[i].b));
+        c->st.sweep_ms += ms;
+        c->st.timed_steps += c->evs[i].steps;
+        c->st.timed_point_updates += c->evs[i].points;
+        const int tag = c->evs[i].tag;
+        if (tag >= 0 && tag < (int)c->phase_rows.size()) {
+            c->phase_rows[tag].ms += ms;
+            c->phase_rows[tag].steps += c->evs[i].steps;
+        }
+    }
+    c->ev_used = 0;
+    return SSX_OK;
+}
+
 int ssx_get_stats(ssx_ctx *c, ssx_stats *out) {
     if (!c || !out) return SSX_ERR_ARG;
-    if (c->ev_used) {
-        CK(cudaStreamSynchronize(c->s));
-        for (size_t i = 0; i < c->ev_used; i++) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->evs[i].a, c->evs[i].b));
-            c->st.sweep_ms += ms;
-            c->st.timed_steps += c->evs[i].steps;
-            c->st.timed_point_updates += c->evs[i].points;
-        }
-        c->ev_used = 0;
-    }
+    TRY(resolve_events(c));
     *out = c->st;
     const DGrid *gs[3] = {&c->full, &c->ss.g, &c->sr.g};
     for (int k = 0; k < 3; k++)
@@ -2226,6 +2271,24 @@ int ssx_reset_stats(ssx_ctx *c) {
     if (c->ev_used) CK(cudaStreamSynchronize(c->s));
     c->ev_used = 0;
     c->st = ssx_stats{};
+    c->phase_rows.clear();
+    c->phase_row_of.clear();
+    return SSX_OK;
+}
+
+int ssx_get_phase_stats(ssx_ctx *c, int k, char *name, int name_len, int *sweeps, int *tiles,
+                        int *tile_cfg, double *ms, long long *steps) {
+    if (!c || k < 0 || !name || name_len < 1 || !sweeps || !tiles || !tile_cfg || !ms || !steps)
+        return SSX_ERR_ARG;
+    TRY(resolve_events(c));
+    if (k >= (int)c->phase_rows.size()) return SSX_ERR_ARG;
+    const PhaseRow &r = c->phase_rows[k];
+    snprintf(name, (size_t)name_len, "%s", r.name.c_str());
+    *sweeps = r.sweeps;
+    *tiles = r.tiles;
+    *tile_cfg = r.cfg;
+    *ms = r.ms;
+    *steps = r.steps;
     return SSX_OK;
 }
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libssx.so")
 SSX_OK = 0
 STATUS = {0: "SSX_OK", 1: "SSX_ERR_ARG", 2: "SSX_ERR_CUDA", 3: "SSX_ERR_CFL", 4: "SSX_ERR_OOM",
           5: "SSX_ERR_BREAKDOWN", 6: "SSX_ERR_NONFINITE", 7: "SSX_ERR_NOT_CONVERGED"}
+ERR_ARG = 1
 MODE_PCG, MODE_CG = 0, 1
 SWEEP_AUTO, SWEEP_STEP, SWEEP_PERSISTENT, SWEEP_TEST_STALL = 0, 1, 2, 3
 W_D, W_M, W_M_INV = 0, 1, 2
@@ -36,7 +37,8 @@ EXPORTS = ["ssx_version", "ssx_create", "ssx_destroy", "ssx_last_error",
            "ssx_solve_batch", "ssx_server_create", "ssx_server_submit", "ssx_server_step",
            "ssx_server_poll", "ssx_server_destroy", "ssx_server_last_error",
            "ssx_velocity_gradient", "ssx_last_objective", "ssx_set_test_hook",
-           "ssx_server_set_timing", "ssx_server_get_stats", "ssx_server_set_cache_budget"]
+           "ssx_server_set_timing", "ssx_server_get_stats", "ssx_server_set_cache_budget",
+           "ssx_get_phase_stats"]
 
 
 class SSXError(RuntimeError):
@@ -99,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         "ssx_set_timing": ([vp, i], i),
         "ssx_get_stats": ([vp, P(Stats)], i),
         "ssx_reset_stats": ([vp], i),
+        "ssx_get_phase_stats": ([vp, i, ctypes.c_char_p, i, P(ctypes.c_int), P(ctypes.c_int),
+                                 P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_longlong)], i),
         "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
         "ssx_set_sweep_mode": ([vp, i], i),
         "ssx_set_tile_config": ([vp, i], i),
@@ -310,6 +314,22 @@ class Context:
 
     def reset_stats(self):
         self._check(self._lib.ssx_reset_stats(self._c))
+
+    def phase_stats(self) -> list:
+        """Per-phase breakdown of the timed sweeps (ssx_get_phase_stats)."""
+        rows = []
+        name = ctypes.create_string_buffer(64)
+        sw, tl, cfg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms, steps = ctypes.c_double(), ctypes.c_longlong()
+        while True:
+            rc = self._lib.ssx_get_phase_stats(self._c, len(rows), name, 64, ctypes.byref(sw),
+                                               ctypes.byref(tl), ctypes.byref(cfg),
+                                               ctypes.byref(ms), ctypes.byref(steps))
+            if rc == ERR_ARG:
+                return rows
+            self._check(rc)
+            rows.append({"phase": name.value.decode(), "sweeps": sw.value, "tiles": tl.value,
+                         "tile_config": cfg.value, "ms": ms.value, "steps": steps.value})
 
 
 def solve_batch(ctxs, ds, alphas, maxit, rtol, mode=MODE_PCG, outs=None):

@@ -105,3 +105,20 @@ def test_every_entry_point_rejects_a_null_handle_without_touching_the_device(lib
     assert len(checked) == len(ssx.EXPORTS) - len(skip)
     assert lib.ssx_last_error(None) == b"null context"
     assert lib.ssx_server_last_error(None) == b"null server"
+
+
+def test_bench_kernel_names_match_the_configuration_tables():
+    """bench.py names each phase's kernel from its configuration id: its
+    tables of shapes must be the library's."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "ssx_internal.cuh")).read()
+    tile = re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)", src)
+    march = re.findall(r"X\((\d+), (\d+), (\d+)\)\s", src)
+    assert len(tile) == 8 and len(march) == 4
+    for cid, tx, tz, nt in tile:
+        assert bench._kernel_name(int(cid)) == f"k_multi {tx}x{tz}/{nt}"
+        assert bench._kernel_name(int(cid) + 8) == f"k_multi_tma {tx}x{tz}/{nt}"
+    for cid, tx, tz in march:
+        assert bench._kernel_name(int(cid) + 16) == f"k_march {tx}x{tz}"

@@ -376,6 +376,30 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     assert len(st["tile_cfg"]) == 6
 
 
+def test_phase_breakdown_accounts_for_the_timed_sweeps(ssx):
+    """ssx_get_phase_stats: a timed PCG solve has rows for its four phases,
+    each with its launches (time steps) and device time; together with the
+    operator sweeps outside phases they make up the timed sweeps."""
+    spec = W.small(order=8, nt=200)
+    ctx = ssx.Context.for_problem(spec, W.velocity(spec))
+    d = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 31))
+    ctx.solve(d, 0.1, 2, 0.0)
+    ctx.reset_stats()
+    assert ctx.phase_stats() == []
+    ctx.set_timing(True)
+    ctx.solve(d, 0.1, 2, 0.0)
+    ctx.set_timing(False)
+    rows = ctx.phase_stats()
+    st = ctx.stats()
+    names = {r["phase"] for r in rows}
+    assert {"e1", "e2", "e3", "e4"} <= names, rows
+    for r in rows:
+        assert r["ms"] > 0 and r["steps"] >= spec.nt and r["sweeps"] >= 1 and r["tiles"] >= 1
+        assert 0 <= r["tile_config"] < 2 * ssx.N_TILE_CONFIGS + ssx.N_MARCH_CONFIGS
+    assert sum(r["ms"] for r in rows) <= st["sweep_ms"] * (1 + 1e-6)
+    assert sum(r["steps"] for r in rows) <= st["timed_steps"]
+
+
 def test_model_change_refreshes_captured_sweeps(ssx, oracle):
     """Captured sweeps hold the grid coefficients: a new model (and density)
     on the same context must give the new operator."""
