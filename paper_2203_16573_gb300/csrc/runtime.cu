@@ -887,8 +887,9 @@ int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &
                                 stall && t == 0 ? 0 : -1, s, true));
         else if (pa.dtab)
             CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, true));
-        else
-            CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, true));
+        else   // the span's first launch is not a dependent launch: its sweeps
+               // may read their injected gathers before the grid dependency wait
+            CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, t != t0));
     }
     return SSX_OK;
 }

@@ -747,9 +747,13 @@ struct GlobalIn {
     const int i0, k0, pitch;
     const float *vxp, *vzp, *kp, *pp;
     float (&spa)[TZ + 4 * R][TX + 4 * R];
+    // the sweep's injected gathers were complete before the launch chain
+    // began (no sweep of the phase produces them): the step may read its
+    // line values before the grid dependency wait, with the constants
+    const bool lines_ready;
     __device__ __forceinline__ GlobalIn(const GridArgs &g_, const StepIO &io_, int i0_, int k0_,
-                                        int rs, int c, TileSmem<R, TX, TZ> &sm)
-        : g(g_), io(io_), i0(i0_), k0(k0_), pitch(g_.pitch), spa(sm.sp) {
+                                        int rs, int c, TileSmem<R, TX, TZ> &sm, bool lines_ready_)
+        : g(g_), io(io_), i0(i0_), k0(k0_), pitch(g_.pitch), spa(sm.sp), lines_ready(lines_ready_) {
         const int o0 = (k0 + rs) * pitch + i0 + c;
         vxp = io.vx_in + o0;
         vzp = io.vz_in + o0;
@@ -840,7 +844,19 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
             szh[j] = __ldg(g.szh + min(k, NZ - 1));
         }
     }
+    // the line's values injected at this step in the thread's column (the
+    // same for every row the line's weights reach): with the constants when
+    // they are ready before the wait, else with the fields after it
+    const int js = i - a.src.i0;
+    const bool jsin = LN && js >= 0 && js < a.src.n;
+    float fsv = 0.0f, hsv = 0.0f;
+    auto line_values = [&]() {
+        if (jsin && a.fsrc) fsv = (float)__ldcg(a.fsrc + (size_t)n * a.src.n + js);
+        if (jsin && a.hsrc) hsv = (float)__ldcg(a.hsrc + (size_t)n * a.src.n + js);
+    };
+    if (LN && in.lines_ready) line_values();
     if (In::kAhead) in.wait();
+    if (LN && !in.lines_ready) line_values();
 #pragma unroll
     for (int j = 0; j < L; j++) {
         rvx[j] = in.own_vx(j);
@@ -876,9 +892,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         }
         if (LN && a.fsrc && okz) {   // vertical load f e_z delta(z - z_s)
             const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-            const int js = i - a.src.i0;
-            if (w != 0.0f && js >= 0 && js < a.src.n)
-                vz = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], vz);
+            if (w != 0.0f && jsin) vz = fmaf(cvz * (w * a.src.scale), fsv, vz);
         }
         if (SP) vz = okz ? vz : 0.0f;
         if (okz) st_out(io.vz_out + k * pitch + i, vz);
@@ -949,9 +963,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         }
         if (LN && a.fsrc && ok) {
             const float w = row_weight(k, a.src.kv, a.src.wv0, a.src.wv1);
-            const int js = i - a.src.i0;
-            if (w != 0.0f && js >= 0 && js < a.src.n)
-                val = fmaf(cvz * (w * a.src.scale), (float)a.fsrc[(size_t)n * a.src.n + js], val);
+            if (w != 0.0f && jsin) val = fmaf(cvz * (w * a.src.scale), fsv, val);
         }
         sm.svz[kk][c] = ok ? val : 0.0f;
     }
@@ -982,9 +994,7 @@ __device__ __forceinline__ void fwd_strip(const FwdArgs &a, const StepIO &io, in
         }
         if (LN && a.hsrc && okp) {   // constitutive defect h delta(z - z_s)
             const float w = row_weight(k, a.src.kp, a.src.wp0, a.src.wp1);
-            const int js = i - a.src.i0;
-            if (w != 0.0f && js >= 0 && js < a.src.n)
-                val = fmaf(cp * (w * a.src.scale), (float)a.hsrc[(size_t)n * a.src.n + js], val);
+            if (w != 0.0f && jsin) val = fmaf(cp * (w * a.src.scale), hsv, val);
         }
         if (okp) st_out(io.p_out + k * pitch + i, val);
         if (LN && a.outp && okp) {   // P p trace
@@ -1032,7 +1042,19 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         }
     }
     in.template prestage<true>();   // C_p of the staged region (constants)
+    // the adjoint data of step n-1 injected in the thread's column (both of
+    // a line's rows take the same value): with the constants when they are
+    // ready before the wait, else with the fields after it
+    const int jr = i - a.rec.i0;
+    const bool jrin = LN && n >= 1 && jr >= 0 && jr < a.rec.n;
+    float yvv = 0.0f, ypv = 0.0f;
+    auto line_values = [&]() {
+        if (jrin && a.yv) yvv = (float)__ldcg(a.yv + (size_t)(n - 1) * a.rec.n + jr);
+        if (jrin && a.yp) ypv = (float)__ldcg(a.yp + (size_t)(n - 1) * a.rec.n + jr);
+    };
+    if (LN && in.lines_ready) line_values();
     if (In::kAhead) in.wait();
+    if (LN && !in.lines_ready) line_values();
 #pragma unroll
     for (int j = 0; j < L; j++) {
         rvx[j] = in.own_vx(j);
@@ -1098,9 +1120,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         }
         if (LN && a.yv && n >= 1 && okz) {   // transposed v_z sampling of step n-1
             const float wy_ = row_weight(k, a.rec.kv, a.rec.wv0, a.rec.wv1);
-            const int jr = i - a.rec.i0;
-            if (wy_ != 0.0f && jr >= 0 && jr < a.rec.n)
-                out = fmaf(wy_, (float)a.yv[(size_t)(n - 1) * a.rec.n + jr], out);
+            if (wy_ != 0.0f && jrin) out = fmaf(wy_, yvv, out);
         }
         if (okz) st_out(io.vz_out + k * pitch + i, out);
         sm.svz[r + R][c] = okz ? vz : 0.0f;
@@ -1174,9 +1194,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
         }
         if (LN && a.yp && n >= 1 && okp) {   // transposed pressure sampling of step n-1
             const float w = row_weight(k, a.rec.kp, a.rec.wp0, a.rec.wp1);
-            const int jr = i - a.rec.i0;
-            if (w != 0.0f && jr >= 0 && jr < a.rec.n)
-                out = fmaf(w, (float)a.yp[(size_t)(n - 1) * a.rec.n + jr], out);
+            if (w != 0.0f && jrin) out = fmaf(w, ypv, out);
         }
         if (okp) st_out(io.p_out + k * pitch + i, out);
     }
@@ -1184,7 +1202,7 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
 
 template <int R, int TX, int TZ, int NT>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int i0, int k0,
-                                         TileSmem<R, TX, TZ> &sm) {
+                                         TileSmem<R, TX, TZ> &sm, bool lines_ready = false) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
@@ -1193,13 +1211,13 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
         // meets (the general one, which reduces to the same arithmetic where a
         // point is undamped and inside the grid)
         if (fwd_lines<R, TZ>(a, k0)) {
-            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
         } else if (in) {
-            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
-            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
@@ -1210,7 +1228,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
 
 template <int R, int TX, int TZ, int NT>
 __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int i0, int k0,
-                                         TileSmem<R, TX, TZ> &sm) {
+                                         TileSmem<R, TX, TZ> &sm, bool lines_ready = false) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
@@ -1219,13 +1237,13 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int
         // meets (the general one, which reduces to the same arithmetic where a
         // point is undamped and inside the grid)
         if (adj_lines<TZ>(a, k0, io.n)) {
-            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
         } else if (in) {
-            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
-            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm);
+            GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
             adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
@@ -1404,10 +1422,13 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(con
     io.n = J.adj ? J.nt - 1 - st : st;
     // the tile step reads the grid's constants, then waits for the previous
     // step (griddepcontrol.wait) before its field loads
+    // a sweep that starts with the phase injects gathers made before it:
+    // its line values are read before the wait too (the phase's first
+    // launch is not a dependent launch, so everything before it is complete)
     if (J.adj)
-        adj_tile<R, TX, TZ, NT>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>());
+        adj_tile<R, TX, TZ, NT>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
     else
-        fwd_tile<R, TX, TZ, NT>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>());
+        fwd_tile<R, TX, TZ, NT>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
 }
 
 // The same for a phase whose sweeps live in a device table (batches of many

@@ -92,6 +92,7 @@ struct TmaIn {
     // the stage is complete (every thread waited on its barrier): nothing to
     // read ahead, nothing to wait for
     static constexpr bool kAhead = true;
+    static constexpr bool lines_ready = false;   // the kernel waited before the copies
     template <bool PRE>
     __device__ __forceinline__ void prestage() {}
     __device__ __forceinline__ void wait() const {}
