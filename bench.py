@@ -272,6 +272,7 @@ def run_ours(args):
     st = ctx.stats()
     phases = [{"phase": r["phase"], "sweeps": r["sweeps"], "tiles": r["tiles"],
                "kernel": _kernel_name(r["tile_config"]), "tile_config": r["tile_config"],
+               "chain": r["chain"],
                "us_per_step": 1000.0 * r["ms"] / max(r["steps"], 1), "steps": r["steps"],
                "share": r["ms"] / max(st["sweep_ms"], 1e-9)}
               for r in ctx.phase_stats()]

@@ -342,11 +342,12 @@ int ssx_reset_stats(ssx_ctx *ctx);
  * row. Row k (from 0, in order of first appearance): the phase's name
  * (NUL-terminated, truncated to name_len - 1 characters), its sweeps, the
  * tiles of its largest launch, its tile configuration (0-7 plain kernel,
- * 8-15 TMA-staged, 16-19 marching), its event-timed device time and its
- * time steps (launches). SSX_ERR_ARG for k past the last row or a NULL
- * output. Synchronises. */
+ * 8-15 TMA-staged, 16-19 marching), its dependent-launch chain length (every
+ * chain-th launch an ordinary launch; 0: one chain a span), its event-timed
+ * device time and its time steps (launches). SSX_ERR_ARG for k past the
+ * last row or a NULL output. Synchronises. */
 int ssx_get_phase_stats(ssx_ctx *ctx, int k, char *name, int name_len, int *sweeps, int *tiles,
-                        int *tile_cfg, double *ms, long long *steps);
+                        int *tile_cfg, int *chain, double *ms, long long *steps);
 
 /* Capacity, in floats (16 MiB), of the fixed device scratch array used by
  * ssx_forward_noalloc. */

@@ -74,7 +74,7 @@ struct EvPair {
 // sweep count, tile count and kernel configuration.
 struct PhaseRow {
     std::string name;
-    int sweeps = 0, tiles = 0, cfg = -1;
+    int sweeps = 0, tiles = 0, cfg = -1, chain = 0;
     double ms = 0.0;
     long long steps = 0;
 };
@@ -129,6 +129,7 @@ struct ssx_ctx {
     // multi-sweep phases: tile configuration and device job table per phase
     struct PhaseInfo {
         int cfg = -1, T = 0;
+        int chain = 0;                // launches per dependent-launch chain (0: whole span)
         std::vector<PhaseSeg> segs;   // spans of launches with the same stepping sweeps
         void *tabmem = nullptr;       // their device tables (one allocation)
     };
@@ -861,9 +862,16 @@ int phase_len(const std::vector<Sweep> &sw) {
 
 // the launches of a phase: transposed sweeps get their initial state (the
 // transposed sampling of their last data sample) just before their first step
+// Launches t0 .. t1-1 of a phase. Consecutive launches are chained by
+// programmatic dependent launch, except every `chain`-th (chain > 0), which
+// is an ordinary launch: on a long chain the CTAs of the next launches become
+// resident early and spread unevenly over the SMs, and a launch with fewer
+// tiles than SMs then runs slower per step (measured; the phase tuner picks
+// the chain length).
 int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int t0, int t1,
-                     int cfg, cudaStream_t s, bool with_init, bool stall = false) {
+                     int cfg, cudaStream_t s, bool with_init, bool stall = false, int chain = 0) {
     for (int t = t0; t < t1; t++) {
+        const bool brk = chain > 0 && (t - t0) % chain == 0;
         if (with_init)
             for (const Sweep &w : sw)
                 if (w.adj && w.offset == t) {
@@ -880,16 +888,16 @@ int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &
         if (pa.mtab)
             CK(launch_march(pa.mtab, pa.njobs, pa.total, t, cfg - kCfgMarch0, pa.cap, c->d_err,
                             stall && t == 0 ? 200000000ull : 2000000000ull,
-                            stall && t == 0 ? 0 : -1, s, true));
+                            stall && t == 0 ? 0 : -1, s, !brk));
         else if (pa.ttab)
             CK(launch_multi_tma(pa.ttab, pa.njobs, pa.total, t, cfg - kNumTileCfgs, pa.cap, c->d_err,
                                 stall && t == 0 ? 200000000ull : 2000000000ull,
-                                stall && t == 0 ? 0 : -1, s, true));
+                                stall && t == 0 ? 0 : -1, s, !brk));
         else if (pa.dtab)
-            CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, true));
+            CK(launch_multi_tab(pa.dtab, pa.njobs, pa.total, t, c->R, cfg, s, !brk));
         else   // the span's first launch is not a dependent launch: its sweeps
                // may read their injected gathers before the grid dependency wait
-            CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, t != t0));
+            CK(launch_multi(pa.set, pa.total, t, c->R, cfg, s, t != t0 && !brk));
     }
     return SSX_OK;
 }
@@ -902,7 +910,10 @@ int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &
 // reuses the choice of one of similar size instead of timing every
 // configuration again. All configurations give identical results.
 std::mutex g_phase_mu;
-std::map<std::vector<long long>, int> g_phase_tuned;
+struct PhaseChoice {
+    int cfg, chain;
+};
+std::map<std::vector<long long>, PhaseChoice> g_phase_tuned;
 
 std::vector<long long> phase_signature(ssx_ctx *c, const std::vector<Sweep> &sw) {
     int dev = 0;
@@ -929,81 +940,125 @@ std::vector<long long> phase_signature(ssx_ctx *c, const std::vector<Sweep> &sw)
     return k;
 }
 
-// time each admissible tile configuration on a short source-free run of the phase
-int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *best_cfg) {
-    if (c->forced_cfg >= 0) {
+// Device time of T launches of a phase in configuration cfg (a graph of the
+// source-free launches, run three times, the best of the last two): 0 and
+// *ok = false if the configuration cannot be set up for these sweeps.
+int time_phase(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, int T, int chain, float *ms,
+               int *tiles, bool *ok) {
+    *ok = false;
+    *ms = 1e30f;
+    PhaseArgs pa;
+    void *tmem = nullptr;
+    if (phase_args(c, sw, cfg, true, &pa, &tmem) != SSX_OK) {   // a candidate that cannot be set up
+        if (tmem) cudaFree(tmem);
+        return SSX_OK;
+    }
+    *tiles = pa.total;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = SSX_OK;
+    cudaError_t ec = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
+    if (ec == cudaSuccess) {
+        rc = enqueue_launches(c, sw, pa, 0, T, cfg, c->s, false, false, chain);
+        ec = cudaStreamEndCapture(c->s, &graph);
+    }
+    if (rc == SSX_OK && ec == cudaSuccess) {
+        ec = cudaGraphInstantiate(&exec, graph, 0);
+        if (ec == cudaSuccess) ec = cudaEventCreate(&e0);
+        if (ec == cudaSuccess) ec = cudaEventCreate(&e1);
+        for (int rep = 0; rep < 3 && ec == cudaSuccess; rep++) {
+            ec = cudaEventRecord(e0, c->s);
+            if (ec == cudaSuccess) ec = cudaGraphLaunch(exec, c->s);
+            if (ec == cudaSuccess) ec = cudaEventRecord(e1, c->s);
+            if (ec == cudaSuccess) ec = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (ec == cudaSuccess) ec = cudaEventElapsedTime(&t, e0, e1);
+            if (ec == cudaSuccess && rep > 0) *ms = std::min(*ms, t);
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (tmem) cudaFree(tmem);
+    if (rc != SSX_OK) return rc;
+    CK(ec);
+    *ok = true;
+    return SSX_OK;
+}
+
+// Tile configuration of a phase: each admissible one timed on a short
+// source-free run (48 launches); then the length of its dependent-launch
+// chains, timed over up to 256 launches of the chosen configuration (a
+// break every 8, 16 or 32 launches, or none), kept only where it gains
+// more than 2 %.
+int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *best_cfg,
+               int *best_chain) {
+    *best_chain = 0;
+    const std::vector<long long> sig = phase_signature(c, sw);
+    const bool forced = c->forced_cfg >= 0;
+    if (forced) {
         const int f = c->forced_cfg;
         if (f >= kCfgMarch0) *best_cfg = march_usable(c, f - kCfgMarch0) ? f : 0;
         else *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
-        return SSX_OK;
-    }
-    const std::vector<long long> sig = phase_signature(c, sw);
-    {
+    } else {
         std::lock_guard<std::mutex> lock(g_phase_mu);
         auto it = g_phase_tuned.find(sig);
         if (it != g_phase_tuned.end()) {
-            *best_cfg = it->second;
+            *best_cfg = it->second.cfg;
+            *best_chain = it->second.chain;
             return SSX_OK;
         }
     }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    const int T = std::min(phase_len(sw), 48);
-    float best = 1e30f;
-    int rc = SSX_OK;
-    for (int k = 0; k < kNumAllCfgs && rc == SSX_OK; k++) {
-        if (k >= kCfgMarch0) {
-            if (!march_usable(c, k - kCfgMarch0)) continue;
-        } else if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) {
-            continue;
-        }
-        PhaseArgs pa;
-        void *tmem = nullptr;
-        if (phase_args(c, sw, k, true, &pa, &tmem) != SSX_OK) {   // a candidate that cannot be set up
-            if (tmem) cudaFree(tmem);
-            continue;
-        }
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_launches(c, sw, pa, 0, T, k, c->s, false);
-        cudaError_t ec = cudaStreamEndCapture(c->s, &graph);
-        if (rc != SSX_OK) {
-            if (tmem) cudaFree(tmem);
-            break;
-        }
-        CK(ec);
-        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        CK(ei);
-        float ms = 1e30f;
-        for (int rep = 0; rep < 3; rep++) {
-            CK(cudaEventRecord(e0, c->s));
-            CK(cudaGraphLaunch(exec, c->s));
-            CK(cudaEventRecord(e1, c->s));
-            CK(cudaEventSynchronize(e1));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) ms = std::min(ms, t);
-        }
-        cudaGraphExecDestroy(exec);
-        if (tmem) cudaFree(tmem);
-        if (c->log_tuning)
-            std::fprintf(stderr, "ssx tune: phase %s (%zu sweeps, %d tiles) config %d: %.3f us/step\n",
-                         name, sw.size(), pa.total, k, 1000.0 * ms / T);
-        if (ms < best) {
-            best = ms;
-            *best_cfg = k;
+    if (!forced) {
+        const int T = std::min(phase_len(sw), 48);
+        float best = 1e30f;
+        for (int k = 0; k < kNumAllCfgs; k++) {
+            if (k >= kCfgMarch0) {
+                if (!march_usable(c, k - kCfgMarch0)) continue;
+            } else if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) {
+                continue;
+            }
+            float ms = 0.f;
+            int tiles = 0;
+            bool ok = false;
+            TRY(time_phase(c, sw, k, T, 0, &ms, &tiles, &ok));
+            if (!ok) continue;
+            if (c->log_tuning)
+                std::fprintf(stderr, "ssx tune: phase %s (%zu sweeps, %d tiles) config %d: %.3f us/step\n",
+                             name, sw.size(), tiles, k, 1000.0 * ms / T);
+            if (ms < best) {
+                best = ms;
+                *best_cfg = k;
+            }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc == SSX_OK) {
+    const int T2 = std::min(phase_len(sw), 256);
+    if (T2 >= 128) {
+        const int chains[] = {0, 8, 16, 32};
+        float t0 = 0.f;
+        for (int chain : chains) {
+            float ms = 0.f;
+            int tiles = 0;
+            bool ok = false;
+            TRY(time_phase(c, sw, *best_cfg, T2, chain, &ms, &tiles, &ok));
+            if (!ok) break;
+            if (c->log_tuning)
+                std::fprintf(stderr, "ssx tune: phase %s config %d chain %d: %.3f us/step\n", name,
+                             *best_cfg, chain, 1000.0 * ms / T2);
+            if (chain == 0) t0 = ms;
+            else if (ms < 0.98f * t0 && (*best_chain == 0 || ms < t0)) {
+                t0 = ms;
+                *best_chain = chain;
+            }
+        }
+    }
+    if (!forced) {
         std::lock_guard<std::mutex> lock(g_phase_mu);
-        g_phase_tuned[sig] = *best_cfg;
+        g_phase_tuned[sig] = PhaseChoice{*best_cfg, *best_chain};
     }
-    return rc;
+    return SSX_OK;
 }
 
 int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
@@ -1023,7 +1078,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     auto it = c->phases.find(key);
     if (it == c->phases.end()) {
         ssx_ctx::PhaseInfo info;
-        TRY(tune_phase(c, name, sw, &info.cfg));
+        TRY(tune_phase(c, name, sw, &info.cfg, &info.chain));
         TRY(check_sweeps_quiet(c));
         // The phase's launches split where a sweep starts or ends: each span
         // launches only the sweeps that step in it (a batch whose shots have
@@ -1070,7 +1125,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
             CK(cudaMemsetAsync(w.G->mem + E, 0, 3 * E * sizeof(float), s));
         }
         for (const PhaseSeg &seg : info.segs)
-            TRY(enqueue_launches(c, sw, seg.pa, seg.t0, seg.t1, info.cfg, s, true, stall));
+            TRY(enqueue_launches(c, sw, seg.pa, seg.t0, seg.t1, info.cfg, s, true, stall, info.chain));
         return SSX_OK;
     };
     double pts = 0;
@@ -1084,7 +1139,8 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         int tiles = 0;
         for (const PhaseSeg &seg : info.segs) tiles = std::max(tiles, seg.pa.total);
         const std::string rk = std::string(name) + "|" + std::to_string(sw.size()) + "|" +
-                               std::to_string(tiles) + "|" + std::to_string(info.cfg);
+                               std::to_string(tiles) + "|" + std::to_string(info.cfg) + "|" +
+                               std::to_string(info.chain);
         auto r = c->phase_row_of.find(rk);
         if (r == c->phase_row_of.end()) {
             PhaseRow row;
@@ -1092,6 +1148,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
             row.sweeps = (int)sw.size();
             row.tiles = tiles;
             row.cfg = info.cfg;
+            row.chain = info.chain;
             c->phase_rows.push_back(row);
             r = c->phase_row_of.emplace(rk, (int)c->phase_rows.size() - 1).first;
         }
@@ -2278,8 +2335,9 @@ int ssx_reset_stats(ssx_ctx *c) {
 }
 
 int ssx_get_phase_stats(ssx_ctx *c, int k, char *name, int name_len, int *sweeps, int *tiles,
-                        int *tile_cfg, double *ms, long long *steps) {
-    if (!c || k < 0 || !name || name_len < 1 || !sweeps || !tiles || !tile_cfg || !ms || !steps)
+                        int *tile_cfg, int *chain, double *ms, long long *steps) {
+    if (!c || k < 0 || !name || name_len < 1 || !sweeps || !tiles || !tile_cfg || !chain || !ms ||
+        !steps)
         return SSX_ERR_ARG;
     TRY(resolve_events(c));
     if (k >= (int)c->phase_rows.size()) return SSX_ERR_ARG;
@@ -2288,6 +2346,7 @@ int ssx_get_phase_stats(ssx_ctx *c, int k, char *name, int name_len, int *sweeps
     *sweeps = r.sweeps;
     *tiles = r.tiles;
     *tile_cfg = r.cfg;
+    *chain = r.chain;
     *ms = r.ms;
     *steps = r.steps;
     return SSX_OK;

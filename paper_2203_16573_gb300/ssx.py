@@ -102,7 +102,8 @@ def load_library(path: str = LIB_PATH):
         "ssx_get_stats": ([vp, P(Stats)], i),
         "ssx_reset_stats": ([vp], i),
         "ssx_get_phase_stats": ([vp, i, ctypes.c_char_p, i, P(ctypes.c_int), P(ctypes.c_int),
-                                 P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_longlong)], i),
+                                 P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double),
+                                 P(ctypes.c_longlong)], i),
         "ssx_forward_noalloc": ([P(GridDesc), P(GeomDesc), vp, d, vp, vp, vp], i),
         "ssx_set_sweep_mode": ([vp, i], i),
         "ssx_set_tile_config": ([vp, i], i),
@@ -319,17 +320,18 @@ class Context:
         """Per-phase breakdown of the timed sweeps (ssx_get_phase_stats)."""
         rows = []
         name = ctypes.create_string_buffer(64)
-        sw, tl, cfg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        sw, tl, cfg, ch = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ms, steps = ctypes.c_double(), ctypes.c_longlong()
         while True:
             rc = self._lib.ssx_get_phase_stats(self._c, len(rows), name, 64, ctypes.byref(sw),
-                                               ctypes.byref(tl), ctypes.byref(cfg),
+                                               ctypes.byref(tl), ctypes.byref(cfg), ctypes.byref(ch),
                                                ctypes.byref(ms), ctypes.byref(steps))
             if rc == ERR_ARG:
                 return rows
             self._check(rc)
             rows.append({"phase": name.value.decode(), "sweeps": sw.value, "tiles": tl.value,
-                         "tile_config": cfg.value, "ms": ms.value, "steps": steps.value})
+                         "tile_config": cfg.value, "chain": ch.value, "ms": ms.value,
+                         "steps": steps.value})
 
 
 def solve_batch(ctxs, ds, alphas, maxit, rtol, mode=MODE_PCG, outs=None):

@@ -396,6 +396,7 @@ def test_phase_breakdown_accounts_for_the_timed_sweeps(ssx):
     for r in rows:
         assert r["ms"] > 0 and r["steps"] >= spec.nt and r["sweeps"] >= 1 and r["tiles"] >= 1
         assert 0 <= r["tile_config"] < 2 * ssx.N_TILE_CONFIGS + ssx.N_MARCH_CONFIGS
+        assert r["chain"] in (0, 8, 16, 32)
     assert sum(r["ms"] for r in rows) <= st["sweep_ms"] * (1 + 1e-6)
     assert sum(r["steps"] for r in rows) <= st["timed_steps"]
 
