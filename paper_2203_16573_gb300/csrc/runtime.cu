@@ -199,9 +199,9 @@ int fail(ssx_ctx *c, int code, const std::string &msg) {
     } while (0)
 
 
-// Phase-kernel configuration ids: 0 .. 7 the plain tile kernel (shape id),
-// 8 .. 15 the TMA-staged tile kernel of shape id - 8, 16 .. 19 the marching
-// kernel of shape id - 16.
+// Phase-kernel configuration ids: 0 .. kNumTileCfgs - 1 the plain tile kernel
+// (shape id), kNumTileCfgs .. 2 kNumTileCfgs - 1 the TMA-staged tile kernel of
+// shape id - kNumTileCfgs, then the marching kernel's shapes.
 constexpr int kCfgMarch0 = 2 * kNumTileCfgs;
 constexpr int kNumAllCfgs = kCfgMarch0 + kNumMarchCfgs;
 void tile_dims(int cfg, int *tx, int *tz) {
@@ -482,6 +482,8 @@ int select_config(ssx_ctx *c, DGrid &G, bool adj) {
     std::vector<Cand> cands;
     for (int k = 0; k < kNumTileCfgs; k++) {
         if (c->forced_cfg >= 0 && k != c->forced_cfg % kNumTileCfgs) continue;
+        // below order 8 a quad shape runs as its strip twin: not timed twice
+        if (c->forced_cfg < 0 && kTileCfgs[k].quads && c->R != kMaxR) continue;
         if (c->sweep_mode != SSX_SWEEP_PERSISTENT) cands.push_back({k, false});
         if (c->sweep_mode != SSX_SWEEP_STEP && tiles_of(G, k) <= capacity(c, k, adj))
             cands.push_back({k, true});
@@ -1019,6 +1021,8 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
                 if (!march_usable(c, k - kCfgMarch0)) continue;
             } else if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) {
                 continue;
+            } else if (kTileCfgs[k % kNumTileCfgs].quads && c->R != kMaxR) {
+                continue;   // below order 8 a quad shape runs as its strip twin
             }
             float ms = 0.f;
             int tiles = 0;

@@ -159,22 +159,31 @@ struct JobSet {
     int njobs;
 };
 
-// Tile configurations of the step kernels: (id, TX, TZ, threads per CTA).
+// Tile configurations of the step kernels: (id, TX, TZ, threads per CTA,
+// quads). With quads = 1 the CTA has one thread per 4-column quad of the tile
+// and its interior and sponge tiles step by 16-byte vectors (order 8; at
+// other orders the configuration runs as strips, like its quads = 0 twin).
 // Every configuration computes bit-identical results; the runtime picks one
 // per grid and direction by timing them (autotune). TX, TZ >= 2k keeps the
 // halo of a persistent sweep within the four edge neighbours.
 #define SSX_TILE_CONFIGS(X) \
-    X(0, 64, 16, 256)       \
-    X(1, 64, 16, 512)       \
-    X(2, 32, 32, 256)       \
-    X(3, 64, 32, 512)       \
-    X(4, 64, 32, 1024)      \
-    X(5, 128, 16, 512)      \
-    X(6, 128, 32, 1024)     \
-    X(7, 32, 16, 256)
-constexpr int kNumTileCfgs = 8;
+    X(0, 64, 16, 256, 0)    \
+    X(1, 64, 16, 512, 0)    \
+    X(2, 32, 32, 256, 0)    \
+    X(3, 64, 32, 512, 0)    \
+    X(4, 64, 32, 1024, 0)   \
+    X(5, 128, 16, 512, 0)   \
+    X(6, 128, 32, 1024, 0)  \
+    X(7, 32, 16, 256, 0)    \
+    X(8, 64, 16, 256, 1)    \
+    X(9, 32, 32, 256, 1)    \
+    X(10, 64, 32, 512, 1)   \
+    X(11, 128, 16, 512, 1)  \
+    X(12, 128, 32, 1024, 1)
+constexpr int kNumTileCfgs = 13;
 struct TileCfg {
     int tx, tz, threads;
+    int quads;   // 1: interior and sponge tiles step by quads (order 8)
 };
 extern const TileCfg kTileCfgs[kNumTileCfgs];
 // Marching-kernel shapes: (id, tile width = threads per CTA, tile height).

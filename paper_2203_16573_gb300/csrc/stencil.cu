@@ -139,7 +139,7 @@ double sponge_scale(double v_max, int nsp, double h, double dt) {
 }
 
 const TileCfg kTileCfgs[kNumTileCfgs] = {
-#define SSX_CFG_ROW(id, TX, TZ, NT) {TX, TZ, NT},
+#define SSX_CFG_ROW(id, TX, TZ, NT, V) {TX, TZ, NT, V},
     SSX_TILE_CONFIGS(SSX_CFG_ROW)
 #undef SSX_CFG_ROW
 };

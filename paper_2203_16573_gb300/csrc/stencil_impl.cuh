@@ -83,9 +83,10 @@ struct TileSmem {
     static constexpr int H = 2 * R;
     static constexpr int PW = TX + 2 * H, PH = TZ + 2 * H;
     static constexpr int VXW = TX + 2 * R - 1, VZH = TZ + 2 * R - 1;
+    static constexpr int VXP = TX + 2 * R;   // row pitch of svx: whole 16-byte quads for order 8
     float sp[PH][PW];      // p^n (forward) or q = C_p pbar (transpose), tile + 2k halo
-    float svx[TZ][VXW];    // v_x^{n+1/2} (forward) or C_vx vbar_x' (transpose)
-    float svz[VZH][TX];    // v_z^{n+1/2} (forward) or C_vz vbar_z' (transpose)
+    alignas(16) float svx[TZ][VXP];    // v_x^{n+1/2} (forward) or C_vx vbar_x' (transpose)
+    alignas(16) float svz[VZH][TX];    // v_z^{n+1/2} (forward) or C_vz vbar_z' (transpose)
 };
 
 // The field buffers and step index of one step (kept in registers).
@@ -770,6 +771,18 @@ struct GlobalIn {
     __device__ __forceinline__ float hvz(int kk, int i) const {
         return ldf(io.vz_in + (k0 - R + kk) * pitch + i);
     }
+    // by quads (fwd_quad / adj_quad): v_x at tile row r from v_x column jj,
+    // v_z at v_z row kk, kappa and p at tile row r, from tile column c4
+    __device__ __forceinline__ float4 vx4(int r, int jj) const {
+        return ldf4(io.vx_in + (k0 + r) * pitch + (i0 - R + jj));
+    }
+    __device__ __forceinline__ float4 vz4(int kk, int c4) const {
+        return ldf4(io.vz_in + (k0 - R + kk) * pitch + i0 + c4);
+    }
+    __device__ __forceinline__ float4 kap4(int r, int c4) const {
+        return __ldg(reinterpret_cast<const float4 *>(g.kap + (k0 + r) * pitch + i0 + c4));
+    }
+    __device__ __forceinline__ float4 p4(int r, int c4) const { return ldf4(io.p_in + (k0 + r) * pitch + i0 + c4); }
     // the transposed step's C_p factors of the staged region, read before the
     // grid dependency wait (set-up data, unchanged by the previous step) where
     // the register budget allows it (CTAs of up to 256 threads); larger CTAs
@@ -1200,12 +1213,478 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiles by quads (order 8). Thread t owns the four consecutive columns
+// i0 + c4 .. i0 + c4 + 3, c4 = 4 (t mod TX/4), of tile row t / (TX/4): the
+// CTA has one thread per quad of the tile. Every operand moves as a 16-byte
+// vector: the thread's own v, kappa and p, the x differences (the eleven
+// values an 8-point difference of four consecutive points needs sit in three
+// aligned quads of a staged row) and the z differences (eight quads down the
+// column). The halo values of v (2k-1 rows of v_z, a quad of v_x on each side
+// of every tile row) are shared out over all threads as quads. Per point the
+// arithmetic is the strips' (fwd_strip / adj_strip), term for term and in the
+// same order, so every tile configuration still gives the same bits. Tiles
+// that a line meets keep the strip step (its injection and sampling).
+// ---------------------------------------------------------------------------
 template <int R, int TX, int TZ, int NT>
+struct QuadShape {
+    static constexpr int QW = TX / 4;                      // quads per tile row
+    static constexpr bool ok = R == 4 && TX % 4 == 0 && NT * 4 == TX * TZ;
+    static constexpr int NHZ = (2 * R - 1) * QW;           // v_z halo quads
+    static constexpr int NHX = 2 * TZ;                     // v_x halo quads
+    static constexpr int NH = (NHZ + NHX + NT - 1) / NT;   // halo quads per thread
+};
+
+struct Q4 {
+    float e[4];
+};
+__device__ __forceinline__ Q4 q4(const float4 v) { return {{v.x, v.y, v.z, v.w}}; }
+__device__ __forceinline__ float4 f4(const Q4 &q) { return make_float4(q.e[0], q.e[1], q.e[2], q.e[3]); }
+__device__ __forceinline__ Q4 lds4(const float *p) { return q4(*reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void sts4(float *p, const Q4 &v) { *reinterpret_cast<float4 *>(p) = f4(v); }
+__device__ __forceinline__ void st_out4(float *p, const Q4 &v) {
+    asm volatile("st.global.cg.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.e[0]), "f"(v.e[1]),
+                 "f"(v.e[2]), "f"(v.e[3])
+                 : "memory");
+}
+// a quad of a field into the storage: one vector store where all four points
+// are inside the grid, else the points that are (masked points are never written)
+__device__ __forceinline__ void st_quad(float *p, const Q4 &v, const bool (&ok)[4], bool all) {
+    if (all) {
+        st_out4(p, v);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            if (ok[e]) st_out(p + e, v.e[e]);
+    }
+}
+
+// the x difference D+ of the four points whose twelve-value window starts at
+// x: u[x + e + k + m] - u[x + e + k + 1 - m] (the v_x points of a p row, or
+// the p points of a v_x row), accumulated as the strips do
+template <int R>
+__device__ __forceinline__ Q4 xdiff(const float *x, const float (&cc)[R]) {
+    float u[12];
+    const Q4 a = lds4(x), b = lds4(x + 4), c = lds4(x + 8);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        u[e] = a.e[e];
+        u[4 + e] = b.e[e];
+        u[8 + e] = c.e[e];
+    }
+    Q4 d;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        float s = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) s = fmaf(cc[m - 1], u[e + R + m] - u[e + R + 1 - m], s);
+        d.e[e] = s;
+    }
+    return d;
+}
+// the z difference of a quad from the 2k quads of a column window w[0 .. 2k-1]:
+// w[k - 1 + m] - w[k - m]
+template <int R>
+__device__ __forceinline__ Q4 zdiff(const Q4 (&w)[2 * R], const float (&cc)[R]) {
+    Q4 d;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        float s = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= R; m++) s = fmaf(cc[m - 1], w[R - 1 + m].e[e] - w[R - m].e[e], s);
+        d.e[e] = s;
+    }
+    return d;
+}
+// the 2k quads of a column window: rows row0, row0 + 1, ... of a staged field
+template <int R, int PW>
+__device__ __forceinline__ void window(Q4 (&w)[2 * R], const float (*rows)[PW], int row0, int col) {
+#pragma unroll
+    for (int q = 0; q < 2 * R; q++) w[q] = lds4(&rows[row0 + q][col]);
+}
+
+// a thread's quad and its halo items: kind 1 = v_z quad at v_z row a,
+// column b; kind 2 = v_x quad at tile row a, v_x column b (x = i0 - k + b);
+// kind 0 = none
+template <int R, int TX, int TZ, int NT>
+struct QuadThread {
+    using Q = QuadShape<R, TX, TZ, NT>;
+    int c4, r;
+    int kind[Q::NH], ha[Q::NH], hb[Q::NH];
+    __device__ __forceinline__ QuadThread() {
+        const int t = threadIdx.x;
+        c4 = 4 * (t % Q::QW);
+        r = t / Q::QW;
+#pragma unroll
+        for (int q = 0; q < Q::NH; q++) {
+            const int e = t + q * NT;
+            if (e < Q::NHZ) {
+                const int hz = e / Q::QW;
+                kind[q] = 1;
+                ha[q] = hz < R ? hz : hz + TZ;
+                hb[q] = 4 * (e % Q::QW);
+            } else if (e < Q::NHZ + Q::NHX) {
+                const int e2 = e - Q::NHZ;
+                kind[q] = 2;
+                ha[q] = e2 >> 1;
+                hb[q] = (e2 & 1) ? TX + R : 0;
+            } else {
+                kind[q] = 0;
+                ha[q] = hb[q] = 0;
+            }
+        }
+    }
+};
+
+// One forward step of a tile by quads (interior or sponge tile; no line).
+template <int R, int TX, int TZ, int NT, bool SP, class In, class Work>
+__device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int i0, int k0,
+                                         In &in, Work &sm) {
+    using Q = QuadShape<R, TX, TZ, NT>;
+    constexpr int H = 2 * R;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
+    const QuadThread<R, TX, TZ, NT> th;
+    const int c4 = th.c4, r = th.r, i = i0 + c4, k = k0 + r;
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+
+    // the grid's constants before the wait for the previous step, the fields after it
+    float sxi[4], sxh[4], szi = 0.0f, szh = 0.0f;
+    if (!In::kAhead) in.wait();
+    if (SP) {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            sxi[e] = __ldg(g.sxi + min(i + e, NX - 1));   // clamped: masked points take any value
+            sxh[e] = __ldg(g.sxh + min(i + e, NX - 1));
+        }
+        szi = __ldg(g.szi + min(k, NZ - 1));
+        szh = __ldg(g.szh + min(k, NZ - 1));
+    }
+    const Q4 rk = q4(in.kap4(r, c4));
+    if (In::kAhead) in.wait();
+    const Q4 rvx = q4(in.vx4(r, c4 + R)), rvz = q4(in.vz4(r + R, c4));
+    Q4 rh[Q::NH];
+#pragma unroll
+    for (int q = 0; q < Q::NH; q++)
+        rh[q] = q4(th.kind[q] == 1 ? in.vz4(th.ha[q], th.hb[q])
+                                   : th.kind[q] == 2 ? in.vx4(th.ha[q], th.hb[q]) : make_float4(0.f, 0.f, 0.f, 0.f));
+    in.template stage<false>();
+    if (!In::kStaged) __syncthreads();   // p staged by all threads
+    float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
+
+    // own quad: v_z from the column window, v_x from the row
+    Q4 pw[2 * R];
+    window<R, TX + 4 * R>(pw, spa, r + H - R + 1, c4 + H);
+    const Q4 pold = pw[R - 1];
+    {
+        const Q4 d = zdiff<R>(pw, cc);
+        Q4 vz;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            ok[e] = !SP || (i + e < NX && k < NZ - 1);
+            all = all && ok[e];
+            if (SP) {
+                float A, B;
+                damp(sxi[e] + szh, A, B);
+                const float cvz = B * cv;
+                vz.e[e] = fmaf(-cvz, d.e[e], A * rvz.e[e]);
+                vz.e[e] = ok[e] ? vz.e[e] : 0.0f;
+            } else {
+                vz.e[e] = fmaf(-cv, d.e[e], rvz.e[e]);
+            }
+        }
+        st_quad(io.vz_out + k * pitch + i, vz, ok, all);
+        sts4(&sm.svz[r + R][c4], vz);
+    }
+    {
+        const Q4 d = xdiff<R>(&spa[r + H][c4 + R], cc);
+        Q4 vx;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            ok[e] = !SP || (i + e < NX - 1 && k < NZ);
+            all = all && ok[e];
+            if (SP) {
+                float A, B;
+                damp(sxh[e] + szi, A, B);
+                vx.e[e] = fmaf(-(B * cv), d.e[e], A * rvx.e[e]);
+                vx.e[e] = ok[e] ? vx.e[e] : 0.0f;
+            } else {
+                vx.e[e] = fmaf(-cv, d.e[e], rvx.e[e]);
+            }
+        }
+        st_quad(io.vx_out + k * pitch + i, vx, ok, all);
+        sts4(&sm.svx[r][c4 + R], vx);
+    }
+    // halo v (not written out)
+#pragma unroll
+    for (int q = 0; q < Q::NH; q++) {
+        const int ha = th.ha[q], hb = th.hb[q];
+        if (th.kind[q] == 1) {
+            const int kh = k0 - R + ha;
+            Q4 w[2 * R];
+            window<R, TX + 4 * R>(w, spa, ha + 1, hb + H);
+            const Q4 d = zdiff<R>(w, cc);
+            Q4 val;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                if (SP) {
+                    const int ih = i0 + hb + e;
+                    const bool ok = ih < NX && kh >= 0 && kh < NZ - 1;
+                    float A, B;
+                    damp(__ldg(g.sxi + min(ih, NX - 1)) + __ldg(g.szh + (ok ? kh : 0)), A, B);
+                    const float cvz = B * cv;
+                    const float v = fmaf(-cvz, d.e[e], A * rh[q].e[e]);
+                    val.e[e] = ok ? v : 0.0f;
+                } else {
+                    val.e[e] = fmaf(-cv, d.e[e], rh[q].e[e]);
+                }
+            }
+            sts4(&sm.svz[ha][hb], val);
+        } else if (th.kind[q] == 2) {
+            const int kh = k0 + ha;
+            const Q4 d = xdiff<R>(&spa[ha + H][hb], cc);
+            Q4 val;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                if (SP) {
+                    const int j = i0 - R + hb + e;
+                    const bool ok = kh < NZ && j >= 0 && j < NX - 1;
+                    float A, B;
+                    damp(__ldg(g.sxh + (ok ? j : 0)) + __ldg(g.szi + (ok ? kh : 0)), A, B);
+                    val.e[e] = ok ? fmaf(-(B * cv), d.e[e], A * rh[q].e[e]) : 0.0f;
+                } else {
+                    val.e[e] = fmaf(-cv, d.e[e], rh[q].e[e]);
+                }
+            }
+            sts4(&sm.svx[ha][hb], val);
+        }
+    }
+    __syncthreads();
+
+    // own quad: p^{n+1}
+    {
+        float u[12];
+        {
+            const Q4 a0 = lds4(&sm.svx[r][c4]), a1 = lds4(&sm.svx[r][c4 + 4]), a2 = lds4(&sm.svx[r][c4 + 8]);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                u[e] = a0.e[e];
+                u[4 + e] = a1.e[e];
+                u[8 + e] = a2.e[e];
+            }
+        }
+        Q4 zw[2 * R];
+        window<R, TX>(zw, sm.svz, r, c4);
+        Q4 val;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            float d = 0.0f;
+#pragma unroll
+            for (int m = 1; m <= R; m++) {
+                d = fmaf(cc[m - 1], u[e + R + m - 1] - u[e + R - m], d);
+                d = fmaf(cc[m - 1], zw[R + m - 1].e[e] - zw[R - m].e[e], d);
+            }
+            ok[e] = !SP || (i + e < NX && k < NZ);
+            all = all && ok[e];
+            float cp = rk.e[e];
+            if (SP) {
+                float A, B;
+                damp(sxi[e] + szi, A, B);
+                cp *= B;
+                val.e[e] = fmaf(-cp, d, A * pold.e[e]);
+            } else {
+                val.e[e] = fmaf(-cp, d, pold.e[e]);
+            }
+        }
+        st_quad(io.p_out + k * pitch + i, val, ok, all);
+    }
+}
+
+// One transposed step of a tile by quads (interior or sponge tile; no line).
+template <int R, int TX, int TZ, int NT, bool SP, class In, class Work>
+__device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int i0, int k0,
+                                         In &in, Work &sm) {
+    using Q = QuadShape<R, TX, TZ, NT>;
+    constexpr int H = 2 * R;
+    const GridArgs &g = a.g;
+    const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
+    const QuadThread<R, TX, TZ, NT> th;
+    const int c4 = th.c4, r = th.r, i = i0 + c4, k = k0 + r;
+    float cc[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) cc[m] = g.c[m];
+    const float cv = g.cv;
+
+    float sxi[4], sxh[4], szi = 0.0f, szh = 0.0f;
+    if (!In::kAhead) in.wait();
+    if (SP) {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            sxi[e] = __ldg(g.sxi + min(i + e, NX - 1));
+            sxh[e] = __ldg(g.sxh + min(i + e, NX - 1));
+        }
+        szi = __ldg(g.szi + min(k, NZ - 1));
+        szh = __ldg(g.szh + min(k, NZ - 1));
+    }
+    in.template prestage<true>();   // C_p of the staged region (constants)
+    if (In::kAhead) in.wait();
+    const Q4 rvx = q4(in.vx4(r, c4 + R)), rvz = q4(in.vz4(r + R, c4)), rp = q4(in.p4(r, c4));
+    Q4 rh[Q::NH];
+#pragma unroll
+    for (int q = 0; q < Q::NH; q++)
+        rh[q] = q4(th.kind[q] == 1 ? in.vz4(th.ha[q], th.hb[q])
+                                   : th.kind[q] == 2 ? in.vx4(th.ha[q], th.hb[q]) : make_float4(0.f, 0.f, 0.f, 0.f));
+    // q = C_p pbar over tile + 2k halo
+    in.template stage<true>();
+    __syncthreads();
+    float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
+
+    {   // vbar_x' = vbar_x + D+ q; C_vx vbar_x' kept for the p update
+        const Q4 d = xdiff<R>(&spa[r + H][c4 + R], cc);
+        Q4 vx, ox;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            ok[e] = !SP || (i + e < NX - 1 && k < NZ);
+            all = all && ok[e];
+            const float vbx = rvx.e[e] + d.e[e];
+            if (SP) {
+                float A, B;
+                damp(sxh[e] + szi, A, B);
+                vx.e[e] = ok[e] ? (B * cv) * vbx : 0.0f;
+                ox.e[e] = A * vbx;
+            } else {
+                vx.e[e] = cv * vbx;
+                ox.e[e] = vbx;
+            }
+        }
+        st_quad(io.vx_out + k * pitch + i, ox, ok, all);
+        sts4(&sm.svx[r][c4 + R], vx);
+    }
+    {   // vbar_z' likewise, from the window down the column
+        Q4 w[2 * R];
+        window<R, TX + 4 * R>(w, spa, r + H - R + 1, c4 + H);
+        const Q4 d = zdiff<R>(w, cc);
+        Q4 vz, out;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            ok[e] = !SP || (i + e < NX && k < NZ - 1);
+            all = all && ok[e];
+            const float vb = rvz.e[e] + d.e[e];
+            float A = 1.0f, B = 1.0f;
+            if (SP) damp(sxi[e] + szh, A, B);
+            const float v = (B * cv) * vb;
+            out.e[e] = SP ? A * vb : vb;
+            vz.e[e] = ok[e] ? v : 0.0f;
+        }
+        st_quad(io.vz_out + k * pitch + i, out, ok, all);
+        sts4(&sm.svz[r + R][c4], vz);
+    }
+    // halo vbar' (not written out)
+#pragma unroll
+    for (int q = 0; q < Q::NH; q++) {
+        const int ha = th.ha[q], hb = th.hb[q];
+        if (th.kind[q] == 1) {
+            const int kh = k0 - R + ha;
+            Q4 w[2 * R];
+            window<R, TX + 4 * R>(w, spa, ha + 1, hb + H);
+            const Q4 d = zdiff<R>(w, cc);
+            Q4 val;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const float vb = rh[q].e[e] + d.e[e];
+                if (SP) {
+                    const int ih = i0 + hb + e;
+                    const bool ok = ih < NX && kh >= 0 && kh < NZ - 1;
+                    float A, B;
+                    damp(__ldg(g.sxi + min(ih, NX - 1)) + __ldg(g.szh + (ok ? kh : 0)), A, B);
+                    val.e[e] = ok ? (B * cv) * vb : 0.0f;
+                } else {
+                    val.e[e] = (1.0f * cv) * vb;
+                }
+            }
+            sts4(&sm.svz[ha][hb], val);
+        } else if (th.kind[q] == 2) {
+            const int kh = k0 + ha;
+            const Q4 d = xdiff<R>(&spa[ha + H][hb], cc);
+            Q4 val;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const float vb = rh[q].e[e] + d.e[e];
+                if (SP) {
+                    const int j = i0 - R + hb + e;
+                    const bool ok = kh < NZ && j >= 0 && j < NX - 1;
+                    float A, B;
+                    damp(__ldg(g.sxh + (ok ? j : 0)) + __ldg(g.szi + (ok ? kh : 0)), A, B);
+                    val.e[e] = ok ? (B * cv) * vb : 0.0f;
+                } else {
+                    val.e[e] = cv * vb;
+                }
+            }
+            sts4(&sm.svx[ha][hb], val);
+        }
+    }
+    __syncthreads();
+
+    {   // pbar <- A_p pbar + D- (C_v vbar')
+        float u[12];
+        {
+            const Q4 a0 = lds4(&sm.svx[r][c4]), a1 = lds4(&sm.svx[r][c4 + 4]), a2 = lds4(&sm.svx[r][c4 + 8]);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                u[e] = a0.e[e];
+                u[4 + e] = a1.e[e];
+                u[8 + e] = a2.e[e];
+            }
+        }
+        Q4 zw[2 * R];
+        window<R, TX>(zw, sm.svz, r, c4);
+        Q4 out;
+        bool ok[4];
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            float d = 0.0f;
+#pragma unroll
+            for (int m = 1; m <= R; m++) {
+                d = fmaf(cc[m - 1], u[e + R + m - 1] - u[e + R - m], d);
+                d = fmaf(cc[m - 1], zw[R + m - 1].e[e] - zw[R - m].e[e], d);
+            }
+            ok[e] = !SP || (i + e < NX && k < NZ);
+            all = all && ok[e];
+            if (SP) {
+                float A, B;
+                damp(sxi[e] + szi, A, B);
+                out.e[e] = fmaf(A, rp.e[e], d);
+            } else {
+                out.e[e] = rp.e[e] + d;
+            }
+        }
+        st_quad(io.p_out + k * pitch + i, out, ok, all);
+    }
+}
+
+// V = 1: interior and sponge tiles step by quads where the shape allows it
+// (QuadShape::ok), tiles that a line meets by strips; V = 0: all by strips.
+template <int R, int TX, int TZ, int NT, int V = 0>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int i0, int k0,
                                          TileSmem<R, TX, TZ> &sm, bool lines_ready = false) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
+        constexpr bool kQuads = V == 1 && QuadShape<R, TX, TZ, NT>::ok;
         const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
         // three variants: interior tiles, sponge / edge tiles, and tiles a line
         // meets (the general one, which reduces to the same arithmetic where a
@@ -1215,10 +1694,12 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
             fwd_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
         } else if (in) {
             GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
-            fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
+            if constexpr (kQuads) fwd_quad<R, TX, TZ, NT, false>(a, io, i0, k0, gi, sm);
+            else fwd_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
             GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
-            fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
+            if constexpr (kQuads) fwd_quad<R, TX, TZ, NT, true>(a, io, i0, k0, gi, sm);
+            else fwd_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) fwd_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
@@ -1226,12 +1707,13 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, const StepIO &io, int
     }
 }
 
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V = 0>
 __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int i0, int k0,
                                          TileSmem<R, TX, TZ> &sm, bool lines_ready = false) {
     const bool in = interior_tile<R, TX, TZ>(a.g, i0, k0);
     if constexpr (StripShape<R, TX, TZ, NT>::ok) {
         using Q = StripShape<R, TX, TZ, NT>;
+        constexpr bool kQuads = V == 1 && QuadShape<R, TX, TZ, NT>::ok;
         const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
         // three variants: interior tiles, sponge / edge tiles, and tiles a line
         // meets (the general one, which reduces to the same arithmetic where a
@@ -1241,10 +1723,12 @@ __device__ __forceinline__ void adj_tile(const AdjArgs &a, const StepIO &io, int
             adj_strip<R, TX, TZ, NT, true, true>(a, io, i0, k0, gi, sm);
         } else if (in) {
             GlobalIn<R, TX, TZ, NT, false> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
-            adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
+            if constexpr (kQuads) adj_quad<R, TX, TZ, NT, false>(a, io, i0, k0, gi, sm);
+            else adj_strip<R, TX, TZ, NT, false, false>(a, io, i0, k0, gi, sm);
         } else {
             GlobalIn<R, TX, TZ, NT, true> gi(a.g, io, i0, k0, rs, c, sm, lines_ready);
-            adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
+            if constexpr (kQuads) adj_quad<R, TX, TZ, NT, true>(a, io, i0, k0, gi, sm);
+            else adj_strip<R, TX, TZ, NT, true, false>(a, io, i0, k0, gi, sm);
         }
     } else {
         if (in) adj_tile_impl<R, TX, TZ, NT, false>(a, io, i0, k0, sm);
@@ -1268,18 +1752,18 @@ __device__ __forceinline__ TileSmem<R, TX, TZ> &tile_smem() {
     return *reinterpret_cast<TileSmem<R, TX, TZ> *>(ssx_smem);
 }
 
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_fwd(const FwdArgs a) {
     griddep_launch();   // the tile step waits for the previous step itself
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
-    fwd_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
+    fwd_tile<R, TX, TZ, NT, V>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
 }
 
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_adj(const AdjArgs a) {
     griddep_launch();
     const StepIO io{a.p_in, a.vx_in, a.vz_in, a.p_out, a.vx_out, a.vz_out, a.n};
-    adj_tile<R, TX, TZ, NT>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
+    adj_tile<R, TX, TZ, NT, V>(a, io, blockIdx.x * TX, blockIdx.y * TZ, tile_smem<R, TX, TZ>());
 }
 
 // ---------------------------------------------------------------------------
@@ -1361,7 +1845,7 @@ __device__ __forceinline__ StepIO ping_pong(const PersistArgs &pa, int t, int n)
     return io;
 }
 
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT) k_fwd_persist(const FwdArgs a, const PersistArgs pa) {
     TileSmem<R, TX, TZ> &sm = tile_smem<R, TX, TZ>();
     __shared__ int s_abort;
@@ -1371,12 +1855,12 @@ __global__ void __launch_bounds__(NT) k_fwd_persist(const FwdArgs a, const Persi
     const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
     for (int n = 0; n < pa.nt; n++) {
         if (n > 0 && !wait_neighbours(pa, tile, (unsigned)n, &s_abort)) return;
-        fwd_tile<R, TX, TZ, NT>(a, ping_pong(pa, n, n), i0, k0, sm);
+        fwd_tile<R, TX, TZ, NT, V>(a, ping_pong(pa, n, n), i0, k0, sm);
         publish(pa, tile, (unsigned)(n + 1));
     }
 }
 
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const PersistArgs pa) {
     TileSmem<R, TX, TZ> &sm = tile_smem<R, TX, TZ>();
     __shared__ int s_abort;
@@ -1386,7 +1870,7 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
     const int i0 = (tile % pa.tiles_x) * TX, k0 = (tile / pa.tiles_x) * TZ;
     for (int t = 0; t < pa.nt; t++) {
         if (t > 0 && !wait_neighbours(pa, tile, (unsigned)t, &s_abort)) return;
-        adj_tile<R, TX, TZ, NT>(a, ping_pong(pa, t, pa.nt - 1 - t), i0, k0, sm);
+        adj_tile<R, TX, TZ, NT, V>(a, ping_pong(pa, t, pa.nt - 1 - t), i0, k0, sm);
         publish(pa, tile, (unsigned)(t + 1));
     }
 }
@@ -1397,7 +1881,7 @@ __global__ void __launch_bounds__(NT) k_adj_persist(const AdjArgs a, const Persi
 // ONE: the phase has a single sweep, so its arguments sit at fixed offsets of
 // the parameter bank and the step reads them as constant operands instead of
 // loading them through a runtime sweep index.
-template <int R, int TX, int TZ, int NT, bool ONE>
+template <int R, int TX, int TZ, int NT, int V, bool ONE>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(const JobSet P, int t) {
     griddep_launch();
     int j = 0;
@@ -1426,15 +1910,15 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi(con
     // its line values are read before the wait too (the phase's first
     // launch is not a dependent launch, so everything before it is complete)
     if (J.adj)
-        adj_tile<R, TX, TZ, NT>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
+        adj_tile<R, TX, TZ, NT, V>(J.aa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
     else
-        fwd_tile<R, TX, TZ, NT>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
+        fwd_tile<R, TX, TZ, NT, V>(J.fa, io, i0, k0, tile_smem<R, TX, TZ>(), J.offset == 0);
 }
 
 // The same for a phase whose sweeps live in a device table (batches of many
 // shots, each launch streams far more data than the look-up costs): binary
 // search of the CTA's sweep, its arguments copied to shared memory.
-template <int R, int TX, int TZ, int NT>
+template <int R, int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi_tab(const Job *__restrict__ jobs, int njobs, int t) {
     griddep_launch();
     __shared__ Job sj;
@@ -1471,9 +1955,9 @@ __global__ void __launch_bounds__(NT, (tile_min_ctas<TX, TZ, NT>())) k_multi_tab
     // latency: wait here (the tile step's own wait is then a no-op)
     griddep_wait();
     if (sj.adj)
-        adj_tile<R, TX, TZ, NT>(sj.aa, io, i0, k0, tile_smem<R, TX, TZ>());
+        adj_tile<R, TX, TZ, NT, V>(sj.aa, io, i0, k0, tile_smem<R, TX, TZ>());
     else
-        fwd_tile<R, TX, TZ, NT>(sj.fa, io, i0, k0, tile_smem<R, TX, TZ>());
+        fwd_tile<R, TX, TZ, NT, V>(sj.fa, io, i0, k0, tile_smem<R, TX, TZ>());
 }
 
 // ----------------------------------------------------------- launchers --
@@ -1498,17 +1982,17 @@ struct Stencil {
         return cudaLaunchKernelEx(&cfg, kern, a);
     }
 
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t fwd_step(const FwdArgs &a, cudaStream_t s, bool pdl) {
         dim3 grid((a.g.NX + TX - 1) / TX, (a.g.NZ + TZ - 1) / TZ);
-        return launch<FwdArgs>(k_fwd<R, TX, TZ, NT>, grid, NT, smem<TX, TZ>(), s, pdl, a);
+        return launch<FwdArgs>(k_fwd<R, TX, TZ, NT, V>, grid, NT, smem<TX, TZ>(), s, pdl, a);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t adj_step(const AdjArgs &a, cudaStream_t s, bool pdl) {
         dim3 grid((a.g.NX + TX - 1) / TX, (a.g.NZ + TZ - 1) / TZ);
-        return launch<AdjArgs>(k_adj<R, TX, TZ, NT>, grid, NT, smem<TX, TZ>(), s, pdl, a);
+        return launch<AdjArgs>(k_adj<R, TX, TZ, NT, V>, grid, NT, smem<TX, TZ>(), s, pdl, a);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t multi(const JobSet &jobs, int total, int t, cudaStream_t s, bool pdl) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(total);
@@ -1520,10 +2004,10 @@ struct Stencil {
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = pdl ? at : nullptr;
         cfg.numAttrs = pdl ? 1 : 0;
-        if (jobs.njobs == 1) return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, true>, jobs, t);
-        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, false>, jobs, t);
+        if (jobs.njobs == 1) return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, V, true>, jobs, t);
+        return cudaLaunchKernelEx(&cfg, k_multi<R, TX, TZ, NT, V, false>, jobs, t);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t multi_tab(const Job *jobs, int njobs, int total, int t, cudaStream_t s,
                                  bool pdl) {
         cudaLaunchConfig_t cfg = {};
@@ -1536,45 +2020,45 @@ struct Stencil {
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = pdl ? at : nullptr;
         cfg.numAttrs = pdl ? 1 : 0;
-        return cudaLaunchKernelEx(&cfg, k_multi_tab<R, TX, TZ, NT>, jobs, njobs, t);
+        return cudaLaunchKernelEx(&cfg, k_multi_tab<R, TX, TZ, NT, V>, jobs, njobs, t);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t fwd_persist(const FwdArgs &a, const PersistArgs &pa, cudaStream_t s) {
         FwdArgs aa = a;
         PersistArgs pp = pa;
         void *args[] = {&aa, &pp};
-        return cudaLaunchCooperativeKernel((void *)k_fwd_persist<R, TX, TZ, NT>,
+        return cudaLaunchCooperativeKernel((void *)k_fwd_persist<R, TX, TZ, NT, V>,
                                            dim3(pa.tiles_x * pa.tiles_z), dim3(NT), args,
                                            smem<TX, TZ>(), s);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t adj_persist(const AdjArgs &a, const PersistArgs &pa, cudaStream_t s) {
         AdjArgs aa = a;
         PersistArgs pp = pa;
         void *args[] = {&aa, &pp};
-        return cudaLaunchCooperativeKernel((void *)k_adj_persist<R, TX, TZ, NT>,
+        return cudaLaunchCooperativeKernel((void *)k_adj_persist<R, TX, TZ, NT, V>,
                                            dim3(pa.tiles_x * pa.tiles_z), dim3(NT), args,
                                            smem<TX, TZ>(), s);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static cudaError_t prepare() {
         const int sm = (int)smem<TX, TZ>();
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_fwd<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_adj<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_fwd_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_multi_tab<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_adj_persist<R, TX, TZ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if ((e = cudaFuncSetAttribute(k_fwd<R, TX, TZ, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_adj<R, TX, TZ, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_fwd_persist<R, TX, TZ, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi<R, TX, TZ, NT, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_multi_tab<R, TX, TZ, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_adj_persist<R, TX, TZ, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     }
-    template <int TX, int TZ, int NT>
+    template <int TX, int TZ, int NT, int V>
     static int capacity(bool adj) {
         int dev = 0, sms = 0, per_sm = 0, coop = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 0;
         if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        const void *fn = adj ? (const void *)k_adj_persist<R, TX, TZ, NT> : (const void *)k_fwd_persist<R, TX, TZ, NT>;
+        const void *fn = adj ? (const void *)k_adj_persist<R, TX, TZ, NT, V> : (const void *)k_fwd_persist<R, TX, TZ, NT, V>;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem<TX, TZ>()) != cudaSuccess) return 0;
         return per_sm * sms;
     }
@@ -1636,13 +2120,16 @@ struct Stencil {
         return e;                                                                                  \
     }
 
-#define SSX_CASE_FWD_STEP(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_step<TX, TZ, NT>(a, s, pdl);
-#define SSX_CASE_ADJ_STEP(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_step<TX, TZ, NT>(a, s, pdl);
-#define SSX_CASE_FWD_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::fwd_persist<TX, TZ, NT>(a, pa, s);
-#define SSX_CASE_ADJ_PERSIST(id, TX, TZ, NT) case id: return Stencil<SSX_R>::adj_persist<TX, TZ, NT>(a, pa, s);
-#define SSX_CASE_MULTI(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi<TX, TZ, NT>(jobs, total, t, s, pdl);
-#define SSX_CASE_MULTI_TAB(id, TX, TZ, NT) case id: return Stencil<SSX_R>::multi_tab<TX, TZ, NT>(jobs, njobs, total, t, s, pdl);
-#define SSX_CASE_CAPACITY(id, TX, TZ, NT) case id: return Stencil<SSX_R>::capacity<TX, TZ, NT>(adj);
-#define SSX_CASE_PREPARE(id, TX, TZ, NT) if (e == cudaSuccess) e = Stencil<SSX_R>::prepare<TX, TZ, NT>();
+// Quads exist for order 8 only: at other orders a quad configuration runs the
+// strip instance of its shape.
+#define SSX_QV(V) (SSX_R == 4 ? (V) : 0)
+#define SSX_CASE_FWD_STEP(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::fwd_step<TX, TZ, NT, SSX_QV(V)>(a, s, pdl);
+#define SSX_CASE_ADJ_STEP(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::adj_step<TX, TZ, NT, SSX_QV(V)>(a, s, pdl);
+#define SSX_CASE_FWD_PERSIST(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::fwd_persist<TX, TZ, NT, SSX_QV(V)>(a, pa, s);
+#define SSX_CASE_ADJ_PERSIST(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::adj_persist<TX, TZ, NT, SSX_QV(V)>(a, pa, s);
+#define SSX_CASE_MULTI(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::multi<TX, TZ, NT, SSX_QV(V)>(jobs, total, t, s, pdl);
+#define SSX_CASE_MULTI_TAB(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::multi_tab<TX, TZ, NT, SSX_QV(V)>(jobs, njobs, total, t, s, pdl);
+#define SSX_CASE_CAPACITY(id, TX, TZ, NT, V) case id: return Stencil<SSX_R>::capacity<TX, TZ, NT, SSX_QV(V)>(adj);
+#define SSX_CASE_PREPARE(id, TX, TZ, NT, V) if (e == cudaSuccess) e = Stencil<SSX_R>::prepare<TX, TZ, NT, SSX_QV(V)>();
 
 }  // namespace ssx

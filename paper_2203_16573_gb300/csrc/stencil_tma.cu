@@ -54,8 +54,8 @@ struct TmaStage {
 template <int TX, int TZ>
 struct TmaSmem {
     TmaStage<TX, TZ> st[2];
-    float svx[TZ][TX + 2 * kR - 1];    // C_v v_x of the step (as in TileSmem)
-    float svz[TZ + 2 * kR - 1][TX];
+    alignas(16) float svx[TZ][TX + 2 * kR];   // C_v v_x of the step (as in TileSmem, pitch in quads)
+    alignas(16) float svz[TZ + 2 * kR - 1][TX];
     Job job;                           // the current tile's sweep
     alignas(8) unsigned long long bar[2];
 };
@@ -63,9 +63,10 @@ struct TmaSmem {
 template <int TX, int TZ>
 constexpr size_t tma_smem_bytes() { return sizeof(TmaSmem<TX, TZ>); }
 
-template <int TX, int TZ, int NT>
+template <int TX, int TZ, int NT, int V>
 constexpr bool tma_shape_ok() {
-    return StripShape<kR, TX, TZ, NT>::ok && tma_smem_bytes<TX, TZ>() <= 232448;
+    return StripShape<kR, TX, TZ, NT>::ok && tma_smem_bytes<TX, TZ>() <= 232448 &&
+           (V == 0 || QuadShape<kR, TX, TZ, NT>::ok);
 }
 
 // ------------------------------------------------------------- operands --
@@ -89,6 +90,19 @@ struct TmaIn {
     __device__ __forceinline__ float own_p(int j) const { return st.p[rs + j + 2 * kR][c + 2 * kR]; }
     __device__ __forceinline__ float hvx(int r, int jj) const { return st.vx[r][jj]; }
     __device__ __forceinline__ float hvz(int kk, int i) const { return st.vz[kk][i - i0]; }
+    // by quads (fwd_quad / adj_quad)
+    __device__ __forceinline__ float4 vx4(int r, int jj) const {
+        return *reinterpret_cast<const float4 *>(&st.vx[r][jj]);
+    }
+    __device__ __forceinline__ float4 vz4(int kk, int c4) const {
+        return *reinterpret_cast<const float4 *>(&st.vz[kk][c4]);
+    }
+    __device__ __forceinline__ float4 kap4(int r, int c4) const {
+        return *reinterpret_cast<const float4 *>(&reinterpret_cast<const float(*)[TX]>(&st.k[0][0])[r][c4]);
+    }
+    __device__ __forceinline__ float4 p4(int r, int c4) const {
+        return *reinterpret_cast<const float4 *>(&st.p[r + 2 * kR][c4 + 2 * kR]);
+    }
     // the stage is complete (every thread waited on its barrier): nothing to
     // read ahead, nothing to wait for
     static constexpr bool kAhead = true;
@@ -104,13 +118,20 @@ struct TmaIn {
     template <bool PRE>
     __device__ __forceinline__ void stage() {
         if (!PRE) return;
-        constexpr int N = St::PH * St::PW;
+        constexpr int N4 = St::PH * St::PW / 4;   // by 16-byte quads (PW is a multiple of 4)
+        float4 *kq = reinterpret_cast<float4 *>(&st.k[0][0]);
+        const float4 *pq = reinterpret_cast<const float4 *>(&st.p[0][0]);
 #pragma unroll
-        for (int q = 0; q < (N + NT - 1) / NT; q++) {
+        for (int q = 0; q < (N4 + NT - 1) / NT; q++) {
             const int e = threadIdx.x + q * NT;
-            if (e < N) {
-                const int r = e / St::PW, x = e % St::PW;
-                st.k[r][x] = __fmul_rn(st.k[r][x], st.p[r][x]);
+            if (N4 % NT == 0 || e < N4) {
+                float4 v = kq[e];
+                const float4 pv = pq[e];
+                v.x = __fmul_rn(v.x, pv.x);
+                v.y = __fmul_rn(v.y, pv.y);
+                v.z = __fmul_rn(v.z, pv.z);
+                v.w = __fmul_rn(v.w, pv.w);
+                kq[e] = v;
             }
         }
         q_in_k = true;
@@ -118,10 +139,11 @@ struct TmaIn {
     __device__ __forceinline__ float (&sp())[TZ + 4 * kR][TX + 4 * kR] { return q_in_k ? st.k : st.p; }
 };
 
-template <int TX, int TZ, int NT>
+template <int TX, int TZ, int NT, int V>
 __device__ __forceinline__ void tma_tile(const Job &J, const StepIO &io, int i0, int k0,
                                          TmaStage<TX, TZ> &st, TmaSmem<TX, TZ> &sm) {
     using Q = StripShape<kR, TX, TZ, NT>;
+    constexpr bool kQuads = V == 1 && QuadShape<kR, TX, TZ, NT>::ok;
     const int c = threadIdx.x % TX, rs = (threadIdx.x / TX) * Q::L;
     if (J.adj) {
         const AdjArgs &a = J.aa;
@@ -130,10 +152,12 @@ __device__ __forceinline__ void tma_tile(const Job &J, const StepIO &io, int i0,
             adj_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
         } else if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
             TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
-            adj_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+            if constexpr (kQuads) adj_quad<kR, TX, TZ, NT, false>(a, io, i0, k0, ti, sm);
+            else adj_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
         } else {
             TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
-            adj_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+            if constexpr (kQuads) adj_quad<kR, TX, TZ, NT, true>(a, io, i0, k0, ti, sm);
+            else adj_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
         }
     } else {
         const FwdArgs &a = J.fa;
@@ -142,10 +166,12 @@ __device__ __forceinline__ void tma_tile(const Job &J, const StepIO &io, int i0,
             fwd_strip<kR, TX, TZ, NT, true, true>(a, io, i0, k0, ti, sm);
         } else if (interior_tile<kR, TX, TZ>(a.g, i0, k0)) {
             TmaIn<TX, TZ, NT, false> ti(st, a.g, i0, k0, rs, c);
-            fwd_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
+            if constexpr (kQuads) fwd_quad<kR, TX, TZ, NT, false>(a, io, i0, k0, ti, sm);
+            else fwd_strip<kR, TX, TZ, NT, false, false>(a, io, i0, k0, ti, sm);
         } else {
             TmaIn<TX, TZ, NT, true> ti(st, a.g, i0, k0, rs, c);
-            fwd_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
+            if constexpr (kQuads) fwd_quad<kR, TX, TZ, NT, true>(a, io, i0, k0, ti, sm);
+            else fwd_strip<kR, TX, TZ, NT, true, false>(a, io, i0, k0, ti, sm);
         }
     }
 }
@@ -169,7 +195,7 @@ __device__ __forceinline__ void issue(const TmaJob *__restrict__ jobs, int j, in
     else tma_load_2d(&st.k[0][0], &J.map[6], x0, y0, bar);
 }
 
-template <int TX, int TZ, int NT>
+template <int TX, int TZ, int NT, int V>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() : 1))
     k_multi_tma(const TmaJob *__restrict__ jobs, int njobs, int total, int t, int *err,
                 unsigned long long timeout_ns, int stall_tile) {
@@ -262,7 +288,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
         io.n = J.adj ? J.nt - 1 - st : st;
         int i0, k0;
         tile_corner<TX, TZ>(J.tx_mul, J.tx_shift, J.tiles_x, tl, i0, k0);
-        tma_tile<TX, TZ, NT>(J, io, i0, k0, sm.st[s], sm);
+        tma_tile<TX, TZ, NT, V>(J, io, i0, k0, sm.st[s], sm);
         // the transposed step rewrote stage s (q = C_p pbar over C_p) with
         // ordinary stores; order them before the copies that will refill it
         // (issued after the next tile's barrier)
@@ -274,22 +300,22 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? tile_min_ctas<TX, TZ, NT>() :
     }
 }
 
-template <int TX, int TZ, int NT>
+template <int TX, int TZ, int NT, int V>
 struct TmaKernel {
     static cudaError_t prepare() {
-        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return cudaSuccess;
+        if constexpr (!tma_shape_ok<TX, TZ, NT, V>()) return cudaSuccess;
         else
-            return cudaFuncSetAttribute(k_multi_tma<TX, TZ, NT>,
+            return cudaFuncSetAttribute(k_multi_tma<TX, TZ, NT, V>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)tma_smem_bytes<TX, TZ>());
     }
     static int capacity() {
-        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return 0;
+        if constexpr (!tma_shape_ok<TX, TZ, NT, V>()) return 0;
         else {
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_tma<TX, TZ, NT>, NT,
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_tma<TX, TZ, NT, V>, NT,
                                                               tma_smem_bytes<TX, TZ>()) != cudaSuccess)
                 return 0;
             return per_sm * sms;
@@ -298,7 +324,7 @@ struct TmaKernel {
     static cudaError_t launch(const TmaJob *jobs, int njobs, int total, int t, int *err,
                               unsigned long long timeout_ns, int stall_tile, int cap,
                               cudaStream_t s, bool pdl) {
-        if constexpr (!tma_shape_ok<TX, TZ, NT>()) return cudaErrorInvalidValue;
+        if constexpr (!tma_shape_ok<TX, TZ, NT, V>()) return cudaErrorInvalidValue;
         else {
             if (cap <= 0) return cudaErrorInvalidValue;
             cudaLaunchConfig_t cfg = {};
@@ -311,7 +337,7 @@ struct TmaKernel {
             at[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = pdl ? at : nullptr;
             cfg.numAttrs = pdl ? 1 : 0;
-            return cudaLaunchKernelEx(&cfg, k_multi_tma<TX, TZ, NT>, jobs, njobs, total, t, err,
+            return cudaLaunchKernelEx(&cfg, k_multi_tma<TX, TZ, NT, V>, jobs, njobs, total, t, err,
                                       timeout_ns, stall_tile);
         }
     }
@@ -321,7 +347,7 @@ struct TmaKernel {
 
 bool tma_shape_supported(int cfg) {
     switch (cfg) {
-#define SSX_CASE_TMA_OK(id, TX, TZ, NT) case id: return tma_shape_ok<TX, TZ, NT>();
+#define SSX_CASE_TMA_OK(id, TX, TZ, NT, V) case id: return tma_shape_ok<TX, TZ, NT, V>();
         SSX_TILE_CONFIGS(SSX_CASE_TMA_OK)
 #undef SSX_CASE_TMA_OK
     }
@@ -330,7 +356,7 @@ bool tma_shape_supported(int cfg) {
 
 int tma_capacity(int cfg) {
     switch (cfg) {
-#define SSX_CASE_TMA_CAP(id, TX, TZ, NT) case id: return TmaKernel<TX, TZ, NT>::capacity();
+#define SSX_CASE_TMA_CAP(id, TX, TZ, NT, V) case id: return TmaKernel<TX, TZ, NT, V>::capacity();
         SSX_TILE_CONFIGS(SSX_CASE_TMA_CAP)
 #undef SSX_CASE_TMA_CAP
     }
@@ -339,7 +365,7 @@ int tma_capacity(int cfg) {
 
 cudaError_t prepare_tma_kernels() {
     cudaError_t e = cudaSuccess;
-#define SSX_CASE_TMA_PREP(id, TX, TZ, NT) if (e == cudaSuccess) e = TmaKernel<TX, TZ, NT>::prepare();
+#define SSX_CASE_TMA_PREP(id, TX, TZ, NT, V) if (e == cudaSuccess) e = TmaKernel<TX, TZ, NT, V>::prepare();
     SSX_TILE_CONFIGS(SSX_CASE_TMA_PREP)
 #undef SSX_CASE_TMA_PREP
     return e;
@@ -349,8 +375,8 @@ cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int
                              int cap, int *err, unsigned long long timeout_ns, int stall_tile,
                              cudaStream_t s, bool pdl) {
     switch (cfg) {
-#define SSX_CASE_TMA_LAUNCH(id, TX, TZ, NT) \
-    case id: return TmaKernel<TX, TZ, NT>::launch(jobs, njobs, total_tiles, t, err, timeout_ns, stall_tile, cap, s, pdl);
+#define SSX_CASE_TMA_LAUNCH(id, TX, TZ, NT, V) \
+    case id: return TmaKernel<TX, TZ, NT, V>::launch(jobs, njobs, total_tiles, t, err, timeout_ns, stall_tile, cap, s, pdl);
         SSX_TILE_CONFIGS(SSX_CASE_TMA_LAUNCH)
 #undef SSX_CASE_TMA_LAUNCH
     }

@@ -114,11 +114,13 @@ def test_bench_kernel_names_match_the_configuration_tables():
     sys.path.insert(0, ROOT)
     import bench
     src = open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "ssx_internal.cuh")).read()
-    tile = re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)", src)
+    tile = re.findall(r"X\((\d+), (\d+), (\d+), (\d+), ([01])\)", src)
     march = re.findall(r"X\((\d+), (\d+), (\d+)\)\s", src)
-    assert len(tile) == 8 and len(march) == 4
-    for cid, tx, tz, nt in tile:
-        assert bench._kernel_name(int(cid)) == f"k_multi {tx}x{tz}/{nt}"
-        assert bench._kernel_name(int(cid) + 8) == f"k_multi_tma {tx}x{tz}/{nt}"
+    n = len(tile)
+    assert n == 13 and len(march) == 4
+    for cid, tx, tz, nt, quads in tile:
+        name = f"{tx}x{tz}/{nt}" + (" quads" if quads == "1" else "")
+        assert bench._kernel_name(int(cid)) == f"k_multi {name}"
+        assert bench._kernel_name(int(cid) + n) == f"k_multi_tma {name}"
     for cid, tx, tz in march:
-        assert bench._kernel_name(int(cid) + 16) == f"k_march {tx}x{tz}"
+        assert bench._kernel_name(int(cid) + 2 * n) == f"k_march {tx}x{tz}"
