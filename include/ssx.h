@@ -325,10 +325,15 @@ int ssx_set_test_hook(ssx_ctx *ctx, int hook, int k);
  * space order 8; for other orders 13 + k runs shape k; 26 + m fixes the
  * marching kernel of shape m (tiles of 64 x 128, 128 x 64, 128 x 128,
  * 128 x 32 points, one thread per column walking down it in blocks of 8 rows
- * fed by tensor copies), available for space order 8 (else shape 0 runs).
- * All configurations compute identical results. */
+ * fed by tensor copies), available for space order 8 (else shape 0 runs);
+ * 30 + m fixes, for the phases of a single sweep, the two-step kernel of
+ * shape m (tiles of 32 x 16 with 256 or 512 threads, 32 x 32 with 512:
+ * temporal blocking, two time steps per launch with the intermediate step
+ * kept in shared memory), available for space order 8 (other phases run
+ * shape 0). All configurations compute identical results. */
 #define SSX_NUM_TILE_CONFIGS 13
 #define SSX_NUM_MARCH_CONFIGS 4
+#define SSX_NUM_TWO_CONFIGS 3
 int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
 
 /* Timing mode: when on, every sweep is bracketed by CUDA events on the
@@ -346,7 +351,7 @@ int ssx_reset_stats(ssx_ctx *ctx);
  * row. Row k (from 0, in order of first appearance): the phase's name
  * (NUL-terminated, truncated to name_len - 1 characters), its sweeps, the
  * tiles of its largest launch, its tile configuration (0-12 plain kernel,
- * 13-25 TMA-staged, 26-29 marching), its dependent-launch chain length (every
+ * 13-25 TMA-staged, 26-29 marching, 30-32 two steps per launch), its dependent-launch chain length (every
  * chain-th launch an ordinary launch; 0: one chain a span), its event-timed
  * device time and its time steps (launches). SSX_ERR_ARG for k past the
  * last row or a NULL output. Synchronises. */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libssx.so")
 SOURCES = ["stencil.cu", "stencil_r1.cu", "stencil_r2.cu", "stencil_r3.cu", "stencil_r4.cu",
-           "stencil_tma.cu", "stencil_march.cu", "krylov.cu", "gradient.cu", "runtime.cu",
+           "stencil_tma.cu", "stencil_march.cu", "stencil_two.cu", "krylov.cu", "gradient.cu", "runtime.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

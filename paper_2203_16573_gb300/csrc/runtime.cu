@@ -201,11 +201,15 @@ int fail(ssx_ctx *c, int code, const std::string &msg) {
 
 // Phase-kernel configuration ids: 0 .. kNumTileCfgs - 1 the plain tile kernel
 // (shape id), kNumTileCfgs .. 2 kNumTileCfgs - 1 the TMA-staged tile kernel of
-// shape id - kNumTileCfgs, then the marching kernel's shapes.
+// shape id - kNumTileCfgs, then the marching kernel's shapes, then the
+// two-step kernel's (single-sweep phases: two time steps per launch).
 constexpr int kCfgMarch0 = 2 * kNumTileCfgs;
-constexpr int kNumAllCfgs = kCfgMarch0 + kNumMarchCfgs;
+constexpr int kCfgTwo0 = kCfgMarch0 + kNumMarchCfgs;
+constexpr int kNumAllCfgs = kCfgTwo0 + kNumTwoCfgs;
 void tile_dims(int cfg, int *tx, int *tz) {
-    const TileCfg &t = cfg >= kCfgMarch0 ? kMarchCfgs[cfg - kCfgMarch0] : kTileCfgs[cfg % kNumTileCfgs];
+    const TileCfg &t = cfg >= kCfgTwo0     ? kTwoCfgs[cfg - kCfgTwo0]
+                       : cfg >= kCfgMarch0 ? kMarchCfgs[cfg - kCfgMarch0]
+                                           : kTileCfgs[cfg % kNumTileCfgs];
     *tx = t.tx;
     *tz = t.tz;
 }
@@ -732,6 +736,12 @@ bool march_usable(ssx_ctx *c, int m) {
     return c->march_cap[m] > 0 && tensor_map_encoder() != nullptr;
 }
 
+// the two-step kernel runs a phase: one sweep from the phase's first launch,
+// order 8
+bool two_usable(ssx_ctx *c, const std::vector<Sweep> &sw) {
+    return c->R == kMaxR && sw.size() == 1 && sw[0].offset == 0;
+}
+
 // the TMA-staged kernel runs shape `base` for this context (order 8 only)
 bool tma_usable(ssx_ctx *c, int base) {
     if (c->R != kMaxR || base < 0 || base >= kNumTileCfgs || !tma_shape_supported(base)) return false;
@@ -794,6 +804,13 @@ int stage_args(ssx_ctx *c, const std::vector<Sweep> &sw, int cfg, bool quiet, Ph
     };
     // offsets are kept +1 in the pointer fields until the upload resolves them
     auto tag = [](size_t off) { return (void *)(off + 1); };
+    if (cfg >= kCfgTwo0) {
+        if (!two_usable(c, sw)) return fail(c, SSX_ERR_ARG, "two-step kernel not available");
+        memset(&pa->set, 0, sizeof pa->set);
+        pa->set.njobs = 1;
+        pa->set.job[0] = jobs[0];
+        return SSX_OK;
+    }
     if (cfg >= kCfgMarch0) {
         const int m = cfg - kCfgMarch0;
         // the choice may come from another context's tuning: this context's
@@ -872,8 +889,8 @@ int phase_len(const std::vector<Sweep> &sw) {
 // the chain length).
 int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &pa, int t0, int t1,
                      int cfg, cudaStream_t s, bool with_init, bool stall = false, int chain = 0) {
-    for (int t = t0; t < t1; t++) {
-        const bool brk = chain > 0 && (t - t0) % chain == 0;
+    // transposed sweeps starting at launch t get their initial state first
+    auto inits = [&](int t) -> int {
         if (with_init)
             for (const Sweep &w : sw)
                 if (w.adj && w.offset == t) {
@@ -887,6 +904,20 @@ int enqueue_launches(ssx_ctx *c, const std::vector<Sweep> &sw, const PhaseArgs &
                     a.vz_in = w.G->f[0][2];
                     CK(launch_adj_init(a, w.nt, s));
                 }
+        return SSX_OK;
+    };
+    if (cfg >= kCfgTwo0) {   // two time steps per launch: launch u runs steps 2u and 2u + 1
+        const int u0 = t0 / 2;
+        for (int u = u0; 2 * u < t1; u++) {
+            const bool brk = chain > 0 && (u - u0) % chain == 0;
+            TRY(inits(2 * u));
+            CK(launch_two(pa.set, pa.total, u, 2 * u + 1 < t1, cfg - kCfgTwo0, s, u != u0 && !brk));
+        }
+        return SSX_OK;
+    }
+    for (int t = t0; t < t1; t++) {
+        const bool brk = chain > 0 && (t - t0) % chain == 0;
+        TRY(inits(t));
         if (pa.mtab)
             CK(launch_march(pa.mtab, pa.njobs, pa.total, t, cfg - kCfgMarch0, pa.cap, c->d_err,
                             stall && t == 0 ? 200000000ull : 2000000000ull,
@@ -1002,7 +1033,8 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
     const bool forced = c->forced_cfg >= 0;
     if (forced) {
         const int f = c->forced_cfg;
-        if (f >= kCfgMarch0) *best_cfg = march_usable(c, f - kCfgMarch0) ? f : 0;
+        if (f >= kCfgTwo0) *best_cfg = two_usable(c, sw) ? f : 0;
+        else if (f >= kCfgMarch0) *best_cfg = march_usable(c, f - kCfgMarch0) ? f : 0;
         else *best_cfg = (f >= kNumTileCfgs && !tma_usable(c, f - kNumTileCfgs)) ? f - kNumTileCfgs : f;
     } else {
         std::lock_guard<std::mutex> lock(g_phase_mu);
@@ -1017,7 +1049,9 @@ int tune_phase(ssx_ctx *c, const char *name, const std::vector<Sweep> &sw, int *
         const int T = std::min(phase_len(sw), 48);
         float best = 1e30f;
         for (int k = 0; k < kNumAllCfgs; k++) {
-            if (k >= kCfgMarch0) {
+            if (k >= kCfgTwo0) {
+                if (!two_usable(c, sw)) continue;
+            } else if (k >= kCfgMarch0) {
                 if (!march_usable(c, k - kCfgMarch0)) continue;
             } else if (k >= kNumTileCfgs && !tma_usable(c, k - kNumTileCfgs)) {
                 continue;
@@ -1115,7 +1149,7 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
     const ssx_ctx::PhaseInfo &info = it->second;
     // test hook: the next TMA-staged phase withholds the copies of its first
     // tile in its first launch (run uncached, so no graph keeps the stall)
-    const bool stall = c->stall_next && info.cfg >= kNumTileCfgs;
+    const bool stall = c->stall_next && info.cfg >= kNumTileCfgs && info.cfg < kCfgTwo0;
     if (stall) c->stall_next = false;
     auto enqueue = [&](cudaStream_t s) -> int {
         for (const Sweep &w : sw) {
@@ -1169,7 +1203,9 @@ int run_phase(ssx_ctx *c, const char *name, std::vector<Sweep> sw) {
         c->use_graphs = g0;
         return rc;
     }
-    return run_cached(c, "phase" + std::to_string(info.cfg) + key, info.T + inits, info.T, pts,
+    // kernel launches: one per time step, or one per two for the two-step kernel
+    const long long launches = info.cfg >= kCfgTwo0 ? (info.T + 1) / 2 : info.T;
+    return run_cached(c, "phase" + std::to_string(info.cfg) + key, launches + inits, info.T, pts,
                       enqueue);
 }
 

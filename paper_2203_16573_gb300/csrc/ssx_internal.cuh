@@ -194,6 +194,14 @@ extern const TileCfg kTileCfgs[kNumTileCfgs];
     X(3, 128, 32)
 constexpr int kNumMarchCfgs = 4;
 extern const TileCfg kMarchCfgs[kNumMarchCfgs];
+// Two-step (temporally blocked) phase kernel shapes (stencil_two.cu, order 8,
+// single-sweep phases): (id, TX, TZ, threads per CTA).
+#define SSX_TWO_CONFIGS(X) \
+    X(0, 32, 16, 256)      \
+    X(1, 32, 16, 512)      \
+    X(2, 32, 32, 512)
+constexpr int kNumTwoCfgs = 3;
+extern const TileCfg kTwoCfgs[kNumTwoCfgs];
 
 // Kernel launchers (stencil.cu). Return the launch's cudaError_t. `pdl` sets
 // programmatic dependent launch (the step waits in-kernel for the previous one).
@@ -216,6 +224,12 @@ cudaError_t prepare_kernels();                     // dynamic shared-memory limi
 bool tma_shape_supported(int cfg);                 // shape cfg has a TMA-staged kernel
 int tma_capacity(int cfg);                         // its co-resident CTAs (the launch's grid cap)
 cudaError_t prepare_tma_kernels();
+// The two-step phase kernel (stencil_two.cu): launch t of a phase of one
+// sweep (jobs.njobs == 1, offset 0) advances it by steps 2t and 2t + 1 (only
+// 2t when `two` is false), reading buffer t mod 2 and writing the other.
+cudaError_t prepare_two_kernels();
+cudaError_t launch_two(const JobSet &jobs, int total_tiles, int t, bool two, int m, cudaStream_t s,
+                       bool pdl);
 // stall_tile >= 0 (test hook): that tile's copies are never issued, so the
 // CTA's bounded wait runs out and reports error 2
 cudaError_t launch_multi_tma(const TmaJob *jobs, int njobs, int total_tiles, int t, int cfg,

@@ -191,6 +191,7 @@ cudaError_t prepare_kernels() {
     if ((e = stencil_prepare_r3()) != cudaSuccess) return e;
     if ((e = stencil_prepare_r4()) != cudaSuccess) return e;
     if ((e = prepare_march_kernels()) != cudaSuccess) return e;
+    if ((e = prepare_two_kernels()) != cudaSuccess) return e;
     return prepare_tma_kernels();
 }
 

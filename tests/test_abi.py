@@ -42,6 +42,9 @@ def test_binding_constants_match_the_header():
     nm = int(re.search(r"#define SSX_NUM_MARCH_CONFIGS (\d+)", text).group(1))
     assert ssx.N_MARCH_CONFIGS == nm
     assert re.search(r"constexpr int kNumMarchCfgs = (\d+);", src).group(1) == str(nm)
+    n2 = int(re.search(r"#define SSX_NUM_TWO_CONFIGS (\d+)", text).group(1))
+    assert ssx.N_TWO_CONFIGS == n2
+    assert re.search(r"constexpr int kNumTwoCfgs = (\d+);", src).group(1) == str(n2)
 
 
 def test_version_string(lib):
@@ -116,11 +119,14 @@ def test_bench_kernel_names_match_the_configuration_tables():
     src = open(os.path.join(ROOT, "paper_2203_16573_gb300", "csrc", "ssx_internal.cuh")).read()
     tile = re.findall(r"X\((\d+), (\d+), (\d+), (\d+), ([01])\)", src)
     march = re.findall(r"X\((\d+), (\d+), (\d+)\)\s", src)
+    two = re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)\s", src)
     n = len(tile)
-    assert n == 13 and len(march) == 4
+    assert n == 13 and len(march) == 4 and len(two) == 3
     for cid, tx, tz, nt, quads in tile:
         name = f"{tx}x{tz}/{nt}" + (" quads" if quads == "1" else "")
         assert bench._kernel_name(int(cid)) == f"k_multi {name}"
         assert bench._kernel_name(int(cid) + n) == f"k_multi_tma {name}"
     for cid, tx, tz in march:
         assert bench._kernel_name(int(cid) + 2 * n) == f"k_march {tx}x{tz}"
+    for cid, tx, tz, nt in two:
+        assert bench._kernel_name(int(cid) + 2 * n + len(march)) == f"k_two {tx}x{tz}/{nt}"

@@ -330,6 +330,24 @@ def test_march_kernel_parity_and_copy_wait_timeout(ssx, oracle, cfg_offset):
     ctx.set_tile_config(-1)
 
 
+@pytest.mark.parametrize("m,nt", [(0, 160), (1, 161), (2, 160)])
+def test_two_step_kernel_parity(ssx, oracle, m, nt):
+    """The two-step (temporally blocked) phase kernel forced on every phase of
+    one sweep: S, S^T, W~_d and a preconditioned solve (whose M^-1 slab
+    phases are single sweeps) against the oracle, with both lines between grid
+    rows; an odd step count ends with a launch of one step."""
+    spec = frac_spec(8, nt=nt)
+    ctx, P = make(ssx, oracle, spec)
+    ctx.set_tile_config(2 * ssx.N_TILE_CONFIGS + ssx.N_MARCH_CONFIGS + m)
+    h = W.smooth_random_gather(spec.nt, spec.n_line, 25)
+    d = W.smooth_random_gather(spec.nt, spec.n_rec, 26)
+    assert rel(ctx.forward(dev(h)), P.S(h)) <= TOL
+    assert rel(ctx.adjoint(dev(d)), P.ST(d)) <= TOL
+    assert rel(ctx.weight_apply(ssx.W_D, dev(d)), P.Wd(d)) <= TOL
+    _check_solve(ctx, P, spec, d, "pcg", 4, 0.0)
+    ctx.set_tile_config(-1)
+
+
 def test_tma_copy_wait_timeout_is_reported_and_context_survives(ssx):
     """The TMA-staged phase kernel: a tile whose copies are withheld (test
     hook) makes its CTA's bounded mbarrier wait run out (0.2 s); the call
@@ -348,13 +366,15 @@ def test_tma_copy_wait_timeout_is_reported_and_context_survives(ssx):
     ctx.set_tile_config(-1)
 
 
-@pytest.mark.parametrize("order", [4, 8])
-def test_every_tile_configuration_gives_identical_results(ssx, order):
+@pytest.mark.parametrize("order,nt", [(4, 120), (8, 120), (8, 121)])
+def test_every_tile_configuration_gives_identical_results(ssx, order, nt):
     """All tile shapes / CTA sizes, both launch forms, the TMA-staged phase
-    kernel (ids N..2N-1) and the marching kernel (ids 2N..; order 8) run the
-    same per-point arithmetic: bitwise-identical sweeps (ragged tiles on both
-    grid edges, lines between rows)."""
-    spec = frac_spec(order, nt=120)
+    kernel (ids N..2N-1), the marching kernel (ids 2N..; order 8) and the
+    two-step kernel (two time steps per launch; order 8; an odd step count
+    ends with a launch of one step) run the same per-point arithmetic:
+    bitwise-identical sweeps (ragged tiles on both grid edges, lines between
+    rows)."""
+    spec = frac_spec(order, nt=nt)
     ctx = ssx.Context.for_problem(spec, W.velocity(spec))
     x = dev(W.smooth_random_gather(spec.nt, spec.n_line, 19))
     y = dev(W.smooth_random_gather(spec.nt, spec.n_rec, 20))
@@ -362,7 +382,8 @@ def test_every_tile_configuration_gives_identical_results(ssx, order):
     for mode in (ssx.SWEEP_STEP, ssx.SWEEP_PERSISTENT):
         ctx.set_sweep_mode(mode)
         N = ssx.N_TILE_CONFIGS
-        for cfg in range(2 * N + ssx.N_MARCH_CONFIGS if mode == ssx.SWEEP_STEP else N):
+        n_all = 2 * N + ssx.N_MARCH_CONFIGS + ssx.N_TWO_CONFIGS
+        for cfg in range(n_all if mode == ssx.SWEEP_STEP else N):
             ctx.set_tile_config(cfg)
             got = (ctx.forward(x).clone(), ctx.adjoint(y).clone(),
                    ctx.weight_apply(ssx.W_D, y).clone())
@@ -395,7 +416,7 @@ def test_phase_breakdown_accounts_for_the_timed_sweeps(ssx):
     assert {"e1", "e2", "e3", "e4"} <= names, rows
     for r in rows:
         assert r["ms"] > 0 and r["steps"] >= spec.nt and r["sweeps"] >= 1 and r["tiles"] >= 1
-        assert 0 <= r["tile_config"] < 2 * ssx.N_TILE_CONFIGS + ssx.N_MARCH_CONFIGS
+        assert 0 <= r["tile_config"] < 2 * ssx.N_TILE_CONFIGS + ssx.N_MARCH_CONFIGS + ssx.N_TWO_CONFIGS
         assert r["chain"] in (0, 8, 16, 32)
     assert sum(r["ms"] for r in rows) <= st["sweep_ms"] * (1 + 1e-6)
     assert sum(r["steps"] for r in rows) <= st["timed_steps"]
