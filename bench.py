@@ -699,7 +699,7 @@ def _kernel_name(cfg):
     nt = ssx.N_TILE_CONFIGS
     shapes = ["64x16/256", "64x16/512", "32x32/256", "64x32/512", "64x32/1024", "128x16/512",
               "128x32/1024", "32x16/256", "64x16/256 quads", "32x32/256 quads", "64x32/512 quads",
-              "128x16/512 quads", "128x32/1024 quads"]
+              "128x16/512 quads", "128x32/1024 quads", "64x16/128 quads"]
     march = ["64x128", "128x64", "128x128", "128x32"]
     two = ["32x16/256", "32x16/512", "32x32/512"]
     if 0 <= cfg < nt:
@@ -755,7 +755,7 @@ def main():
     ap.add_argument("--cache-mb", type=float, default=-1,
                     help="serve: working-set admission limit in MB (0: off; default: 4x the L2 size)")
     ap.add_argument("--tile-config", type=int, default=-1,
-                    help="fix the stencil tile configuration (0-12; 13-25: TMA-staged phase kernel of shape 0-12; 26-29: marching kernel; 30-32: two steps per launch) instead of autotuning")
+                    help="fix the stencil tile configuration (0-13; 14-27: TMA-staged phase kernel of shape 0-13; 28-31: marching kernel; 32-34: two steps per launch) instead of autotuning")
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--nt", type=int, default=0,
                     help="time steps (0: the workload's own; c3 default 5000)")

@@ -314,24 +314,24 @@ int ssx_set_test_hook(ssx_ctx *ctx, int hook, int k);
 
 /* Tile configuration of the step kernels: -1 (default) lets the library time
  * every configuration on each grid's first sweep in each direction and keep
- * the fastest; 0..12 fixes one shape: 0..7 step by column strips (tile
+ * the fastest; 0..13 fixes one shape: 0..7 step by column strips (tile
  * 64x16/256 threads, 64x16/512, 32x32/256, 64x32/512, 64x32/1024, 128x16/512,
- * 128x32/1024, 32x16/256), 8..12 by quads, one thread per four consecutive
+ * 128x32/1024, 32x16/256), 8..13 by quads, one thread per four consecutive
  * columns with 16-byte vector operands (64x16/256, 32x32/256, 64x32/512,
- * 128x16/512, 128x32/1024; for space order 8, other orders run them as
- * strips); 13 + k fixes shape k with the multi-sweep steps run by the
- * TMA-staged kernel (operand tiles copied by the tensor memory accelerator
- * into a two-stage shared-memory pipeline, persistent CTAs), available for
- * space order 8; for other orders 13 + k runs shape k; 26 + m fixes the
- * marching kernel of shape m (tiles of 64 x 128, 128 x 64, 128 x 128,
- * 128 x 32 points, one thread per column walking down it in blocks of 8 rows
- * fed by tensor copies), available for space order 8 (else shape 0 runs);
- * 30 + m fixes, for the phases of a single sweep, the two-step kernel of
- * shape m (tiles of 32 x 16 with 256 or 512 threads, 32 x 32 with 512:
- * temporal blocking, two time steps per launch with the intermediate step
- * kept in shared memory), available for space order 8 (other phases run
- * shape 0). All configurations compute identical results. */
-#define SSX_NUM_TILE_CONFIGS 13
+ * 128x16/512, 128x32/1024 with one row a thread; 64x16/128 with two; for
+ * space order 8, other orders run them as strips); 14 + k fixes shape k with
+ * the multi-sweep steps run by the TMA-staged kernel (operand tiles copied by
+ * the tensor memory accelerator into a two-stage shared-memory pipeline,
+ * persistent CTAs), available for space order 8; for other orders 14 + k
+ * runs shape k; 28 + m fixes the marching kernel of shape m (tiles of
+ * 64 x 128, 128 x 64, 128 x 128, 128 x 32 points, one thread per column
+ * walking down it in blocks of 8 rows fed by tensor copies), available for
+ * space order 8 (else shape 0 runs); 32 + m fixes, for the phases of a
+ * single sweep, the two-step kernel of shape m (tiles of 32 x 16 with 256 or
+ * 512 threads, 32 x 32 with 512: temporal blocking, two time steps per launch
+ * with the intermediate step kept in shared memory), available for space
+ * order 8 (other phases run shape 0). All configurations compute identical results. */
+#define SSX_NUM_TILE_CONFIGS 14
 #define SSX_NUM_MARCH_CONFIGS 4
 #define SSX_NUM_TWO_CONFIGS 3
 int ssx_set_tile_config(ssx_ctx *ctx, int cfg);
@@ -350,8 +350,8 @@ int ssx_reset_stats(ssx_ctx *ctx);
  * the same name, sweep count, tile count and kernel configuration share a
  * row. Row k (from 0, in order of first appearance): the phase's name
  * (NUL-terminated, truncated to name_len - 1 characters), its sweeps, the
- * tiles of its largest launch, its tile configuration (0-12 plain kernel,
- * 13-25 TMA-staged, 26-29 marching, 30-32 two steps per launch), its dependent-launch chain length (every
+ * tiles of its largest launch, its tile configuration (0-13 plain kernel,
+ * 14-27 TMA-staged, 28-31 marching, 32-34 two steps per launch), its dependent-launch chain length (every
  * chain-th launch an ordinary launch; 0: one chain a span), its event-timed
  * device time and its time steps (launches). SSX_ERR_ARG for k past the
  * last row or a NULL output. Synchronises. */

@@ -160,8 +160,8 @@ struct JobSet {
 };
 
 // Tile configurations of the step kernels: (id, TX, TZ, threads per CTA,
-// quads). With quads = 1 the CTA has one thread per 4-column quad of the tile
-// and its interior and sponge tiles step by 16-byte vectors (order 8; at
+// quads). With quads = 1 the CTA has one thread per 4-column quad of one or
+// two tile rows, and its interior and sponge tiles step by 16-byte vectors (order 8; at
 // other orders the configuration runs as strips, like its quads = 0 twin).
 // Every configuration computes bit-identical results; the runtime picks one
 // per grid and direction by timing them (autotune). TX, TZ >= 2k keeps the
@@ -179,8 +179,9 @@ struct JobSet {
     X(9, 32, 32, 256, 1)    \
     X(10, 64, 32, 512, 1)   \
     X(11, 128, 16, 512, 1)  \
-    X(12, 128, 32, 1024, 1)
-constexpr int kNumTileCfgs = 13;
+    X(12, 128, 32, 1024, 1) \
+    X(13, 64, 16, 128, 1)
+constexpr int kNumTileCfgs = 14;
 struct TileCfg {
     int tx, tz, threads;
     int quads;   // 1: interior and sponge tiles step by quads (order 8)

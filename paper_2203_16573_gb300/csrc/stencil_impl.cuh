@@ -1215,12 +1215,13 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
 
 // ---------------------------------------------------------------------------
 // Tiles by quads (order 8). Thread t owns the four consecutive columns
-// i0 + c4 .. i0 + c4 + 3, c4 = 4 (t mod TX/4), of tile row t / (TX/4): the
-// CTA has one thread per quad of the tile. Every operand moves as a 16-byte
-// vector: the thread's own v, kappa and p, the x differences (the eleven
-// values an 8-point difference of four consecutive points needs sit in three
-// aligned quads of a staged row) and the z differences (eight quads down the
-// column). The halo values of v (2k-1 rows of v_z, a quad of v_x on each side
+// i0 + c4 .. i0 + c4 + 3, c4 = 4 (t mod TX/4), of tile rows L (t / (TX/4))
+// .. + L - 1 (L = 1 or 2 quads down its column, as the CTA size gives). Every
+// operand moves as a 16-byte vector: the thread's own v, kappa and p, the x
+// differences (the eleven values an 8-point difference of four consecutive
+// points needs sit in three aligned quads of a staged row) and the z
+// differences (a window of 2k + L - 1 quads down the column, shared by the
+// thread's L rows). The halo values of v (2k-1 rows of v_z, a quad of v_x on each side
 // of every tile row) are shared out over all threads as quads. Per point the
 // arithmetic is the strips' (fwd_strip / adj_strip), term for term and in the
 // same order, so every tile configuration still gives the same bits. Tiles
@@ -1229,7 +1230,10 @@ __device__ __forceinline__ void adj_strip(const AdjArgs &a, const StepIO &io, in
 template <int R, int TX, int TZ, int NT>
 struct QuadShape {
     static constexpr int QW = TX / 4;                      // quads per tile row
-    static constexpr bool ok = R == 4 && TX % 4 == 0 && NT * 4 == TX * TZ;
+    // rows per thread: the thread's quads are rows r .. r + L - 1 of its column
+    static constexpr int L = NT > 0 ? TX * TZ / (4 * NT) : 0;
+    static constexpr bool ok = R == 4 && TX % 4 == 0 && (L == 1 || L == 2) && NT * 4 * L == TX * TZ;
+    static constexpr int NW = 2 * R + L - 1;               // quads of a column window
     static constexpr int NHZ = (2 * R - 1) * QW;           // v_z halo quads
     static constexpr int NHX = 2 * TZ;                     // v_x halo quads
     static constexpr int NH = (NHZ + NHX + NT - 1) / NT;   // halo quads per thread
@@ -1282,28 +1286,28 @@ __device__ __forceinline__ Q4 xdiff(const float *x, const float (&cc)[R]) {
     }
     return d;
 }
-// the z difference of a quad from the 2k quads of a column window w[0 .. 2k-1]:
-// w[k - 1 + m] - w[k - m]
-template <int R>
-__device__ __forceinline__ Q4 zdiff(const Q4 (&w)[2 * R], const float (&cc)[R]) {
+// the z difference of the quad whose 2k-quad column window starts at w[j]:
+// w[j + k - 1 + m] - w[j + k - m]
+template <int R, int NW>
+__device__ __forceinline__ Q4 zdiff(const Q4 (&w)[NW], int j, const float (&cc)[R]) {
     Q4 d;
 #pragma unroll
     for (int e = 0; e < 4; e++) {
         float s = 0.0f;
 #pragma unroll
-        for (int m = 1; m <= R; m++) s = fmaf(cc[m - 1], w[R - 1 + m].e[e] - w[R - m].e[e], s);
+        for (int m = 1; m <= R; m++) s = fmaf(cc[m - 1], w[j + R - 1 + m].e[e] - w[j + R - m].e[e], s);
         d.e[e] = s;
     }
     return d;
 }
-// the 2k quads of a column window: rows row0, row0 + 1, ... of a staged field
-template <int R, int PW>
-__device__ __forceinline__ void window(Q4 (&w)[2 * R], const float (*rows)[PW], int row0, int col) {
+// the NW quads of a column window: rows row0, row0 + 1, ... of a staged field
+template <int NW, int PW>
+__device__ __forceinline__ void window(Q4 (&w)[NW], const float (*rows)[PW], int row0, int col) {
 #pragma unroll
-    for (int q = 0; q < 2 * R; q++) w[q] = lds4(&rows[row0 + q][col]);
+    for (int q = 0; q < NW; q++) w[q] = lds4(&rows[row0 + q][col]);
 }
 
-// a thread's quad and its halo items: kind 1 = v_z quad at v_z row a,
+// a thread's quads and its halo items: kind 1 = v_z quad at v_z row a,
 // column b; kind 2 = v_x quad at tile row a, v_x column b (x = i0 - k + b);
 // kind 0 = none
 template <int R, int TX, int TZ, int NT>
@@ -1314,7 +1318,7 @@ struct QuadThread {
     __device__ __forceinline__ QuadThread() {
         const int t = threadIdx.x;
         c4 = 4 * (t % Q::QW);
-        r = t / Q::QW;
+        r = Q::L * (t / Q::QW);
 #pragma unroll
         for (int q = 0; q < Q::NH; q++) {
             const int e = t + q * NT;
@@ -1341,7 +1345,7 @@ template <int R, int TX, int TZ, int NT, bool SP, class In, class Work>
 __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int i0, int k0,
                                          In &in, Work &sm) {
     using Q = QuadShape<R, TX, TZ, NT>;
-    constexpr int H = 2 * R;
+    constexpr int H = 2 * R, L = Q::L, NW = Q::NW;
     const GridArgs &g = a.g;
     const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
     const QuadThread<R, TX, TZ, NT> th;
@@ -1352,7 +1356,7 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
     const float cv = g.cv;
 
     // the grid's constants before the wait for the previous step, the fields after it
-    float sxi[4], sxh[4], szi = 0.0f, szh = 0.0f;
+    float sxi[4], sxh[4], szi[L], szh[L];
     if (!In::kAhead) in.wait();
     if (SP) {
 #pragma unroll
@@ -1360,12 +1364,22 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
             sxi[e] = __ldg(g.sxi + min(i + e, NX - 1));   // clamped: masked points take any value
             sxh[e] = __ldg(g.sxh + min(i + e, NX - 1));
         }
-        szi = __ldg(g.szi + min(k, NZ - 1));
-        szh = __ldg(g.szh + min(k, NZ - 1));
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            szi[j] = __ldg(g.szi + min(k + j, NZ - 1));
+            szh[j] = __ldg(g.szh + min(k + j, NZ - 1));
+        }
     }
-    const Q4 rk = q4(in.kap4(r, c4));
+    Q4 rk[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) rk[j] = q4(in.kap4(r + j, c4));
     if (In::kAhead) in.wait();
-    const Q4 rvx = q4(in.vx4(r, c4 + R)), rvz = q4(in.vz4(r + R, c4));
+    Q4 rvx[L], rvz[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        rvx[j] = q4(in.vx4(r + j, c4 + R));
+        rvz[j] = q4(in.vz4(r + j + R, c4));
+    }
     Q4 rh[Q::NH];
 #pragma unroll
     for (int q = 0; q < Q::NH; q++)
@@ -1375,53 +1389,57 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
     if (!In::kStaged) __syncthreads();   // p staged by all threads
     float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
 
-    // own quad: v_z from the column window, v_x from the row
-    Q4 pw[2 * R];
-    window<R, TX + 4 * R>(pw, spa, r + H - R + 1, c4 + H);
-    const Q4 pold = pw[R - 1];
-    {
-        const Q4 d = zdiff<R>(pw, cc);
+    // own quads: v_z from the column window, v_x from the rows
+    Q4 pw[NW];
+    window<NW, TX + 4 * R>(pw, spa, r + H - R + 1, c4 + H);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const Q4 d = zdiff<R>(pw, j, cc);
         Q4 vz;
         bool ok[4];
         bool all = true;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            ok[e] = !SP || (i + e < NX && k < NZ - 1);
+            ok[e] = !SP || (i + e < NX && k + j < NZ - 1);
             all = all && ok[e];
             if (SP) {
                 float A, B;
-                damp(sxi[e] + szh, A, B);
+                damp(sxi[e] + szh[j], A, B);
                 const float cvz = B * cv;
-                vz.e[e] = fmaf(-cvz, d.e[e], A * rvz.e[e]);
+                vz.e[e] = fmaf(-cvz, d.e[e], A * rvz[j].e[e]);
                 vz.e[e] = ok[e] ? vz.e[e] : 0.0f;
             } else {
-                vz.e[e] = fmaf(-cv, d.e[e], rvz.e[e]);
+                vz.e[e] = fmaf(-cv, d.e[e], rvz[j].e[e]);
             }
         }
-        st_quad(io.vz_out + k * pitch + i, vz, ok, all);
-        sts4(&sm.svz[r + R][c4], vz);
+        st_quad(io.vz_out + (k + j) * pitch + i, vz, ok, all);
+        sts4(&sm.svz[r + j + R][c4], vz);
     }
-    {
-        const Q4 d = xdiff<R>(&spa[r + H][c4 + R], cc);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        const Q4 d = xdiff<R>(&spa[r + j + H][c4 + R], cc);
         Q4 vx;
         bool ok[4];
         bool all = true;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            ok[e] = !SP || (i + e < NX - 1 && k < NZ);
+            ok[e] = !SP || (i + e < NX - 1 && k + j < NZ);
             all = all && ok[e];
             if (SP) {
                 float A, B;
-                damp(sxh[e] + szi, A, B);
-                vx.e[e] = fmaf(-(B * cv), d.e[e], A * rvx.e[e]);
+                damp(sxh[e] + szi[j], A, B);
+                vx.e[e] = fmaf(-(B * cv), d.e[e], A * rvx[j].e[e]);
                 vx.e[e] = ok[e] ? vx.e[e] : 0.0f;
             } else {
-                vx.e[e] = fmaf(-cv, d.e[e], rvx.e[e]);
+                vx.e[e] = fmaf(-cv, d.e[e], rvx[j].e[e]);
             }
         }
-        st_quad(io.vx_out + k * pitch + i, vx, ok, all);
-        sts4(&sm.svx[r][c4 + R], vx);
+        st_quad(io.vx_out + (k + j) * pitch + i, vx, ok, all);
+        sts4(&sm.svx[r + j][c4 + R], vx);
     }
+    Q4 pold[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) pold[j] = pw[j + R - 1];
     // halo v (not written out)
 #pragma unroll
     for (int q = 0; q < Q::NH; q++) {
@@ -1429,8 +1447,8 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
         if (th.kind[q] == 1) {
             const int kh = k0 - R + ha;
             Q4 w[2 * R];
-            window<R, TX + 4 * R>(w, spa, ha + 1, hb + H);
-            const Q4 d = zdiff<R>(w, cc);
+            window<2 * R, TX + 4 * R>(w, spa, ha + 1, hb + H);
+            const Q4 d = zdiff<R>(w, 0, cc);
             Q4 val;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
@@ -1468,11 +1486,15 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
     }
     __syncthreads();
 
-    // own quad: p^{n+1}
-    {
+    // own quads: p^{n+1}, z differences from a window over the v_z rows
+    Q4 zw[NW];
+    window<NW, TX>(zw, sm.svz, r, c4);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
         float u[12];
         {
-            const Q4 a0 = lds4(&sm.svx[r][c4]), a1 = lds4(&sm.svx[r][c4 + 4]), a2 = lds4(&sm.svx[r][c4 + 8]);
+            const Q4 a0 = lds4(&sm.svx[r + j][c4]), a1 = lds4(&sm.svx[r + j][c4 + 4]),
+                     a2 = lds4(&sm.svx[r + j][c4 + 8]);
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 u[e] = a0.e[e];
@@ -1480,8 +1502,6 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
                 u[8 + e] = a2.e[e];
             }
         }
-        Q4 zw[2 * R];
-        window<R, TX>(zw, sm.svz, r, c4);
         Q4 val;
         bool ok[4];
         bool all = true;
@@ -1491,21 +1511,21 @@ __device__ __forceinline__ void fwd_quad(const FwdArgs &a, const StepIO &io, int
 #pragma unroll
             for (int m = 1; m <= R; m++) {
                 d = fmaf(cc[m - 1], u[e + R + m - 1] - u[e + R - m], d);
-                d = fmaf(cc[m - 1], zw[R + m - 1].e[e] - zw[R - m].e[e], d);
+                d = fmaf(cc[m - 1], zw[j + R + m - 1].e[e] - zw[j + R - m].e[e], d);
             }
-            ok[e] = !SP || (i + e < NX && k < NZ);
+            ok[e] = !SP || (i + e < NX && k + j < NZ);
             all = all && ok[e];
-            float cp = rk.e[e];
+            float cp = rk[j].e[e];
             if (SP) {
                 float A, B;
-                damp(sxi[e] + szi, A, B);
+                damp(sxi[e] + szi[j], A, B);
                 cp *= B;
-                val.e[e] = fmaf(-cp, d, A * pold.e[e]);
+                val.e[e] = fmaf(-cp, d, A * pold[j].e[e]);
             } else {
-                val.e[e] = fmaf(-cp, d, pold.e[e]);
+                val.e[e] = fmaf(-cp, d, pold[j].e[e]);
             }
         }
-        st_quad(io.p_out + k * pitch + i, val, ok, all);
+        st_quad(io.p_out + (k + j) * pitch + i, val, ok, all);
     }
 }
 
@@ -1514,7 +1534,7 @@ template <int R, int TX, int TZ, int NT, bool SP, class In, class Work>
 __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int i0, int k0,
                                          In &in, Work &sm) {
     using Q = QuadShape<R, TX, TZ, NT>;
-    constexpr int H = 2 * R;
+    constexpr int H = 2 * R, L = Q::L, NW = Q::NW;
     const GridArgs &g = a.g;
     const int pitch = g.pitch, NX = g.NX, NZ = g.NZ;
     const QuadThread<R, TX, TZ, NT> th;
@@ -1524,7 +1544,7 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
     for (int m = 0; m < R; m++) cc[m] = g.c[m];
     const float cv = g.cv;
 
-    float sxi[4], sxh[4], szi = 0.0f, szh = 0.0f;
+    float sxi[4], sxh[4], szi[L], szh[L];
     if (!In::kAhead) in.wait();
     if (SP) {
 #pragma unroll
@@ -1532,12 +1552,21 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
             sxi[e] = __ldg(g.sxi + min(i + e, NX - 1));
             sxh[e] = __ldg(g.sxh + min(i + e, NX - 1));
         }
-        szi = __ldg(g.szi + min(k, NZ - 1));
-        szh = __ldg(g.szh + min(k, NZ - 1));
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+            szi[j] = __ldg(g.szi + min(k + j, NZ - 1));
+            szh[j] = __ldg(g.szh + min(k + j, NZ - 1));
+        }
     }
     in.template prestage<true>();   // C_p of the staged region (constants)
     if (In::kAhead) in.wait();
-    const Q4 rvx = q4(in.vx4(r, c4 + R)), rvz = q4(in.vz4(r + R, c4)), rp = q4(in.p4(r, c4));
+    Q4 rvx[L], rvz[L], rp[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+        rvx[j] = q4(in.vx4(r + j, c4 + R));
+        rvz[j] = q4(in.vz4(r + j + R, c4));
+        rp[j] = q4(in.p4(r + j, c4));
+    }
     Q4 rh[Q::NH];
 #pragma unroll
     for (int q = 0; q < Q::NH; q++)
@@ -1548,19 +1577,20 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
     __syncthreads();
     float (&spa)[TZ + 4 * R][TX + 4 * R] = in.sp();
 
-    {   // vbar_x' = vbar_x + D+ q; C_vx vbar_x' kept for the p update
-        const Q4 d = xdiff<R>(&spa[r + H][c4 + R], cc);
+#pragma unroll
+    for (int j = 0; j < L; j++) {   // vbar_x' = vbar_x + D+ q; C_vx vbar_x' kept for the p update
+        const Q4 d = xdiff<R>(&spa[r + j + H][c4 + R], cc);
         Q4 vx, ox;
         bool ok[4];
         bool all = true;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            ok[e] = !SP || (i + e < NX - 1 && k < NZ);
+            ok[e] = !SP || (i + e < NX - 1 && k + j < NZ);
             all = all && ok[e];
-            const float vbx = rvx.e[e] + d.e[e];
+            const float vbx = rvx[j].e[e] + d.e[e];
             if (SP) {
                 float A, B;
-                damp(sxh[e] + szi, A, B);
+                damp(sxh[e] + szi[j], A, B);
                 vx.e[e] = ok[e] ? (B * cv) * vbx : 0.0f;
                 ox.e[e] = A * vbx;
             } else {
@@ -1568,29 +1598,32 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
                 ox.e[e] = vbx;
             }
         }
-        st_quad(io.vx_out + k * pitch + i, ox, ok, all);
-        sts4(&sm.svx[r][c4 + R], vx);
+        st_quad(io.vx_out + (k + j) * pitch + i, ox, ok, all);
+        sts4(&sm.svx[r + j][c4 + R], vx);
     }
     {   // vbar_z' likewise, from the window down the column
-        Q4 w[2 * R];
-        window<R, TX + 4 * R>(w, spa, r + H - R + 1, c4 + H);
-        const Q4 d = zdiff<R>(w, cc);
-        Q4 vz, out;
-        bool ok[4];
-        bool all = true;
+        Q4 w[NW];
+        window<NW, TX + 4 * R>(w, spa, r + H - R + 1, c4 + H);
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            ok[e] = !SP || (i + e < NX && k < NZ - 1);
-            all = all && ok[e];
-            const float vb = rvz.e[e] + d.e[e];
-            float A = 1.0f, B = 1.0f;
-            if (SP) damp(sxi[e] + szh, A, B);
-            const float v = (B * cv) * vb;
-            out.e[e] = SP ? A * vb : vb;
-            vz.e[e] = ok[e] ? v : 0.0f;
+        for (int j = 0; j < L; j++) {
+            const Q4 d = zdiff<R>(w, j, cc);
+            Q4 vz, out;
+            bool ok[4];
+            bool all = true;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                ok[e] = !SP || (i + e < NX && k + j < NZ - 1);
+                all = all && ok[e];
+                const float vb = rvz[j].e[e] + d.e[e];
+                float A = 1.0f, B = 1.0f;
+                if (SP) damp(sxi[e] + szh[j], A, B);
+                const float v = (B * cv) * vb;
+                out.e[e] = SP ? A * vb : vb;
+                vz.e[e] = ok[e] ? v : 0.0f;
+            }
+            st_quad(io.vz_out + (k + j) * pitch + i, out, ok, all);
+            sts4(&sm.svz[r + j + R][c4], vz);
         }
-        st_quad(io.vz_out + k * pitch + i, out, ok, all);
-        sts4(&sm.svz[r + R][c4], vz);
     }
     // halo vbar' (not written out)
 #pragma unroll
@@ -1599,8 +1632,8 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
         if (th.kind[q] == 1) {
             const int kh = k0 - R + ha;
             Q4 w[2 * R];
-            window<R, TX + 4 * R>(w, spa, ha + 1, hb + H);
-            const Q4 d = zdiff<R>(w, cc);
+            window<2 * R, TX + 4 * R>(w, spa, ha + 1, hb + H);
+            const Q4 d = zdiff<R>(w, 0, cc);
             Q4 val;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
@@ -1638,10 +1671,15 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
     }
     __syncthreads();
 
-    {   // pbar <- A_p pbar + D- (C_v vbar')
+    // pbar <- A_p pbar + D- (C_v vbar')
+    Q4 zw[NW];
+    window<NW, TX>(zw, sm.svz, r, c4);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
         float u[12];
         {
-            const Q4 a0 = lds4(&sm.svx[r][c4]), a1 = lds4(&sm.svx[r][c4 + 4]), a2 = lds4(&sm.svx[r][c4 + 8]);
+            const Q4 a0 = lds4(&sm.svx[r + j][c4]), a1 = lds4(&sm.svx[r + j][c4 + 4]),
+                     a2 = lds4(&sm.svx[r + j][c4 + 8]);
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 u[e] = a0.e[e];
@@ -1649,8 +1687,6 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
                 u[8 + e] = a2.e[e];
             }
         }
-        Q4 zw[2 * R];
-        window<R, TX>(zw, sm.svz, r, c4);
         Q4 out;
         bool ok[4];
         bool all = true;
@@ -1660,19 +1696,19 @@ __device__ __forceinline__ void adj_quad(const AdjArgs &a, const StepIO &io, int
 #pragma unroll
             for (int m = 1; m <= R; m++) {
                 d = fmaf(cc[m - 1], u[e + R + m - 1] - u[e + R - m], d);
-                d = fmaf(cc[m - 1], zw[R + m - 1].e[e] - zw[R - m].e[e], d);
+                d = fmaf(cc[m - 1], zw[j + R + m - 1].e[e] - zw[j + R - m].e[e], d);
             }
-            ok[e] = !SP || (i + e < NX && k < NZ);
+            ok[e] = !SP || (i + e < NX && k + j < NZ);
             all = all && ok[e];
             if (SP) {
                 float A, B;
-                damp(sxi[e] + szi, A, B);
-                out.e[e] = fmaf(A, rp.e[e], d);
+                damp(sxi[e] + szi[j], A, B);
+                out.e[e] = fmaf(A, rp[j].e[e], d);
             } else {
-                out.e[e] = rp.e[e] + d;
+                out.e[e] = rp[j].e[e] + d;
             }
         }
-        st_quad(io.p_out + k * pitch + i, out, ok, all);
+        st_quad(io.p_out + (k + j) * pitch + i, out, ok, all);
     }
 }
 

@@ -25,7 +25,7 @@ W_D, W_M, W_M_INV = 0, 1, 2
 HOOK_NONE, HOOK_BREAKDOWN, HOOK_NONFINITE = 0, 1, 2
 
 # every symbol the header declares, in declaration order
-N_TILE_CONFIGS = 13   # SSX_NUM_TILE_CONFIGS of include/ssx.h
+N_TILE_CONFIGS = 14   # SSX_NUM_TILE_CONFIGS of include/ssx.h
 N_MARCH_CONFIGS = 4   # SSX_NUM_MARCH_CONFIGS: marching-kernel ids 2N .. 2N + N_MARCH_CONFIGS - 1
 N_TWO_CONFIGS = 3     # SSX_NUM_TWO_CONFIGS: two-step kernel ids 2N + N_MARCH_CONFIGS + m
 

@@ -121,7 +121,7 @@ def test_bench_kernel_names_match_the_configuration_tables():
     march = re.findall(r"X\((\d+), (\d+), (\d+)\)\s", src)
     two = re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)\s", src)
     n = len(tile)
-    assert n == 13 and len(march) == 4 and len(two) == 3
+    assert n == 14 and len(march) == 4 and len(two) == 3
     for cid, tx, tz, nt, quads in tile:
         name = f"{tx}x{tz}/{nt}" + (" quads" if quads == "1" else "")
         assert bench._kernel_name(int(cid)) == f"k_multi {name}"
