@@ -384,12 +384,16 @@ def run_ours(args):
     return 0
 
 
-def batched_survey(shots, nt, maxit, tile_config=-1):
+def batched_survey(shots, nt, maxit, tile_config=-1, rtol=0.0, solo=False):
     """The batched survey (shots on one 2001 x 801 lens model): one
     ssx_solve_batch call, all shots' sweeps of each PCG phase in shared
     launches; a warm-up call (tuning, graph capture), then one timed call of
-    the set-up phases plus `maxit` iterations. Returns the measurement as a
-    dict (stencil throughput, its HBM roofline, wall time)."""
+    the set-up phases plus at most `maxit` iterations (stopping at `rtol`).
+    Returns the measurement as a dict (stencil throughput, its HBM roofline,
+    wall time). With `solo`, the same shots are then solved one at a time
+    (each its own ssx_solve_source_subproblem, same maxit and rtol; one
+    untimed warm-up solve first) and both arms' solves/s are reported, with
+    whether every batched source equals its one-at-a-time source bit for bit."""
     import torch
     from paper_2203_16573_gb300 import ssx, workloads as W
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -408,7 +412,7 @@ def batched_survey(shots, nt, maxit, tile_config=-1):
     lead = ctxs[0]
     if tile_config >= 0:
         lead.set_tile_config(tile_config)
-    ssx.solve_batch(ctxs, ds, alphas, maxit, 0.0, ssx.MODE_PCG, outs)
+    ssx.solve_batch(ctxs, ds, alphas, maxit, rtol, ssx.MODE_PCG, outs)
     torch.cuda.synchronize()
     lead.reset_stats()
     lead.set_timing(True)
@@ -416,7 +420,7 @@ def batched_survey(shots, nt, maxit, tile_config=-1):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    _, hist, iters, status = ssx.solve_batch(ctxs, ds, alphas, maxit, 0.0, ssx.MODE_PCG, outs)
+    _, hist, iters, status = ssx.solve_batch(ctxs, ds, alphas, maxit, rtol, ssx.MODE_PCG, outs)
     ev1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -425,12 +429,29 @@ def batched_survey(shots, nt, maxit, tile_config=-1):
     ms = ev0.elapsed_time(ev1)
     hbm, peak_kind = peaks()
     gpts = st["timed_point_updates"] / (st["sweep_ms"] / 1000.0) / 1e9
+    solo_rec = None
+    if solo:
+        ctxs[0].solve(ds[0], alphas[0], maxit, rtol)   # warm-up: tuning of the single-shot phases
+        torch.cuda.synchronize()
+        clk_s = ClockSampler(torch.cuda.current_device())
+        clk_s.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solo_out = [c.solve(d, a, maxit, rtol) for c, d, a in zip(ctxs, ds, alphas)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        solo_rec = {"value": shots / (ms_s / 1000.0), "unit": "solves/s", "ms": ms_s,
+                    "iterations": [int(o[2]) for o in solo_out],
+                    "results_identical_to_batched": all(torch.equal(o[0], b) for o, b in zip(solo_out, outs)),
+                    "clocks": clk_s.stop()}
     for c in ctxs:
         c.close()
     return {"metric": "batched survey: stencil Gpt-updates/s & HBM % of peak", "value": gpts,
             "unit": "Gpt-updates/s", "ms": ms,
             "config": {"workload": f"c3 survey: {shots} shots, 2001x801 lens model, h 5 m, "
-                                   f"order 8, nt {nt}, set-up + {maxit} PCG iterations",
+                                   f"order 8, nt {nt}, set-up + {maxit} PCG iterations"
+                                   + (f" at most, each shot stopped at {rtol:g} rel. residual" if rtol else ""),
                        "l2": "inputs larger than L2 (per-step state of all shots "
                              f"~{shots * 64 / 1000:.1f} GB)"},
             "iterations": iters, "status": sorted(set(status)),
@@ -442,7 +463,9 @@ def batched_survey(shots, nt, maxit, tile_config=-1):
                          "bytes_per_point_update": BYTES_PER_POINT,
                          "avg_launch_us": 1000.0 * st["sweep_ms"] / max(st["timed_steps"], 1)},
             "stencil_share_of_timed_region": st["sweep_ms"] / ms if ms else None,
-            "gpu_launches": st["kernel_launches"], "tile_config": tile_config, "clocks": clk}
+            "gpu_launches": st["kernel_launches"], "tile_config": tile_config, "clocks": clk,
+            "rtol": rtol, "solves_per_s": shots / (ms / 1000.0),
+            **({"one_at_a_time": solo_rec} if solo_rec else {})}
 
 
 def run_batch(args):
@@ -453,7 +476,7 @@ def run_batch(args):
     from paper_2203_16573_gb300 import build
     build.build()
     torch.cuda.set_device(0)
-    r = batched_survey(args.shots, args.nt, args.maxit, args.tile_config)
+    r = batched_survey(args.shots, args.nt, args.maxit, args.tile_config, args.rtol, args.solo)
     line = {"metric": r["metric"], "value": r["value"], "unit": r["unit"], "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": r["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -750,6 +773,10 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--scale", type=float, default=0.25)
     ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--rtol", type=float, default=0.0,
+                    help="c3: stop each shot at this relative residual (0: run maxit iterations)")
+    ap.add_argument("--solo", action="store_true",
+                    help="c3: also solve the shots one at a time and report both arms' solves/s")
     ap.add_argument("--no-solo", action="store_true",
                     help="serve: run the batched arm only (no one-at-a-time comparison)")
     ap.add_argument("--cache-mb", type=float, default=-1,
