@@ -2093,7 +2093,7 @@ static int velocity_gradient(ssx_ctx *c, const double *h, const double *d, doubl
         }
     }
     // 4. onto the physical model: dPhi/dv = 2 rho v (dt/h) sum dPhi/dkappa~
-    CK(launch_grad_fold(grad, gacc, c->vel, c->gd.nx, c->gd.nz, c->gd.n_sponge, G.L.NX,
+    CK(launch_grad_fold(grad, gacc, c->vel, G.args.kap, G.L.pitch, c->gd.nx, c->gd.nz, c->gd.n_sponge, G.L.NX,
                         2.0 * c->rho * c->gd.dt / c->gd.h, s));
     return SSX_OK;
     };

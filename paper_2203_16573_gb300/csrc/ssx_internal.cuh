@@ -287,8 +287,11 @@ cudaError_t launch_colscale_add(double *q, const double *in, const double *w, do
 // Velocity-gradient kernels (gradient.cu).
 cudaError_t launch_grad_accum(double *g, const float *mu, const float *pn1, const float *pn,
                               const GridArgs &a, cudaStream_t s);
-cudaError_t launch_grad_fold(double *out, const double *g, const float *vel, int nx, int nz,
-                             int nsp, int NX, double scale, cudaStream_t s);
+// g / kappa~ summed over each model point's padded copies (kap: kappa dt/h,
+// origin-offset storage with the given pitch)
+cudaError_t launch_grad_fold(double *out, const double *g, const float *vel, const float *kap,
+                             int pitch, int nx, int nz, int nsp, int NX, double scale,
+                             cudaStream_t s);
 cudaError_t launch_residual2(double *ybar, const double *y, const double *d, size_t n,
                              cudaStream_t s);
 
