@@ -464,7 +464,9 @@ def batched_survey(shots, nt, maxit, tile_config=-1, rtol=0.0, solo=False):
                          "avg_launch_us": 1000.0 * st["sweep_ms"] / max(st["timed_steps"], 1)},
             "stencil_share_of_timed_region": st["sweep_ms"] / ms if ms else None,
             "gpu_launches": st["kernel_launches"], "tile_config": tile_config, "clocks": clk,
-            "rtol": rtol, "solves_per_s": shots / (ms / 1000.0),
+            "rtol": rtol,
+            # solves/s only for solves run to a tolerance (not a bounded iteration count)
+            **({"solves_per_s": shots / (ms / 1000.0)} if rtol > 0 else {}),
             **({"one_at_a_time": solo_rec} if solo_rec else {})}
 
 
